@@ -1,0 +1,224 @@
+/*
+ * ctqr.h -- C ABI of libctqr: direct algebraic CT reconstruction by dense
+ * Householder QR on one B300 (sm_103a).
+ *
+ * The three operations follow the paper's statement of the problem
+ * (arxiv 2412.07631, Sec. 2): build the system matrix A of the linear model
+ * A X = B (Eq. 1), factor A = QR once (Eq. 2), and solve X = R^-1 (Q^T B)
+ * for as many sinograms as share A (Eq. 3), with Q kept as Householder
+ * reflectors and R^-1 applied by back-substitution, never formed.
+ *
+ * Conventions used by every call:
+ *   - Dense matrices are column-major (Fortran/LAPACK): element (i, j) of a
+ *     matrix with leading dimension ld is at p[i + j*ld].  Leading dimensions
+ *     are in elements and must be >= the row count.
+ *   - Ray (row) index i = v*n_bins + d (view v, detector bin d); pixel
+ *     (column) index j = iy*n_side + ix.  The image has n = n_side^2 pixels,
+ *     the scan m = n_views*n_bins rays.
+ *   - With sqrt_lambda > 0 the factored matrix is A~ = [A; sqrt_lambda*I]
+ *     with M' = m + n rows and the right-hand sides are b~ = [b; 0]
+ *     (Tikhonov regularisation; the paper's A is square-ish and full rank,
+ *     Sec. 3.1.1).  With sqrt_lambda = 0, M' = m and A must have full column
+ *     rank.
+ *   - "device" pointers are CUDA device addresses of the current device;
+ *     "host" pointers are ordinary host memory.  The library never keeps a
+ *     caller pointer after a call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated; results
+ *     written to device memory are valid once the stream reaches the call.
+ *   - Every call returns ct_status and never aborts the process.  A kernel
+ *     that times out a bounded wait, or sees a non-finite value, records it in
+ *     a device status word that the library reads at its synchronisation
+ *     points and returns as CT_ERR_TIMEOUT / CT_ERR_NONFINITE.
+ *
+ * Ownership: the library owns the storage of a ct_system and a ct_factor
+ * (device memory allocated by the library); the caller owns every buffer it
+ * passes in.  Handles are not thread-safe: one host thread per handle.
+ */
+#ifndef CTQR_H
+#define CTQR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CT_API __attribute__((visibility("default")))
+#else
+#define CT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CT_OK = 0,
+    CT_ERR_ARG = 1,         /* invalid argument (null pointer, bad size/leading dimension) */
+    CT_ERR_OOM = 2,         /* device or pinned-host allocation failed */
+    CT_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
+    CT_ERR_RANK = 4,        /* |R_jj| < n * u * max|R_jj|: A~ is numerically rank deficient */
+    CT_ERR_NOCONV = 5,      /* refinement hit its step limit; best X still written */
+    CT_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired; the kernel returned early */
+    CT_ERR_NONFINITE = 7,   /* NaN/Inf met in the input or in a reflector */
+    CT_ERR_HOSTMEM = 8,     /* host memory (pinned/registered) could not be obtained */
+    CT_ERR_STATE = 9,       /* handle in the wrong state (e.g. system already consumed) */
+    CT_ERR_UNSUPPORTED = 10 /* option not available in this build */
+} ct_status;
+
+/* Arithmetic of the factorisation and the solve.
+ *  CT_FP64        FP64 storage and arithmetic throughout.
+ *  CT_FP32        FP32 storage and arithmetic (the paper's single-precision
+ *                 variant, Sec. 2.2 last paragraph and Sec. 3.1.2).
+ *  CT_TF32_REFINE FP32 storage, trailing updates and Q^T applications on the
+ *                 tensor cores with TF32 operands and FP32 accumulation, then
+ *                 FP64 iterative refinement (residual and update in FP64).
+ *  CT_BF16_REFINE as CT_TF32_REFINE with BF16 operands. */
+typedef enum { CT_FP64 = 0, CT_FP32 = 1, CT_TF32_REFINE = 2, CT_BF16_REFINE = 3 } ct_precision;
+
+/* Parallel-beam scan geometry.  Pixels of width pixel_width tile the square
+ * centred on the rotation axis; views at v*arc_deg/n_views degrees
+ * (v = 0..n_views-1); bin d centred at (d - (n_bins-1)/2)*bin_width. */
+typedef struct {
+    int32_t n_side;
+    int32_t n_views;
+    int32_t n_bins;
+    double pixel_width;  /* > 0, usually 1 */
+    double bin_width;    /* > 0, usually 1 */
+    double arc_deg;      /* usually 180 */
+    double sqrt_lambda;  /* >= 0; 0 = no regularisation rows */
+} ct_geometry;
+
+typedef struct {
+    ct_precision precision;
+    int32_t refine_max_iter; /* refinement step limit (<= 0: 10) */
+    double refine_tol;       /* stop when max_s ||dx_s||/||x_s|| <= tol (<= 0: 1e-7) */
+    int32_t nb_outer;        /* outer WY block width (0: automatic) */
+    int32_t nb_inner;        /* panel width (0: automatic) */
+} ct_opts;
+
+typedef struct {
+    int32_t iterations;       /* refinement steps taken (0 for CT_FP64 / CT_FP32) */
+    double last_rel_update;   /* max over slices of ||dx||/||x|| in the last step */
+    double rjj_min_abs;       /* min |R_jj| */
+    double rjj_max_abs;       /* max |R_jj| */
+} ct_solve_info;
+
+typedef struct ct_system_s *ct_system;
+typedef struct ct_factor_s *ct_factor;
+
+/* Human-readable name of a status code (static string). */
+CT_API const char *ct_status_str(ct_status s);
+
+/* Detail of the last error raised on the calling thread (static per-thread
+ * buffer, "" if none). */
+CT_API const char *ct_last_error(void);
+
+/* Build the system matrix (Sec. 2 Eq. 1: a_ij = contribution of ray i to
+ * pixel j), here the Siddon intersection length of ray i in pixel j.
+ * On the device: the dense column-major A~ (M' x n, leading dimension lda,
+ * `storage` = CT_FP64 -> double, otherwise float) and an FP64 CSR and CSC of
+ * the m ray rows (for FP64 residuals).  The view table is computed once on
+ * the host.  `out` receives a new handle; free it with ct_system_free.
+ * Errors: CT_ERR_ARG (bad geometry), CT_ERR_OOM, CT_ERR_CUDA. */
+CT_API ct_status ct_build_system(const ct_geometry *geom, ct_precision storage, void *stream,
+                          ct_system *out);
+
+/* Sizes of a built system. Any output pointer may be NULL. */
+CT_API ct_status ct_system_info(ct_system sys, int64_t *m_rays, int64_t *n_pixels, int64_t *rows,
+                         int64_t *lda, int64_t *nnz);
+
+/* Device pointers to the system's storage (owned by the library, valid until
+ * ct_system_free; the dense pointer is NULL once ct_qr_factor consumed it).
+ * row_ptr: int64[m+1]; col_idx: int32[nnz]; val: double[nnz] (CSR of A, ray
+ * rows only, entries of a row in Siddon walk order).  Any output may be NULL. */
+CT_API ct_status ct_system_device_ptrs(ct_system sys, void **dense, const int64_t **row_ptr,
+                                const int32_t **col_idx, const double **val);
+
+/* Copy the system to HOST buffers (synchronous; any pointer may be NULL):
+ * row_ptr int64[m+1], col_idx int32[nnz], val double[nnz] (CSR of the ray
+ * rows, each row in Siddon walk order); dense: the column-major M' x n matrix
+ * A~ in the storage type (double for CT_FP64, float otherwise) with leading
+ * dimension ldd >= M'.  CT_ERR_STATE if dense is requested after
+ * ct_qr_factor consumed it. */
+CT_API ct_status ct_system_export(ct_system sys, int64_t *row_ptr, int32_t *col_idx, double *val,
+                           void *dense, int64_t ldd);
+
+/* P = A X on the device (forward projection with the CSR, FP64):
+ * X: device double, n x k, ldx >= n; P: device double, m x k, ldp >= m. */
+CT_API ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx, int32_t k, double *P,
+                             int64_t ldp, void *stream);
+
+/* Householder QR of A~ (Sec. 2 Eq. 2; Sec. 2.1 'dgeqrf'), blocked: panels
+ * of nb_inner columns are factored by reflectors H = I - tau v v^T
+ * (v(0) = 1, beta = -sign(alpha)||x||, LAPACK convention), and the trailing
+ * matrix is updated by compact-WY blocks of nb_outer columns,
+ * C <- C - V T^T V^T C ... as (I - V T V^T)^T C.  The factorisation happens in
+ * place: the system's dense storage moves into the factor (R in the upper
+ * triangle, V below the diagonal), so the system's dense pointer becomes
+ * NULL; its CSR stays with the system, which must outlive the factor when a
+ * refining precision is used.  opts->precision must match the storage the
+ * system was built with (CT_FP64 <-> double, others <-> float).
+ * Synchronises `stream` at the end to check the device status and R's
+ * diagonal.  Errors: CT_ERR_ARG, CT_ERR_STATE (already consumed), CT_ERR_RANK,
+ * CT_ERR_NONFINITE, CT_ERR_TIMEOUT, CT_ERR_OOM, CT_ERR_CUDA. */
+CT_API ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_factor *out);
+
+/* Device pointers of the factor: VR (M' x n, leading dimension lda, R in the
+ * upper triangle, Householder vectors below), tau[n] (same element type as
+ * VR).  For tests and checkpointing; owned by the library. */
+CT_API ct_status ct_factor_device_ptrs(ct_factor f, void **VR, int64_t *lda, void **tau);
+
+/* Copy the factor to HOST buffers (synchronous; any pointer may be NULL):
+ * VR (M' x n, leading dimension ldv >= M', R on and above the diagonal,
+ * Householder vectors below it), tau[n]; element type double for CT_FP64,
+ * float otherwise. */
+CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau);
+
+/* X = R^-1 (Q^T b~) for k sinograms (Sec. 2 Eq. 3: C = Q^T B, then R X = C;
+ * Sec. 2.1 'dormqr' + 'dtrsm').  B: device, m x k (ray rows only; the
+ * library appends the zero rows of b~), ldb >= m.  X: device, n x k,
+ * ldx >= n.  Element type: float for a CT_FP32 factor, double otherwise.
+ * For refining factors, FP64 iterative refinement follows the first solve
+ * (residual and update in FP64, corrections from the low-precision factors)
+ * until the relative update is below opts->refine_tol or refine_max_iter
+ * steps.  opts may be NULL (factor's precision, defaults).  info may be NULL.
+ * Synchronises `stream` at the end (to read the convergence state).
+ * Errors: CT_ERR_ARG, CT_ERR_NOCONV (X still holds the best iterate),
+ * CT_ERR_NONFINITE, CT_ERR_TIMEOUT, CT_ERR_OOM, CT_ERR_CUDA. */
+CT_API ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
+                   const ct_opts *opts, void *stream, ct_solve_info *info);
+
+/* As ct_solve, but B and X are HOST buffers; the host-to-device copy of B
+ * and the device-to-host copy of X are part of the call (staged through
+ * library-owned pinned buffers).  Blocks until X is written. */
+CT_API ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
+                        const ct_opts *opts, void *stream, ct_solve_info *info);
+
+/* Adjoint of the (unrefined) solve map b -> x = R^-1 [Q^T b~]_{0:n}:
+ * gB = [Q [R^-T gX; 0]]_{0:m}  (the gradient of a loss L(x) with respect to
+ * b, given gX = dL/dx).  gX: device, n x k, ldgx >= n; gB: device, m x k,
+ * ldgb >= m; element type as ct_solve.  For refining factors the adjoint is
+ * taken in FP64 arithmetic on the FP32 factors followed by the same FP64
+ * refinement applied to the transposed problem.
+ * Errors: as ct_solve. */
+CT_API ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
+                           int64_t ldgb, const ct_opts *opts, void *stream, ct_solve_info *info);
+
+CT_API void ct_system_free(ct_system sys);
+CT_API void ct_factor_free(ct_factor f);
+
+/* ---- Kernel-level entry points (used by the parity tests) --------------- */
+
+/* GEMM engine behind the WY updates: C = alpha * op(A) * op(B) + beta * C,
+ * column-major, op = 'N' or 'T'.  kind: 0 = FP64 (DFMA), 1 = FP32 (FFMA),
+ * 2 = TF32 tensor cores (tcgen05, FP32 accumulate), 3 = BF16 tensor cores.
+ * A, B, C are device pointers of double (kind 0) or float (kinds 1-3).
+ * Errors: CT_ERR_ARG, CT_ERR_TIMEOUT, CT_ERR_CUDA. */
+CT_API ct_status ct_gemm(int32_t kind, char transa, char transb, int64_t M, int64_t N, int64_t K,
+                  double alpha, const void *A, int64_t lda, const void *B, int64_t ldb,
+                  double beta, void *C, int64_t ldc, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTQR_H */

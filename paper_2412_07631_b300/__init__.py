@@ -1,0 +1,266 @@
+"""Python binding of libctqr (include/ctqr.h): direct algebraic CT
+reconstruction by dense Householder QR on a B300 (arxiv 2412.07631).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libctqr.so; torch supplies device memory and the current stream.
+If the compiled library is missing and cannot be built, importing the
+binding's entry points raises -- there is no CPU fallback.
+
+Layout convention: a batch of k sinograms is a torch tensor of shape (k, m)
+(row s = sinogram s), which is exactly the column-major m x k matrix B of the
+C ABI with ldb = m; likewise images X are (k, n).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+GEMM_KINDS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+
+
+class Geometry(C.Structure):
+    _fields_ = [("n_side", C.c_int32), ("n_views", C.c_int32), ("n_bins", C.c_int32),
+                ("pixel_width", C.c_double), ("bin_width", C.c_double),
+                ("arc_deg", C.c_double), ("sqrt_lambda", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("refine_max_iter", C.c_int32),
+                ("refine_tol", C.c_double), ("nb_outer", C.c_int32), ("nb_inner", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("last_rel_update", C.c_double),
+                ("rjj_min_abs", C.c_double), ("rjj_max_abs", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class CTQRError(RuntimeError):
+    def __init__(self, status: int, name: str, detail: str):
+        super().__init__(f"{name}: {detail}")
+        self.status = status
+        self.name = name
+
+
+_LIB = None
+SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info",
+           "ct_system_device_ptrs", "ct_system_export", "ct_forward_project", "ct_qr_factor",
+           "ct_factor_device_ptrs", "ct_factor_export", "ct_solve", "ct_solve_host",
+           "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libctqr.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build()
+    L = C.CDLL(path)
+    vp, I64, I32 = C.c_void_p, C.c_int64, C.c_int32
+    L.ct_status_str.restype = C.c_char_p
+    L.ct_status_str.argtypes = [C.c_int]
+    L.ct_last_error.restype = C.c_char_p
+    L.ct_build_system.argtypes = [C.POINTER(Geometry), C.c_int, vp, C.POINTER(vp)]
+    L.ct_system_info.argtypes = [vp] + [C.POINTER(I64)] * 5
+    L.ct_system_device_ptrs.argtypes = [vp] + [C.POINTER(vp)] * 4
+    L.ct_system_export.argtypes = [vp, vp, vp, vp, vp, I64]
+    L.ct_forward_project.argtypes = [vp, vp, I64, I32, vp, I64, vp]
+    L.ct_qr_factor.argtypes = [vp, C.POINTER(Opts), vp, C.POINTER(vp)]
+    L.ct_factor_device_ptrs.argtypes = [vp, C.POINTER(vp), C.POINTER(I64), C.POINTER(vp)]
+    L.ct_factor_export.argtypes = [vp, vp, I64, vp]
+    for name in ("ct_solve", "ct_solve_host", "ct_solve_adjoint"):
+        getattr(L, name).argtypes = [vp, vp, I64, I32, vp, I64, C.POINTER(Opts), vp,
+                                     C.POINTER(SolveInfo)]
+    L.ct_system_free.argtypes = [vp]
+    L.ct_system_free.restype = None
+    L.ct_factor_free.argtypes = [vp]
+    L.ct_factor_free.restype = None
+    L.ct_gemm.argtypes = [I32, C.c_char, C.c_char, I64, I64, I64, C.c_double, vp, I64, vp, I64,
+                          C.c_double, vp, I64, vp]
+    for name in SYMBOLS:
+        if name not in ("ct_status_str", "ct_last_error", "ct_system_free", "ct_factor_free"):
+            getattr(L, name).restype = C.c_int
+    _LIB = L
+    return L
+
+
+def _check(st: int, allow=()):
+    if st == 0 or st in allow:
+        return st
+    L = lib()
+    raise CTQRError(st, L.ct_status_str(st).decode(), (L.ct_last_error() or b"").decode())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def make_geometry(n_side, n_views, n_bins, sqrt_lambda=0.0, pixel_width=1.0, bin_width=1.0,
+                  arc_deg=180.0) -> Geometry:
+    return Geometry(n_side, n_views, n_bins, pixel_width, bin_width, arc_deg, sqrt_lambda)
+
+
+class System:
+    """Device-resident system matrix A~ = [A; sqrt(lambda) I] (dense, column
+    major) plus the FP64 CSR/CSC of A, built by the Siddon kernels."""
+
+    def __init__(self, geom: Geometry, storage: str = "fp32", stream=None):
+        self.geom = geom
+        self.storage = storage
+        h = C.c_void_p()
+        _check(lib().ct_build_system(C.byref(geom), PRECISIONS[storage], _stream(stream), C.byref(h)))
+        self.h = h
+        vals = [C.c_int64() for _ in range(5)]
+        _check(lib().ct_system_info(h, *[C.byref(v) for v in vals]))
+        self.m, self.n, self.rows, self.lda, self.nnz = (v.value for v in vals)
+
+    def export_csr(self):
+        import numpy as np
+        rp = np.empty(self.m + 1, np.int64)
+        ci = np.empty(max(self.nnz, 1), np.int32)
+        va = np.empty(max(self.nnz, 1), np.float64)
+        _check(lib().ct_system_export(self.h, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, None, 0))
+        return rp, ci[: self.nnz], va[: self.nnz]
+
+    def export_dense(self):
+        import numpy as np
+        dt = np.float64 if self.storage == "fp64" else np.float32
+        A = np.empty((self.rows, self.n), dt, order="F")
+        _check(lib().ct_system_export(self.h, None, None, None, A.ctypes.data, self.rows))
+        return A
+
+    def forward(self, X, stream=None):
+        """P = A X for images X: torch float64 CUDA tensor (k, n) -> (k, m)."""
+        import torch
+        assert X.dtype == torch.float64 and X.is_cuda and X.is_contiguous()
+        k = X.shape[0]
+        P = torch.empty((k, self.m), dtype=torch.float64, device=X.device)
+        _check(lib().ct_forward_project(self.h, _ptr(X), self.n, k, _ptr(P), self.m, _stream(stream)))
+        return P
+
+    def factor(self, precision: str | None = None, nb_outer: int = 0, nb_inner: int = 0,
+               stream=None) -> "Factor":
+        if precision is None:
+            precision = "fp64" if self.storage == "fp64" else "tf32"
+        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner)
+        h = C.c_void_p()
+        _check(lib().ct_qr_factor(self.h, C.byref(o), _stream(stream), C.byref(h)))
+        return Factor(h, self, precision)
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().ct_system_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Factor:
+    """Householder factors (V, T blocks, R) of a System, on the device."""
+
+    def __init__(self, h, system: System, precision: str):
+        self.h = h
+        self.system = system  # kept alive: refinement reads its sparse rows
+        self.precision = precision
+        self.m, self.n, self.rows = system.m, system.n, system.rows
+        self.last_info = None
+
+    @property
+    def io_dtype(self):
+        import torch
+        return torch.float32 if self.precision == "fp32" else torch.float64
+
+    def _opts(self, max_iter=0, tol=0.0):
+        return Opts(PRECISIONS[self.precision], max_iter, tol, 0, 0)
+
+    def solve(self, B, out=None, max_iter: int = 0, tol: float = 0.0, stream=None,
+              allow_noconv: bool = False):
+        """X = R^-1 (Q^T b~) (+ FP64 refinement for refining precisions).
+        B: CUDA tensor (k, m) of io_dtype; returns X (k, n)."""
+        import torch
+        assert B.is_cuda and B.dtype == self.io_dtype and B.is_contiguous() and B.shape[1] == self.m
+        k = B.shape[0]
+        X = out if out is not None else torch.empty((k, self.n), dtype=B.dtype, device=B.device)
+        info = SolveInfo()
+        o = self._opts(max_iter, tol)
+        st = lib().ct_solve(self.h, _ptr(B), self.m, k, _ptr(X), self.n, C.byref(o),
+                            _stream(stream), C.byref(info))
+        _check(st, allow=(5,) if allow_noconv else ())
+        self.last_info = info.as_dict()
+        return X
+
+    def solve_host(self, B, out=None, max_iter: int = 0, tol: float = 0.0, stream=None):
+        """As solve() with HOST tensors (k, m) -> (k, n); the copies are inside the call."""
+        import torch
+        assert not B.is_cuda and B.dtype == self.io_dtype and B.is_contiguous()
+        k = B.shape[0]
+        X = out if out is not None else torch.empty((k, self.n), dtype=B.dtype)
+        info = SolveInfo()
+        o = self._opts(max_iter, tol)
+        _check(lib().ct_solve_host(self.h, _ptr(B), self.m, k, _ptr(X), self.n, C.byref(o),
+                                   _stream(stream), C.byref(info)))
+        self.last_info = info.as_dict()
+        return X
+
+    def adjoint(self, gX, out=None, stream=None):
+        """gB = [Q [R^-T gX; 0]]_{0:m} for gX (k, n) -> (k, m)."""
+        import torch
+        assert gX.is_cuda and gX.dtype == self.io_dtype and gX.is_contiguous()
+        k = gX.shape[0]
+        gB = out if out is not None else torch.empty((k, self.m), dtype=gX.dtype, device=gX.device)
+        info = SolveInfo()
+        o = self._opts()
+        _check(lib().ct_solve_adjoint(self.h, _ptr(gX), self.n, k, _ptr(gB), self.m, C.byref(o),
+                                      _stream(stream), C.byref(info)))
+        return gB
+
+    def export(self):
+        import numpy as np
+        dt = np.float64 if self.precision == "fp64" else np.float32
+        VR = np.empty((self.rows, self.n), dt, order="F")
+        tau = np.empty(self.n, dt)
+        _check(lib().ct_factor_export(self.h, VR.ctypes.data, self.rows, tau.ctypes.data))
+        return VR, tau
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().ct_factor_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def gemm(kind: str, transa: str, transb: str, M: int, N: int, K: int, alpha: float, A, lda: int,
+         B, ldb: int, beta: float, Cm, ldc: int, stream=None):
+    """C = alpha op(A) op(B) + beta C on column-major device buffers (torch
+    tensors used as raw storage)."""
+    _check(lib().ct_gemm(GEMM_KINDS[kind], transa.encode(), transb.encode(), M, N, K, alpha,
+                         _ptr(A), lda, _ptr(B), ldb, beta, _ptr(Cm), ldc, _stream(stream)))
+
+
+__all__ = ["Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
+           "lib_path", "make_geometry", "PRECISIONS", "SYMBOLS"]

@@ -1,0 +1,457 @@
+// api.cu -- the extern "C" entry points declared in include/ctqr.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace ctqr {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+ct_status cuda_status(cudaError_t e, const char *what, const char *file, int line) {
+    set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    if (e == cudaErrorMemoryAllocation) return CT_ERR_OOM;
+    return CT_ERR_CUDA;
+}
+
+int num_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (sms[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 148;
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+
+DevStatus *device_status() {
+    static DevStatus *st[64] = {nullptr};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!st[dev]) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(DevStatus)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, sizeof(DevStatus));
+        cudaDeviceSynchronize();
+        st[dev] = (DevStatus *)p;
+    }
+    return st[dev];
+}
+
+ct_status check_device_status(cudaStream_t s) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    DevStatus h{};
+    DevStatus *d = device_status();
+    if (!d) return CT_ERR_OOM;
+    CT_CUDA(cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.code == DEV_OK) return CT_OK;
+    CT_CUDA(cudaMemset(d, 0, sizeof(DevStatus)));
+    set_error("device status %d at site %d (aux %d)", h.code, h.where, h.aux);
+    switch (h.code) {
+        case DEV_TIMEOUT: return CT_ERR_TIMEOUT;
+        case DEV_NONFINITE: return CT_ERR_NONFINITE;
+        default: return CT_ERR_ARG;
+    }
+}
+
+ct_status Scratch::ensure(size_t need) {
+    if (need <= bytes) return CT_OK;
+    if (ptr) {
+        cudaError_t e = cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        if (e != cudaSuccess) return cuda_status(e, "cudaFree", __FILE__, __LINE__);
+    }
+    size_t sz = (need + (2u << 20) - 1) & ~(size_t)((2u << 20) - 1);
+    cudaError_t e = cudaMalloc(&ptr, sz);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return cuda_status(e, "cudaMalloc(scratch)", __FILE__, __LINE__);
+    }
+    bytes = sz;
+    return CT_OK;
+}
+
+Scratch::~Scratch() {
+    if (ptr) cudaFree(ptr);
+}
+
+}  // namespace ctqr
+
+using namespace ctqr;
+
+namespace {
+
+void free_system_storage(ct_system s) {
+    cudaFree(s->dense);
+    cudaFree(s->d_cs);
+    cudaFree(s->row_nnz);
+    cudaFree(s->row_ptr);
+    cudaFree(s->col);
+    cudaFree(s->val);
+    cudaFree(s->col_ptr);
+    cudaFree(s->csc_row);
+    cudaFree(s->csc_val);
+}
+
+template <typename T>
+ct_status dmalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc", __FILE__, __LINE__);
+    return CT_OK;
+}
+
+bool is_refine(ct_precision p) { return p == CT_TF32_REFINE || p == CT_BF16_REFINE; }
+
+}  // namespace
+
+extern "C" {
+
+const char *ct_status_str(ct_status s) {
+    switch (s) {
+        case CT_OK: return "CT_OK";
+        case CT_ERR_ARG: return "CT_ERR_ARG";
+        case CT_ERR_OOM: return "CT_ERR_OOM";
+        case CT_ERR_CUDA: return "CT_ERR_CUDA";
+        case CT_ERR_RANK: return "CT_ERR_RANK";
+        case CT_ERR_NOCONV: return "CT_ERR_NOCONV";
+        case CT_ERR_TIMEOUT: return "CT_ERR_TIMEOUT";
+        case CT_ERR_NONFINITE: return "CT_ERR_NONFINITE";
+        case CT_ERR_HOSTMEM: return "CT_ERR_HOSTMEM";
+        case CT_ERR_STATE: return "CT_ERR_STATE";
+        case CT_ERR_UNSUPPORTED: return "CT_ERR_UNSUPPORTED";
+    }
+    return "CT_ERR_UNKNOWN";
+}
+
+const char *ct_last_error(void) { return g_err; }
+
+ct_status ct_build_system(const ct_geometry *geom, ct_precision storage, void *stream,
+                          ct_system *out) {
+    if (!geom || !out) return CT_ERR_ARG;
+    *out = nullptr;
+    const ct_geometry g = *geom;
+    if (g.n_side < 1 || g.n_views < 1 || g.n_bins < 1 || !(g.pixel_width > 0) ||
+        !(g.bin_width > 0) || !(g.arc_deg > 0) || !(g.sqrt_lambda >= 0) ||
+        !std::isfinite(g.sqrt_lambda) || g.n_side > 46340) {
+        set_error("invalid geometry");
+        return CT_ERR_ARG;
+    }
+    if ((int64_t)g.n_views * g.n_bins > INT32_MAX) {
+        set_error("too many rays");
+        return CT_ERR_ARG;
+    }
+    if (storage < CT_FP64 || storage > CT_BF16_REFINE) return CT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    ct_system sys = new (std::nothrow) ct_system_s;
+    if (!sys) return CT_ERR_HOSTMEM;
+    sys->geom = g;
+    sys->fp64 = storage == CT_FP64;
+    sys->m = (int64_t)g.n_views * g.n_bins;
+    sys->n = (int64_t)g.n_side * g.n_side;
+    sys->rows = sys->m + (g.sqrt_lambda > 0 ? sys->n : 0);
+    if (sys->rows < sys->n) {
+        set_error("fewer rows (%lld) than unknowns (%lld): add views/bins or sqrt_lambda > 0",
+                  (long long)sys->rows, (long long)sys->n);
+        delete sys;
+        return CT_ERR_ARG;
+    }
+    sys->lda = round_up(sys->rows, 32);
+    auto fail = [&](ct_status st) {
+        free_system_storage(sys);
+        delete sys;
+        return st;
+    };
+    // View table: theta_v = v * arc / n_views degrees; exact axis values.
+    std::vector<double> cs(2 * (size_t)g.n_views);
+    for (int v = 0; v < g.n_views; ++v) {
+        double theta = ((double)v * g.arc_deg / (double)g.n_views) * (M_PI / 180.0);
+        double c = std::cos(theta), sn = std::sin(theta);
+        if (std::fabs(c) < 1e-15) { c = 0.0; sn = (sn > 0.0) ? 1.0 : -1.0; }
+        if (std::fabs(sn) < 1e-15) { sn = 0.0; c = (c > 0.0) ? 1.0 : -1.0; }
+        cs[2 * v] = c;
+        cs[2 * v + 1] = sn;
+    }
+    ct_status st;
+    if ((st = dmalloc(&sys->d_cs, cs.size())) != CT_OK) return fail(st);
+    if (cudaMemcpyAsync(sys->d_cs, cs.data(), sizeof(double) * cs.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return fail(CT_ERR_CUDA);
+    if ((st = dmalloc(&sys->row_nnz, sys->m)) != CT_OK) return fail(st);
+    if ((st = dmalloc(&sys->row_ptr, sys->m + 1)) != CT_OK) return fail(st);
+    SiddonArgs a{g.n_side, g.n_views, g.n_bins, g.pixel_width, g.bin_width, g.sqrt_lambda,
+                 sys->d_cs, sys->row_nnz, sys->row_ptr, nullptr, nullptr, &sys->tmp};
+    if ((st = siddon_build(a, s)) != CT_OK) return fail(st);
+    int64_t nnz = 0;
+    if (cudaMemcpyAsync(&nnz, sys->row_ptr + sys->m, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(CT_ERR_CUDA);
+    sys->nnz = nnz;
+    if ((st = dmalloc(&sys->col, nnz)) != CT_OK) return fail(st);
+    if ((st = dmalloc(&sys->val, nnz)) != CT_OK) return fail(st);
+    const size_t es = sys->fp64 ? 8 : 4;
+    {
+        cudaError_t e = cudaMalloc(&sys->dense, es * (size_t)sys->lda * sys->n);
+        if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(dense A)", __FILE__, __LINE__));
+        e = cudaMemsetAsync(sys->dense, 0, es * (size_t)sys->lda * sys->n, s);
+        if (e != cudaSuccess) return fail(CT_ERR_CUDA);
+    }
+    a.d_col = sys->col;
+    a.d_val = sys->val;
+    if ((st = siddon_fill(a, sys->dense, sys->fp64, sys->lda, s)) != CT_OK) return fail(st);
+    if ((st = dmalloc(&sys->col_ptr, sys->n + 1)) != CT_OK) return fail(st);
+    if ((st = dmalloc(&sys->csc_row, nnz)) != CT_OK) return fail(st);
+    if ((st = dmalloc(&sys->csc_val, nnz)) != CT_OK) return fail(st);
+    if ((st = build_csc(sys->m, sys->n, nnz, sys->row_ptr, sys->col, sys->val, sys->col_ptr,
+                        sys->csc_row, sys->csc_val, sys->tmp, sys->tmp2, s)) != CT_OK)
+        return fail(st);
+    if ((st = check_device_status(s)) != CT_OK) return fail(st);
+    *out = sys;
+    return CT_OK;
+}
+
+ct_status ct_system_info(ct_system sys, int64_t *m_rays, int64_t *n_pixels, int64_t *rows,
+                         int64_t *lda, int64_t *nnz) {
+    if (!sys) return CT_ERR_ARG;
+    if (m_rays) *m_rays = sys->m;
+    if (n_pixels) *n_pixels = sys->n;
+    if (rows) *rows = sys->rows;
+    if (lda) *lda = sys->lda;
+    if (nnz) *nnz = sys->nnz;
+    return CT_OK;
+}
+
+ct_status ct_system_device_ptrs(ct_system sys, void **dense, const int64_t **row_ptr,
+                                const int32_t **col_idx, const double **val) {
+    if (!sys) return CT_ERR_ARG;
+    if (dense) *dense = sys->dense;
+    if (row_ptr) *row_ptr = sys->row_ptr;
+    if (col_idx) *col_idx = sys->col;
+    if (val) *val = sys->val;
+    return CT_OK;
+}
+
+ct_status ct_system_export(ct_system sys, int64_t *row_ptr, int32_t *col_idx, double *val,
+                           void *dense, int64_t ldd) {
+    if (!sys) return CT_ERR_ARG;
+    if (dense && !sys->dense) return CT_ERR_STATE;
+    if (dense && ldd < sys->rows) return CT_ERR_ARG;
+    if (row_ptr) CT_CUDA(cudaMemcpy(row_ptr, sys->row_ptr, sizeof(int64_t) * (sys->m + 1), cudaMemcpyDeviceToHost));
+    if (col_idx && sys->nnz) CT_CUDA(cudaMemcpy(col_idx, sys->col, sizeof(int32_t) * sys->nnz, cudaMemcpyDeviceToHost));
+    if (val && sys->nnz) CT_CUDA(cudaMemcpy(val, sys->val, sizeof(double) * sys->nnz, cudaMemcpyDeviceToHost));
+    if (dense) {
+        const size_t es = sys->fp64 ? 8 : 4;
+        CT_CUDA(cudaMemcpy2D(dense, es * ldd, sys->dense, es * sys->lda, es * sys->rows, sys->n,
+                             cudaMemcpyDeviceToHost));
+    }
+    return CT_OK;
+}
+
+ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau) {
+    if (!f) return CT_ERR_ARG;
+    const size_t es = f->es();
+    if (VR) {
+        if (ldv < f->M) return CT_ERR_ARG;
+        CT_CUDA(cudaMemcpy2D(VR, es * ldv, f->VR, es * f->lda, es * f->M, f->n, cudaMemcpyDeviceToHost));
+    }
+    if (tau) CT_CUDA(cudaMemcpy(tau, f->tau, es * f->n, cudaMemcpyDeviceToHost));
+    return CT_OK;
+}
+
+ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx, int32_t k, double *P,
+                             int64_t ldp, void *stream) {
+    if (!sys || !X || !P || k < 0 || ldx < sys->n || ldp < sys->m) return CT_ERR_ARG;
+    if (k == 0) return CT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // column-major in, column-major out: go through slice-fastest staging.
+    double *xr = nullptr, *pr = nullptr;
+    CT_CUDA(cudaMallocAsync((void **)&xr, sizeof(double) * sys->n * k, s));
+    CT_CUDA(cudaMallocAsync((void **)&pr, sizeof(double) * sys->m * k, s));
+    ct_status st = transpose_d(X, ldx, xr, k, sys->n, k, s);  // (n x k, ld ldx) -> row-major
+    SparseSys S = sys->sparse();
+    S.sqrt_lambda = 0.0;
+    if (st == CT_OK) st = spmm_ax(S, k, xr, 0.0, nullptr, 1.0, pr, s);
+    if (st == CT_OK) st = transpose_d(pr, k, P, ldp, k, sys->m, s);  // row-major (m x k) -> col-major
+    cudaFreeAsync(xr, s);
+    cudaFreeAsync(pr, s);
+    if (st != CT_OK) return st;
+    return check_device_status(s);
+}
+
+ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_factor *out) {
+    if (!sys || !out) return CT_ERR_ARG;
+    *out = nullptr;
+    if (!sys->dense) {
+        set_error("system matrix already consumed by a factorisation");
+        return CT_ERR_STATE;
+    }
+    ct_opts o{};
+    o.precision = sys->fp64 ? CT_FP64 : CT_TF32_REFINE;
+    if (opts) o = *opts;
+    if (o.precision < CT_FP64 || o.precision > CT_BF16_REFINE) return CT_ERR_ARG;
+    if ((o.precision == CT_FP64) != sys->fp64) {
+        set_error("precision does not match the system's storage");
+        return CT_ERR_ARG;
+    }
+    if (o.precision == CT_BF16_REFINE) {
+        set_error("BF16 factorisation is not available in this build");
+        return CT_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    ct_factor f = new (std::nothrow) ct_factor_s;
+    if (!f) return CT_ERR_HOSTMEM;
+    f->sys = sys;
+    f->prec = o.precision;
+    f->fp64 = o.precision == CT_FP64;
+    f->kind = o.precision == CT_FP64 ? GEMM_F64 : (o.precision == CT_FP32 ? GEMM_F32 : GEMM_TF32);
+    f->M = sys->rows;
+    f->n = sys->n;
+    f->m = sys->m;
+    f->lda = sys->lda;
+    int nb = o.nb_inner > 0 ? o.nb_inner : (f->fp64 ? 16 : 32);
+    nb = std::min(nb, 32);
+    int NB = o.nb_outer > 0 ? o.nb_outer : (f->fp64 ? 32 : (f->kind == GEMM_F32 ? 128 : 256));
+    NB = (int)round_up(std::max(NB, nb), nb);
+    if (NB % 32) NB = (int)round_up(NB, 32);
+    f->nb = nb;
+    f->NB = NB;
+    f->nblocks = ceil_div(f->n, NB);
+    const size_t es = f->es();
+    auto fail = [&](ct_status st) {
+        // the dense storage stays consumed only on success
+        if (f->VR && !sys->dense) sys->dense = f->VR;
+        cudaFree(f->tau);
+        cudaFree(f->Tall);
+        cudaFree(f->Vtop);
+        delete f;
+        return st;
+    };
+    if (cudaMalloc(&f->tau, es * (size_t)f->n) != cudaSuccess) return fail(CT_ERR_OOM);
+    if (cudaMalloc(&f->Tall, es * (size_t)f->nblocks * NB * NB) != cudaSuccess) return fail(CT_ERR_OOM);
+    if (cudaMalloc(&f->Vtop, es * (size_t)f->nblocks * NB * NB) != cudaSuccess) return fail(CT_ERR_OOM);
+    f->VR = sys->dense;
+    sys->dense = nullptr;
+    ct_status st = qr_factor_run(f, s);
+    if (st != CT_OK) return fail(st);
+    double *dmm = nullptr;
+    if (cudaMallocAsync((void **)&dmm, 2 * sizeof(double), s) != cudaSuccess) return fail(CT_ERR_OOM);
+    st = rdiag_minmax(f->fp64, f->VR, f->lda, f->n, dmm, s);
+    double hmm[2] = {0, 0};
+    if (st == CT_OK && cudaMemcpyAsync(hmm, dmm, sizeof(hmm), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = CT_ERR_CUDA;
+    cudaFreeAsync(dmm, s);
+    if (st == CT_OK) st = check_device_status(s);
+    if (st != CT_OK) return fail(st);
+    f->rjj_min = hmm[0];
+    f->rjj_max = hmm[1];
+    const double u = f->fp64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
+    if (!(f->rjj_min >= (double)f->n * u * f->rjj_max)) {
+        set_error("rank deficient: min|R_jj| = %g, max|R_jj| = %g", f->rjj_min, f->rjj_max);
+        // keep the factor: the caller may still inspect it
+        *out = f;
+        return CT_ERR_RANK;
+    }
+    *out = f;
+    return CT_OK;
+}
+
+ct_status ct_factor_device_ptrs(ct_factor f, void **VR, int64_t *lda, void **tau) {
+    if (!f) return CT_ERR_ARG;
+    if (VR) *VR = f->VR;
+    if (lda) *lda = f->lda;
+    if (tau) *tau = f->tau;
+    return CT_OK;
+}
+
+ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
+                   const ct_opts *opts, void *stream, ct_solve_info *info) {
+    if (!f || k < 0 || ldb < f->m || ldx < f->n) return CT_ERR_ARG;
+    if (k == 0) return CT_OK;
+    if (!B || !X) return CT_ERR_ARG;
+    if (is_refine(f->prec) && !f->sys) return CT_ERR_STATE;
+    return solve_run(f, B, ldb, k, X, ldx, opts, (cudaStream_t)stream, info);
+}
+
+ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
+                        const ct_opts *opts, void *stream, ct_solve_info *info) {
+    if (!f || k < 0 || ldb < f->m || ldx < f->n) return CT_ERR_ARG;
+    if (k == 0) return CT_OK;
+    if (!B || !X) return CT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ies = f->prec == CT_FP32 ? 4 : 8;
+    const size_t bbytes = ies * (size_t)f->m * k, xbytes = ies * (size_t)f->n * k;
+    CT_TRY(f->host_pinned.ensure(bbytes + xbytes + 256));
+    void *dB = f->host_pinned.ptr;
+    void *dX = (char *)f->host_pinned.ptr + ((bbytes + 255) & ~(size_t)255);
+    CT_CUDA(cudaMemcpy2DAsync(dB, ies * f->m, B, ies * ldb, ies * f->m, k, cudaMemcpyHostToDevice, s));
+    ct_status st = solve_run(f, dB, f->m, k, dX, f->n, opts, s, info);
+    if (st != CT_OK && st != CT_ERR_NOCONV) return st;
+    CT_CUDA(cudaMemcpy2DAsync(X, ies * ldx, dX, ies * f->n, ies * f->n, k, cudaMemcpyDeviceToHost, s));
+    CT_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
+                           int64_t ldgb, const ct_opts *opts, void *stream, ct_solve_info *info) {
+    if (!f || k < 0 || ldgx < f->n || ldgb < f->m) return CT_ERR_ARG;
+    if (k == 0) return CT_OK;
+    if (!gX || !gB) return CT_ERR_ARG;
+    return adjoint_run(f, gX, ldgx, k, gB, ldgb, opts, (cudaStream_t)stream, info);
+}
+
+void ct_system_free(ct_system sys) {
+    if (!sys) return;
+    free_system_storage(sys);
+    delete sys;
+}
+
+void ct_factor_free(ct_factor f) {
+    if (!f) return;
+    cudaFree(f->VR);
+    cudaFree(f->tau);
+    cudaFree(f->Tall);
+    cudaFree(f->Vtop);
+    delete f;
+}
+
+ct_status ct_gemm(int32_t kind, char transa, char transb, int64_t M, int64_t N, int64_t K,
+                  double alpha, const void *A, int64_t lda, const void *B, int64_t ldb, double beta,
+                  void *C, int64_t ldc, void *stream) {
+    if (kind < 0 || kind > 3) return CT_ERR_ARG;
+    const bool ta = transa == 'T' || transa == 't';
+    const bool tb = transb == 'T' || transb == 't';
+    if ((!ta && transa != 'N' && transa != 'n') || (!tb && transb != 'N' && transb != 'n'))
+        return CT_ERR_ARG;
+    if (M < 0 || N < 0 || K < 0) return CT_ERR_ARG;
+    if (ldc < std::max<int64_t>(1, M)) return CT_ERR_ARG;
+    if (lda < std::max<int64_t>(1, ta ? K : M) || ldb < std::max<int64_t>(1, tb ? N : K))
+        return CT_ERR_ARG;
+    static Scratch ws;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    GemmArgs g{(GemmKind)kind, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc};
+    cudaStream_t s = (cudaStream_t)stream;
+    CT_TRY(gemm(g, ws, s));
+    return check_device_status(s);
+}
+
+}  // extern "C"

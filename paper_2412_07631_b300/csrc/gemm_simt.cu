@@ -1,0 +1,215 @@
+// gemm_simt.cu -- CUDA-core GEMM for the FP64 and FP32 paths, and the
+// split-K reduction shared with the tensor-core engine.
+//
+// C = alpha * op(A) * op(B) + beta * C, column-major.  Block tile BM x BN,
+// 256 threads, each owning a TM x TN register tile; op(A)/op(B) tiles staged
+// in shared memory with the M (resp. N) index fastest so the inner product
+// loop reads contiguous vectors.  FP64 on B300 runs at roughly 1/64 of the
+// FP32 rate, so the FP64 instance is bound by the DFMA pipe, not by memory.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace ctqr {
+
+namespace {
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(bool ta, bool tb, int64_t M, int64_t N,
+                                                        int64_t K, int64_t kchunk, T alpha,
+                                                        const T *__restrict__ A, int64_t lda,
+                                                        const T *__restrict__ B, int64_t ldb,
+                                                        T beta, T *C, int64_t ldc,
+                                                        int64_t split_stride) {
+    static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    const int64_t kb = (int64_t)blockIdx.z * kchunk;
+    const int64_t ke = min(K, kb + kchunk);
+    C += (int64_t)blockIdx.z * split_stride;
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+        // op(A) tile: element (i, kk) = A(m0+i, k0+kk) or A(k0+kk, m0+i).
+        for (int idx = tid; idx < BM * BK; idx += 256) {
+            int i, kk;
+            if (!ta) { i = idx % BM; kk = idx / BM; }
+            else { kk = idx % BK; i = idx / BK; }
+            int64_t gm = m0 + i, gk = k0 + kk;
+            T v = T(0);
+            if (gm < M && gk < ke) v = ta ? A[gk + gm * lda] : A[gm + gk * lda];
+            As[kk][i] = v;
+        }
+        // op(B) tile: element (kk, j) = B(k0+kk, n0+j) or B(n0+j, k0+kk).
+        for (int idx = tid; idx < BN * BK; idx += 256) {
+            int j, kk;
+            if (!tb) { kk = idx % BK; j = idx / BK; }
+            else { j = idx % BN; kk = idx / BN; }
+            int64_t gn = n0 + j, gk = k0 + kk;
+            T v = T(0);
+            if (gn < N && gk < ke) v = tb ? B[gn + gk * ldb] : B[gk + gn * ldb];
+            Bs[kk][j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        int64_t gn = n0 + tx * TN + j;
+        if (gn >= N) continue;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            int64_t gm = m0 + ty * TM + i;
+            if (gm >= M) continue;
+            T *c = C + gm + gn * ldc;
+            T v = alpha * acc[i][j];
+            if (beta != T(0)) v += beta * *c;
+            *c = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const T *P, T alpha, T beta,
+                                     T *C, int64_t ldc) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * N) return;
+    int64_t i = idx % M, j = idx / M;
+    T acc = T(0);
+    for (int z = 0; z < splits; ++z) acc += P[(int64_t)z * M * N + idx];
+    T *c = C + i + j * ldc;
+    T v = alpha * acc;
+    if (beta != T(0)) v += beta * *c;
+    *c = v;
+}
+
+}  // namespace
+
+ct_status gemm_simt_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
+                           cudaStream_t s) {
+    if (g.kind == GEMM_F64) {
+        constexpr int BM = 64, BN = 64;
+        dim3 grid((unsigned)ceil_div(g.M, BM), (unsigned)ceil_div(g.N, BN), (unsigned)splits);
+        gemm_simt_kernel<double, BM, BN, 16, 4, 4><<<grid, 256, 0, s>>>(
+            g.ta, g.tb, g.M, g.N, g.K, kchunk, g.alpha, (const double *)g.A, g.lda,
+            (const double *)g.B, g.ldb, g.beta, (double *)g.C, g.ldc, split_stride);
+    } else {
+        constexpr int BM = 128, BN = 128;
+        dim3 grid((unsigned)ceil_div(g.M, BM), (unsigned)ceil_div(g.N, BN), (unsigned)splits);
+        gemm_simt_kernel<float, BM, BN, 8, 8, 8><<<grid, 256, 0, s>>>(
+            g.ta, g.tb, g.M, g.N, g.K, kchunk, (float)g.alpha, (const float *)g.A, g.lda,
+            (const float *)g.B, g.ldb, (float)g.beta, (float *)g.C, g.ldc, split_stride);
+    }
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void *P, double alpha,
+                        double beta, void *C, int64_t ldc, cudaStream_t s) {
+    const int64_t total = M * N;
+    if (total == 0) return CT_OK;
+    const unsigned blocks = (unsigned)ceil_div(total, 256);
+    if (fp64)
+        splitk_reduce_kernel<double><<<blocks, 256, 0, s>>>(M, N, splits, (const double *)P, alpha,
+                                                            beta, (double *)C, ldc);
+    else
+        splitk_reduce_kernel<float><<<blocks, 256, 0, s>>>(M, N, splits, (const float *)P,
+                                                           (float)alpha, (float)beta, (float *)C,
+                                                           ldc);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+// Split-K policy: enough CTAs to cover the machine about twice, each split
+// at least kMinChunk deep.
+ct_status gemm(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
+    if (g.M < 0 || g.N < 0 || g.K < 0) return CT_ERR_ARG;
+    if (g.M == 0 || g.N == 0) return CT_OK;
+    const bool fp64 = g.kind == GEMM_F64;
+    bool tc = g.kind == GEMM_TF32 || g.kind == GEMM_BF16;
+    if (tc && (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15) || (g.lda & 3) || (g.ldb & 3))) {
+        // A TMA tile must start on a 16-byte boundary; ragged sub-blocks that
+        // do not (only at the edges of odd-sized problems) use the FP32 SIMT path.
+        GemmArgs h = g;
+        h.kind = GEMM_F32;
+        return gemm(h, ws, s);
+    }
+    if (tc && (!g.ta || g.tb) && g.K > 0) {
+        // The tensor cores take TF32 operands K-major only (each output row's K
+        // values contiguous; the MN-major form is not available for 32-bit
+        // operands).  An operand stored the other way round is transposed
+        // into a K-major copy first.
+        static Scratch tws;
+        GemmArgs h = g;
+        const int64_t ldta = round_up(g.K, 32);
+        const size_t abytes = !g.ta ? sizeof(float) * (size_t)ldta * g.M : 0;
+        const size_t bbytes = g.tb ? sizeof(float) * (size_t)ldta * g.N : 0;
+        CT_TRY(tws.ensure(abytes + bbytes + 256));
+        if (!g.ta) {
+            CT_TRY(transpose_any(0, g.A, g.lda, 0, tws.ptr, ldta, g.M, g.K, s));  // A (M x K) -> K x M
+            h.A = tws.ptr;
+            h.lda = ldta;
+            h.ta = true;
+        }
+        if (g.tb) {
+            void *bt = (char *)tws.ptr + round_up((int64_t)abytes, 256);
+            CT_TRY(transpose_any(0, g.B, g.ldb, 0, bt, ldta, g.N, g.K, s));  // B (N x K) -> K x N
+            h.B = bt;
+            h.ldb = ldta;
+            h.tb = false;
+        }
+        return gemm(h, ws, s);
+    }
+    if (g.K == 0) {
+        // C = beta * C
+        if (g.beta == 1.0) return CT_OK;
+        return splitk_reduce(fp64, g.M, g.N, 0, nullptr, 0.0, g.beta, g.C, g.ldc, s);
+    }
+    const int64_t BM = tc ? 128 : (fp64 ? 64 : 128);
+    const int64_t BN = tc ? 256 : (fp64 ? 64 : 128);
+    const int64_t tiles = ceil_div(g.M, BM) * ceil_div(g.N, BN);
+    const int64_t target = 2 * (int64_t)num_sms();
+    const int64_t kMinChunk = tc ? 1024 : 512;
+    int64_t splits = 1;
+    if (tiles < target) splits = std::min(ceil_div(target, tiles), std::max<int64_t>(1, g.K / kMinChunk));
+    splits = std::min<int64_t>(splits, 64);
+    if (splits <= 1) {
+        return tc ? gemm_tc_launch(g, 1, g.K, 0, s) : gemm_simt_launch(g, 1, g.K, 0, s);
+    }
+    const int64_t align = tc ? 32 : 16;
+    int64_t kchunk = round_up(ceil_div(g.K, splits), align);
+    splits = ceil_div(g.K, kchunk);
+    const size_t esz = fp64 ? 8 : 4;
+    CT_TRY(ws.ensure(esz * (size_t)(g.M * g.N * splits)));
+    GemmArgs p = g;
+    p.alpha = 1.0;
+    p.beta = 0.0;
+    p.C = ws.ptr;
+    p.ldc = g.M;
+    CT_TRY(tc ? gemm_tc_launch(p, (int)splits, kchunk, g.M * g.N, s)
+              : gemm_simt_launch(p, (int)splits, kchunk, g.M * g.N, s));
+    return splitk_reduce(fp64, g.M, g.N, (int)splits, ws.ptr, g.alpha, g.beta, g.C, g.ldc, s);
+}
+
+}  // namespace ctqr

@@ -1,0 +1,113 @@
+// kernels.cuh -- internal entry points between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace ctqr {
+
+// ---- system build (siddon.cu) ---------------------------------------------------
+struct SiddonArgs {
+    int n_side, n_views, n_bins;
+    double pixel_width, bin_width, sqrt_lambda;
+    const double *d_cs;  // [2*n_views] (cos, sin) per view
+    int32_t *d_row_nnz;  // [m]
+    int64_t *d_row_ptr;  // [m+1]
+    int32_t *d_col;      // [nnz]
+    double *d_val;       // [nnz]
+    Scratch *tmp;
+};
+ct_status siddon_build(const SiddonArgs &a, cudaStream_t s);  // counts + row_ptr
+ct_status siddon_fill(const SiddonArgs &a, void *dense, bool dense_fp64, int64_t lda,
+                      cudaStream_t s);
+ct_status exclusive_scan(const int32_t *in, int64_t n, int64_t *out_np1, Scratch &tmp,
+                         cudaStream_t s);
+ct_status build_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                    const int32_t *col_idx, const double *val, int64_t *col_ptr, int32_t *csc_row,
+                    double *csc_val, Scratch &tmp, Scratch &tmp2, cudaStream_t s);
+
+// ---- GEMM engines (gemm_simt.cu, gemm_tc.cu) ---------------------------------------
+enum GemmKind : int { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TF32 = 2, GEMM_BF16 = 3 };
+
+struct GemmArgs {
+    GemmKind kind;
+    bool ta, tb;  // op(A) = A^T, op(B) = B^T
+    int64_t M, N, K;
+    double alpha;
+    const void *A;
+    int64_t lda;
+    const void *B;
+    int64_t ldb;
+    double beta;
+    void *C;
+    int64_t ldc;
+};
+// C = alpha op(A) op(B) + beta C (column-major).  Chooses split-K when the
+// output has too few tiles for the machine; partial sums go through `ws`
+// and are reduced in a fixed order (deterministic).
+ct_status gemm(const GemmArgs &g, Scratch &ws, cudaStream_t s);
+
+// Kernel-level launchers (no split logic): partial products over K range
+// [k0, k0 + kc) of split z written to C + z*split_stride (alpha/beta applied).
+ct_status gemm_simt_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
+                           cudaStream_t s);
+ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
+                         cudaStream_t s);
+// C = alpha * sum_z P[z] + beta * C  (P: splits x (M x N) packed, ld = M)
+ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void *P, double alpha,
+                        double beta, void *C, int64_t ldc, cudaStream_t s);
+
+// ---- factorisation pieces (panel.cu) -------------------------------------------------
+// Householder QR of the panel A[j0:M, j0:j0+nb] in place (LAPACK convention),
+// tau[j0:j0+nb].  Cooperative kernel, one bounded grid barrier per column.
+ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int nb, void *tau,
+                   Scratch &ws, cudaStream_t s);
+// Copy the unit-lower-triangular top block of V (nb x nb at A[j0, j0]) into
+// Vtop (leading dimension ldv): ones on the diagonal, zeros above.
+ct_status extract_vtop(bool fp64, const void *A, int64_t lda, int64_t j0, int nb, void *Vtop,
+                       int64_t ldv, cudaStream_t s);
+// T (nb x nb, upper triangular, leading dimension ldt) of the block reflector
+// H = I - V T V^T from the Gram matrix G = V^T V (leading dimension ldg) and tau.
+ct_status larft_from_gram(bool fp64, int nb, const void *G, int64_t ldg, const void *tau, void *T,
+                          int64_t ldt, cudaStream_t s);
+
+// ---- triangular solves (trsm.cu) ---------------------------------------------------------
+// Solve R X = C (upper, n x n, ld ldr) for k columns in place in C (ld ldc)
+// (trans = false), or R^T X = C (trans = true).  Blocked: diagonal blocks by a
+// SIMT kernel, off-diagonal updates by `gemm` of the given kind.
+ct_status trsm_upper(GemmKind kind, bool trans, int64_t n, int64_t k, const void *R, int64_t ldr,
+                     void *C, int64_t ldc, Scratch &ws, cudaStream_t s);
+
+// ---- elementwise / layout helpers (util.cu) -----------------------------------------------
+ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
+                          int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s);
+// 0 = float, 1 = double for src/dst kinds above.
+// dst (cols x rows, ld ldd) = transpose of src (rows x cols, ld lds), with conversion.
+ct_status transpose_any(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
+                        int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s);
+ct_status transpose_d(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t rows,
+                      int64_t cols, cudaStream_t s);
+ct_status fill_zero_2d(bool fp64, void *dst, int64_t ld, int64_t rows, int64_t cols,
+                       cudaStream_t s);
+ct_status rdiag_minmax(bool fp64, const void *A, int64_t lda, int64_t n, double *dmin_dmax_dev,
+                       cudaStream_t s);
+
+// ---- FP64 sparse products and refinement helpers (spmm.cu) -------------------------------
+struct SparseSys {
+    int64_t m, n, nnz;
+    double sqrt_lambda;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+    const int64_t *col_ptr;
+    const int32_t *csc_row;
+    const double *csc_val;
+};
+// Row-major (slice-fastest) k-column operands:  Y[i*k + s].
+// out = alpha*Y + beta*(A~ X)   (rows m+n if sqrt_lambda > 0, else m)
+ct_status spmm_ax(const SparseSys &S, int64_t k, const double *X, double alpha, const double *Y,
+                  double beta, double *out, cudaStream_t s);
+// out = alpha*Y + beta*(A~^T Rv)  (n rows)
+ct_status spmm_atr(const SparseSys &S, int64_t k, const double *Rv, double alpha, const double *Y,
+                   double beta, double *out, cudaStream_t s);
+
+}  // namespace ctqr

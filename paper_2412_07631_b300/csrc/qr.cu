@@ -1,0 +1,139 @@
+// qr.cu -- blocked Householder QR driver (Sec. 2 Eq. 2; 'dgeqrf' of Sec. 2.1)
+// and the block-reflector application used by the solve (Eq. 3, 'dormqr').
+//
+// Two-level right-looking blocking.  Outer blocks of NB columns; inside a
+// block, panels of nb columns are factored by the cooperative panel kernel
+// and applied to the rest of the block with their own compact-WY factors.
+// When a block is finished its T_J (larft from the Gram matrix V_J^T V_J) and
+// the unit-lower top of V_J are kept, and the trailing matrix is updated
+//      C <- (I - V_J T_J V_J^T)^T C = C - V_J (T_J^T (V_J^T C))
+// with three GEMMs (two of them large, on the precision's GEMM engine).
+// V_J lives in place below the diagonal of A; only its NB x NB top triangle
+// (ones on the diagonal, R above it in A) is copied out, so the GEMMs split
+// V_J into that small top block and the in-place rows below it.
+#include <algorithm>
+
+#include "handles.cuh"
+
+namespace ctqr {
+
+namespace {
+
+inline char *at(void *base, int64_t i, int64_t j, int64_t ld, size_t es) {
+    return (char *)base + es * (size_t)(i + j * ld);
+}
+
+GemmArgs mk(ct_factor f, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+            const void *A, int64_t lda, const void *B, int64_t ldb, double beta, void *C,
+            int64_t ldc) {
+    GemmArgs g;
+    g.kind = f->kind;
+    g.ta = ta;
+    g.tb = tb;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.alpha = alpha;
+    g.A = A;
+    g.lda = lda;
+    g.B = B;
+    g.ldb = ldb;
+    g.beta = beta;
+    g.C = C;
+    g.ldc = ldc;
+    return g;
+}
+
+// G (w x w, ld NB) = V^T V for the reflector block starting at column j.
+ct_status gram(ct_factor f, int64_t j, int w, const void *Vt, void *G, cudaStream_t s) {
+    const int64_t NB = f->NB;
+    CT_TRY(gemm(mk(f, true, false, w, w, w, 1.0, Vt, NB, Vt, NB, 0.0, G, NB), f->gemm_ws, s));
+    const int64_t kb = f->M - j - w;
+    if (kb > 0) {
+        const void *Vb = at(f->VR, j + w, j, f->lda, f->es());
+        CT_TRY(gemm(mk(f, true, false, w, w, kb, 1.0, Vb, f->lda, Vb, f->lda, 1.0, G, NB),
+                    f->gemm_ws, s));
+    }
+    return CT_OK;
+}
+
+// C[j:M, 0:ncols] <- (I - V op(T) V^T) C, op(T) = T^T for Q^T, T for Q.
+// C points at row j of the target; V is the block at column j of width w.
+ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void *T, bool qt,
+                      void *C, int64_t ldc, int64_t ncols, cudaStream_t s) {
+    if (ncols <= 0) return CT_OK;
+    const int64_t NB = f->NB;
+    const size_t es = f->es();
+    CT_TRY(f->W.ensure(es * (size_t)NB * ncols));
+    CT_TRY(f->W2.ensure(es * (size_t)NB * ncols));
+    void *W = f->W.ptr, *W2 = f->W2.ptr;
+    const int64_t kb = f->M - j - w;
+    const void *Vb = at(f->VR, j + w, j, f->lda, es);
+    void *Cb = (char *)C + es * (size_t)w;
+    // W = V^T C
+    CT_TRY(gemm(mk(f, true, false, w, ncols, w, 1.0, Vt, NB, C, ldc, 0.0, W, NB), f->gemm_ws, s));
+    if (kb > 0)
+        CT_TRY(gemm(mk(f, true, false, w, ncols, kb, 1.0, Vb, f->lda, Cb, ldc, 1.0, W, NB),
+                    f->gemm_ws, s));
+    // W2 = op(T) W
+    CT_TRY(gemm(mk(f, qt, false, w, ncols, w, 1.0, T, NB, W, NB, 0.0, W2, NB), f->gemm_ws, s));
+    // C -= V W2
+    CT_TRY(gemm(mk(f, false, false, w, ncols, w, -1.0, Vt, NB, W2, NB, 1.0, C, ldc), f->gemm_ws, s));
+    if (kb > 0)
+        CT_TRY(gemm(mk(f, false, false, kb, ncols, w, -1.0, Vb, f->lda, W2, NB, 1.0, Cb, ldc),
+                    f->gemm_ws, s));
+    return CT_OK;
+}
+
+}  // namespace
+
+ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
+    const size_t es = f->es();
+    const int64_t NB = f->NB, nb = f->nb, n = f->n, M = f->M, lda = f->lda;
+    CT_TRY(f->G.ensure(es * (size_t)NB * NB));
+    // misc: Vt_p | T_p for inner panels (ld NB)
+    CT_TRY(f->misc.ensure(2 * es * (size_t)NB * NB));
+    void *Vtp = f->misc.ptr;
+    void *Tp = (char *)f->misc.ptr + es * (size_t)NB * NB;
+    for (int64_t J = 0; J < f->nblocks; ++J) {
+        const int64_t j = J * NB;
+        const int w = (int)std::min<int64_t>(NB, n - j);
+        for (int64_t p = j; p < j + w; p += nb) {
+            const int wp = (int)std::min<int64_t>(nb, j + w - p);
+            CT_TRY(panel_qr(f->fp64, f->VR, lda, M, p, wp, f->tau, f->panel_ws, s));
+            const int64_t ncols_in = j + w - (p + wp);
+            if (ncols_in > 0) {
+                CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
+                CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
+                CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
+                CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,
+                                   ncols_in, s));
+            }
+        }
+        void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
+        void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
+        CT_TRY(extract_vtop(f->fp64, f->VR, lda, j, w, VtJ, NB, s));
+        CT_TRY(gram(f, j, w, VtJ, f->G.ptr, s));
+        CT_TRY(larft_from_gram(f->fp64, w, f->G.ptr, NB, (char *)f->tau + es * j, TJ, NB, s));
+        if (j + w < n)
+            CT_TRY(apply_block(f, j, w, VtJ, TJ, true, at(f->VR, j, j + w, lda, es), lda, n - j - w, s));
+    }
+    return CT_OK;
+}
+
+ct_status apply_q_blocks(ct_factor f, bool transpose, void *C, int64_t ldc, int64_t k,
+                         cudaStream_t s) {
+    const size_t es = f->es();
+    const int64_t NB = f->NB;
+    for (int64_t t = 0; t < f->nblocks; ++t) {
+        const int64_t J = transpose ? t : f->nblocks - 1 - t;
+        const int64_t j = J * NB;
+        const int w = (int)std::min<int64_t>(NB, f->n - j);
+        const void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
+        const void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
+        CT_TRY(apply_block(f, j, w, VtJ, TJ, transpose, (char *)C + es * (size_t)j, ldc, k, s));
+    }
+    return CT_OK;
+}
+
+}  // namespace ctqr

@@ -1,0 +1,207 @@
+// refine.cu -- FP64 iterative refinement on top of the low-precision factors.
+//
+// The direct solve x0 = R~^-1 [Q~^T b~]_{0:n} with TF32/BF16 factors carries
+// an error of order kappa(A~) * u_low, and for the regularised, noisy
+// problems kappa(A~) * u_low can exceed 1, where classical refinement
+// (x += R~^-1 Q~^T (b~ - A~ x)) has the wrong fixed point or diverges.  The
+// refinement here is Krylov-based: CGLS on the right-preconditioned problem
+//     min_y || A~ R~^-1 y - r0 ||,   r0 = b~ - A~ x0,   x = x0 + R~^-1 y,
+// whose convergence depends on kappa(A~ R~^-1) (close to 1 when R~ is a good
+// factor) rather than on kappa(A~).  The iterate x, the residual r, the
+// search directions and every inner product are FP64; the residual and the
+// back-projection use the exact sparse FP64 Siddon matrix (never the
+// low-precision dense copy); only the two triangular solves with R~ per step
+// run in the factor's precision.  Each slice has its own step lengths.
+//
+// Per step:  t = R~^-1 p,  q = A~ t,  alpha = gamma / ||q||^2,
+//            x += alpha t,  r -= alpha q,  s = R~^-T (A~^T r),
+//            gamma' = ||s||^2,  p = s + (gamma'/gamma) p.
+// Stop when max over slices of ||alpha t|| / ||x|| <= tol, or after
+// max_iter steps (CT_ERR_NOCONV, x holds the last iterate).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace ctqr {
+
+namespace {
+
+constexpr int RB = 256;  // rows per reduction block
+
+// part[b*k + s] = sum over rows [b*RB, (b+1)*RB) of U[i,s]*V[i,s] (row-major, slice fastest)
+__global__ void coldot_partial(int64_t rows, int64_t k, const double *U, const double *V,
+                               double *part) {
+    const int64_t r0 = (int64_t)blockIdx.x * RB;
+    const int64_t r1 = min(rows, r0 + RB);
+    for (int64_t s = threadIdx.x; s < k; s += blockDim.x) {
+        double acc = 0.0;
+        for (int64_t i = r0; i < r1; ++i) acc += U[i * k + s] * V[i * k + s];
+        part[(int64_t)blockIdx.x * k + s] = acc;
+    }
+}
+
+__global__ void coldot_final(int64_t nblk, int64_t k, const double *part, double *out) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k) return;
+    double acc = 0.0;
+    for (int64_t b = 0; b < nblk; ++b) acc += part[b * k + s];
+    out[s] = acc;
+}
+
+// Y[i,s] += a[s] * X[i,s]   (a per slice)
+__global__ void axpy_cols(int64_t rows, int64_t k, const double *a, double sign, const double *X,
+                          double *Y) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * k) return;
+    int64_t s = idx % k;
+    Y[idx] += sign * a[s] * X[idx];
+}
+
+// P[i,s] = S[i,s] + b[s] * P[i,s]
+__global__ void xpby_cols(int64_t rows, int64_t k, const double *S, const double *b, double *P) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * k) return;
+    int64_t s = idx % k;
+    P[idx] = S[idx] + b[s] * P[idx];
+}
+
+// alpha[s] = gamma[s] / qq[s] (0 if qq is 0);  upd[s] = alpha^2 * tt[s]
+__global__ void step_scalars(int64_t k, const double *gamma, const double *qq, double *alpha) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k) return;
+    alpha[s] = (qq[s] > 0.0) ? gamma[s] / qq[s] : 0.0;
+}
+
+__global__ void beta_scalars(int64_t k, const double *gnew, double *gamma, double *beta) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k) return;
+    beta[s] = (gamma[s] > 0.0) ? gnew[s] / gamma[s] : 0.0;
+    gamma[s] = gnew[s];
+}
+
+struct Ws {
+    double *x, *r, *p, *s, *t, *q, *btil;  // row-major FP64
+    double *part, *vec;                    // reductions
+    void *lp;                              // low-precision column-major n x k
+};
+
+}  // namespace
+
+// Per-slice inner products of row-major k-column blocks (deterministic order).
+static ct_status coldot(int64_t rows, int64_t k, const double *U, const double *V, double *part,
+                        double *out, cudaStream_t s) {
+    const int64_t nblk = ceil_div(rows, RB);
+    coldot_partial<<<(unsigned)nblk, 128, 0, s>>>(rows, k, U, V, part);
+    coldot_final<<<(unsigned)ceil_div(k, 128), 128, 0, s>>>(nblk, k, part, out);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+// t = R~^-1 u (trans = false) or R~^-T u (trans = true) for row-major FP64 u (n x k):
+// convert to the factor's column-major storage, triangular solve, convert back.
+static ct_status apply_rinv(ct_factor f, bool trans, const double *u, double *t, int64_t k,
+                            void *lp, cudaStream_t s) {
+    const int64_t n = f->n, ldl = round_up(n, 32);
+    const int dk = f->fp64 ? 1 : 0;
+    CT_TRY(transpose_any(1, u, k, dk, lp, ldl, k, n, s));  // (k x n row view) -> n x k col-major
+    CT_TRY(trsm_upper(f->kind, trans, n, k, f->VR, f->lda, lp, ldl, f->trsm_ws, s));
+    return transpose_any(dk, lp, ldl, 1, t, k, n, k, s);   // n x k col-major -> row-major
+}
+
+ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
+                     const ct_opts *o, cudaStream_t st, ct_solve_info *info) {
+    const ct_system sys = f->sys;
+    const SparseSys S = sys->sparse();
+    const int64_t n = f->n, m = f->m, M = f->M;
+    const int max_iter = (o && o->refine_max_iter > 0) ? o->refine_max_iter : 10;
+    const double tol = (o && o->refine_tol > 0) ? o->refine_tol : 1e-7;
+    if (o && o->refine_max_iter < 0) return check_device_status(st);  // refinement disabled
+
+    // workspace
+    const int64_t nblk = ceil_div(std::max(M, n), RB);
+    const size_t nk = (size_t)n * k, Mk = (size_t)M * k;
+    const size_t ldl = round_up(n, 32);
+    const size_t bytes = sizeof(double) * (3 * Mk + 4 * nk + (size_t)nblk * k + 8 * (size_t)k) +
+                         f->es() * ldl * k + 1024;
+    CT_TRY(f->refine_ws.ensure(bytes));
+    char *base = (char *)f->refine_ws.ptr;
+    auto take = [&](size_t b) { char *p = base; base += round_up((int64_t)b, 256); return p; };
+    Ws w;
+    w.r = (double *)take(sizeof(double) * Mk);
+    w.q = (double *)take(sizeof(double) * Mk);
+    w.btil = (double *)take(sizeof(double) * Mk);
+    w.x = (double *)take(sizeof(double) * nk);
+    w.p = (double *)take(sizeof(double) * nk);
+    w.s = (double *)take(sizeof(double) * nk);
+    w.t = (double *)take(sizeof(double) * nk);
+    w.part = (double *)take(sizeof(double) * nblk * k);
+    w.vec = (double *)take(sizeof(double) * 8 * k);
+    w.lp = take(f->es() * ldl * k);
+    double *gamma = w.vec, *qq = w.vec + k, *alpha = w.vec + 2 * k, *beta = w.vec + 3 * k,
+           *gnew = w.vec + 4 * k, *tt = w.vec + 5 * k, *xx = w.vec + 6 * k;
+    const unsigned bn = (unsigned)ceil_div((int64_t)nk, 256), bk = (unsigned)ceil_div(k, 128);
+
+    // b~ (row-major, zero sqrt(lambda) rows), x0 (row-major)
+    CT_CUDA(cudaMemsetAsync(w.btil, 0, sizeof(double) * Mk, st));
+    CT_TRY(transpose_any(1, B, ldb, 1, w.btil, k, m, k, st));
+    CT_TRY(transpose_any(1, X, ldx, 1, w.x, k, n, k, st));
+    // r = b~ - A~ x0 ; s = R^-T A~^T r ; p = s ; gamma = ||s||^2
+    CT_TRY(spmm_ax(S, k, w.x, 1.0, w.btil, -1.0, w.r, st));
+    CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));
+    CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));
+    CT_CUDA(cudaMemcpyAsync(w.p, w.s, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
+    CT_TRY(coldot(n, k, w.s, w.s, w.part, gamma, st));
+
+    std::vector<double> h_tt(k), h_xx(k), h_alpha(k);
+    int it = 0;
+    double last = INFINITY;
+    bool converged = false;
+    while (it < max_iter) {
+        ++it;
+        CT_TRY(apply_rinv(f, false, w.p, w.t, k, w.lp, st));       // t = R^-1 p
+        CT_TRY(spmm_ax(S, k, w.t, 0.0, nullptr, 1.0, w.q, st));    // q = A~ t
+        CT_TRY(coldot(M, k, w.q, w.q, w.part, qq, st));
+        step_scalars<<<bk, 128, 0, st>>>(k, gamma, qq, alpha);
+        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, 1.0, w.t, w.x);                       // x += a t
+        axpy_cols<<<(unsigned)ceil_div((int64_t)Mk, 256), 256, 0, st>>>(M, k, alpha, -1.0, w.q, w.r);  // r -= a q
+        CT_TRY(coldot(n, k, w.t, w.t, w.part, tt, st));
+        CT_TRY(coldot(n, k, w.x, w.x, w.part, xx, st));
+        CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));   // t = A~^T r (reuse)
+        CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));        // s = R^-T t
+        CT_TRY(coldot(n, k, w.s, w.s, w.part, gnew, st));
+        beta_scalars<<<bk, 128, 0, st>>>(k, gnew, gamma, beta);
+        xpby_cols<<<bn, 256, 0, st>>>(n, k, w.s, beta, w.p);
+        CT_CUDA(cudaGetLastError());
+        CT_CUDA(cudaMemcpyAsync(h_tt.data(), tt, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaMemcpyAsync(h_xx.data(), xx, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaStreamSynchronize(st));
+        double worst = 0.0;
+        for (int32_t q = 0; q < k; ++q) {
+            const double xn = std::sqrt(h_xx[q]);
+            const double up = std::fabs(h_alpha[q]) * std::sqrt(h_tt[q]);
+            if (!std::isfinite(up)) { worst = INFINITY; break; }
+            worst = std::max(worst, xn > 0 ? up / xn : up);
+        }
+        last = worst;
+        if (worst <= tol) {
+            converged = true;
+            break;
+        }
+    }
+    CT_TRY(transpose_any(1, w.x, k, 1, X, ldx, k, n, st));  // row-major -> X (n x k col-major)
+    if (info) {
+        info->iterations = it;
+        info->last_rel_update = last;
+    }
+    CT_TRY(check_device_status(st));
+    if (!converged) {
+        set_error("refinement: %d steps, last relative update %.3g > tol %.3g", it, last, tol);
+        return CT_ERR_NOCONV;
+    }
+    return CT_OK;
+}
+
+}  // namespace ctqr

@@ -1,0 +1,119 @@
+// spmm.cu -- FP64 sparse products with the Siddon matrix for k images at
+// once: the forward projection A X, the regularised residual b~ - A~ X and the
+// back-projection A~^T R.  The refinement computes its residuals here, in
+// FP64, from the exact sparse A rather than from the low-precision dense copy.
+//
+// Operands are row-major with the slice index fastest (element (i, s) at
+// Y[i*k + s]) so that the k values a nonzero multiplies are one contiguous,
+// coalesced run.  One warp per matrix row; lanes stride over the slices.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ctqr {
+
+namespace {
+
+// out[i, :] = alpha*Y[i, :] + beta * sum_q val[q] * X[col[q], :]   (ray rows)
+// and for the sqrt(lambda) rows i = m + j:  (A~ X)[m+j, :] = sl * X[j, :].
+__global__ void spmm_ax_kernel(int64_t m, int64_t n, int64_t k, double sl, const int64_t *row_ptr,
+                               const int32_t *col, const double *val, const double *X, double alpha,
+                               const double *Y, double beta, double *out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t rows = m + (sl > 0.0 ? n : 0);
+    if (row >= rows) return;
+    for (int64_t s0 = 0; s0 < k; s0 += 32 * 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        if (row < m) {
+            for (int64_t q = row_ptr[row]; q < row_ptr[row + 1]; ++q) {
+                const double a = val[q];
+                const double *xr = X + (int64_t)col[q] * k;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t s = s0 + lane + 32 * u;
+                    if (s < k) acc[u] += a * xr[s];
+                }
+            }
+        } else {
+            const double *xr = X + (row - m) * k;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t s = s0 + lane + 32 * u;
+                if (s < k) acc[u] = sl * xr[s];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t s = s0 + lane + 32 * u;
+            if (s < k) {
+                double v = beta * acc[u];
+                if (alpha != 0.0) v += alpha * Y[row * k + s];
+                out[row * k + s] = v;
+            }
+        }
+    }
+}
+
+// out[j, :] = alpha*Y[j, :] + beta * (sum_{q in col j} csc_val[q] * R[csc_row[q], :]
+//                                     + sl * R[m + j, :])
+__global__ void spmm_atr_kernel(int64_t m, int64_t n, int64_t k, double sl, const int64_t *col_ptr,
+                                const int32_t *csc_row, const double *csc_val, const double *R,
+                                double alpha, const double *Y, double beta, double *out) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (j >= n) return;
+    for (int64_t s0 = 0; s0 < k; s0 += 32 * 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t q = col_ptr[j]; q < col_ptr[j + 1]; ++q) {
+            const double a = csc_val[q];
+            const double *rr = R + (int64_t)csc_row[q] * k;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t s = s0 + lane + 32 * u;
+                if (s < k) acc[u] += a * rr[s];
+            }
+        }
+        if (sl > 0.0) {
+            const double *rr = R + (m + j) * k;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t s = s0 + lane + 32 * u;
+                if (s < k) acc[u] += sl * rr[s];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t s = s0 + lane + 32 * u;
+            if (s < k) {
+                double v = beta * acc[u];
+                if (alpha != 0.0) v += alpha * Y[j * k + s];
+                out[j * k + s] = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+ct_status spmm_ax(const SparseSys &S, int64_t k, const double *X, double alpha, const double *Y,
+                  double beta, double *out, cudaStream_t s) {
+    const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
+    if (rows == 0 || k == 0) return CT_OK;
+    const unsigned blocks = (unsigned)ceil_div(rows * 32, 256);
+    spmm_ax_kernel<<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.row_ptr, S.col, S.val, X,
+                                          alpha, Y, beta, out);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status spmm_atr(const SparseSys &S, int64_t k, const double *R, double alpha, const double *Y,
+                   double beta, double *out, cudaStream_t s) {
+    if (S.n == 0 || k == 0) return CT_OK;
+    const unsigned blocks = (unsigned)ceil_div(S.n * 32, 256);
+    spmm_atr_kernel<<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.col_ptr, S.csc_row,
+                                           S.csc_val, R, alpha, Y, beta, out);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+}  // namespace ctqr

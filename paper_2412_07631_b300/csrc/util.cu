@@ -1,0 +1,132 @@
+// util.cu -- layout/precision copies and small reductions used around the
+// factorisation and the solve.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ctqr {
+
+namespace {
+
+template <typename S, typename D>
+__global__ void copy_convert_kernel(const S *src, int64_t lds, D *dst, int64_t ldd, int64_t rows,
+                                    int64_t cols) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    int64_t i = idx % rows, j = idx / rows;
+    dst[i + j * ldd] = (D)src[i + j * lds];
+}
+
+template <typename T>
+__global__ void fill_zero_kernel(T *dst, int64_t ld, int64_t rows, int64_t cols) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    int64_t i = idx % rows, j = idx / rows;
+    dst[i + j * ld] = T(0);
+}
+
+template <typename T>
+__global__ void rdiag_minmax_kernel(const T *A, int64_t lda, int64_t n, double *out,
+                                    DevStatus *st) {
+    __shared__ double smin[256], smax[256];
+    double mn = INFINITY, mx = 0.0;
+    bool bad = false;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        double v = fabs((double)A[j + j * lda]);
+        if (!isfinite(v)) bad = true;
+        mn = fmin(mn, v);
+        mx = fmax(mx, v);
+    }
+    if (bad) raise_status(st, DEV_NONFINITE, 30, 0);
+    smin[threadIdx.x] = mn;
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = smin[0];
+        out[1] = smax[0];
+    }
+}
+
+// dst[j + i*ldd] = src[i + j*lds] for i < rows, j < cols (32 x 32 smem tiles).
+template <typename S, typename D>
+__global__ void transpose_kernel(const S *src, int64_t lds, D *dst, int64_t ldd, int64_t rows,
+                                 int64_t cols) {
+    __shared__ D tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int64_t i = i0 + threadIdx.x, j = j0 + r;
+        if (i < rows && j < cols) tile[r][threadIdx.x] = (D)src[i + j * lds];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int64_t j = j0 + threadIdx.x, i = i0 + r;
+        if (i < rows && j < cols) dst[j + i * ldd] = tile[threadIdx.x][r];
+    }
+}
+
+}  // namespace
+
+ct_status transpose_any(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
+                        int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
+    if (rows == 0 || cols == 0) return CT_OK;
+    dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32)), block(32, 8);
+    if (src_kind == 1 && dst_kind == 1)
+        transpose_kernel<double, double><<<grid, block, 0, s>>>((const double *)src, lds, (double *)dst, ldd, rows, cols);
+    else if (src_kind == 1 && dst_kind == 0)
+        transpose_kernel<double, float><<<grid, block, 0, s>>>((const double *)src, lds, (float *)dst, ldd, rows, cols);
+    else if (src_kind == 0 && dst_kind == 1)
+        transpose_kernel<float, double><<<grid, block, 0, s>>>((const float *)src, lds, (double *)dst, ldd, rows, cols);
+    else
+        transpose_kernel<float, float><<<grid, block, 0, s>>>((const float *)src, lds, (float *)dst, ldd, rows, cols);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status transpose_d(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t rows,
+                      int64_t cols, cudaStream_t s) {
+    return transpose_any(1, src, lds, 1, dst, ldd, rows, cols, s);
+}
+
+ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
+                          int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
+    const int64_t total = rows * cols;
+    if (total == 0) return CT_OK;
+    const unsigned b = (unsigned)ceil_div(total, 256);
+    if (src_kind == 0 && dst_kind == 0)
+        copy_convert_kernel<float, float><<<b, 256, 0, s>>>((const float *)src, lds, (float *)dst, ldd, rows, cols);
+    else if (src_kind == 0 && dst_kind == 1)
+        copy_convert_kernel<float, double><<<b, 256, 0, s>>>((const float *)src, lds, (double *)dst, ldd, rows, cols);
+    else if (src_kind == 1 && dst_kind == 0)
+        copy_convert_kernel<double, float><<<b, 256, 0, s>>>((const double *)src, lds, (float *)dst, ldd, rows, cols);
+    else
+        copy_convert_kernel<double, double><<<b, 256, 0, s>>>((const double *)src, lds, (double *)dst, ldd, rows, cols);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status fill_zero_2d(bool fp64, void *dst, int64_t ld, int64_t rows, int64_t cols,
+                       cudaStream_t s) {
+    const int64_t total = rows * cols;
+    if (total == 0) return CT_OK;
+    const unsigned b = (unsigned)ceil_div(total, 256);
+    if (fp64) fill_zero_kernel<double><<<b, 256, 0, s>>>((double *)dst, ld, rows, cols);
+    else fill_zero_kernel<float><<<b, 256, 0, s>>>((float *)dst, ld, rows, cols);
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status rdiag_minmax(bool fp64, const void *A, int64_t lda, int64_t n, double *out,
+                       cudaStream_t s) {
+    if (fp64) rdiag_minmax_kernel<double><<<1, 256, 0, s>>>((const double *)A, lda, n, out, device_status());
+    else rdiag_minmax_kernel<float><<<1, 256, 0, s>>>((const float *)A, lda, n, out, device_status());
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+}  // namespace ctqr

@@ -1,0 +1,54 @@
+"""GEMM engine behind the WY updates and the Q^T application (tcgen05 TF32
+tensor cores; CUDA-core FP32/FP64) against a float64 matmul of the same
+operands.  TF32 operands are pre-rounded to TF32 so the tensor-core products
+are exact and only FP32 accumulation error remains."""
+import numpy as np
+import pytest
+
+from gpu_util import need_cuda
+
+SHAPES = [(128, 256, 64), (300, 520, 1000), (64, 96, 40000), (1, 1, 1), (513, 257, 33),
+          (256, 512, 4096)]
+
+
+def tf32_round(a):
+    b = a.astype(np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+    return b.view(np.float32)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["tf32", "fp32", "fp64"])
+@pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "N"), ("N", "T"), ("T", "T")])
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_gemm_matches_float64(kind, ta, tb, M, N, K):
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    dt = np.float64 if kind == "fp64" else np.float32
+    pad = 4
+    # logical op(A) is M x K, op(B) is K x N; storage is column-major
+    ra, ca = (K, M) if ta == "T" else (M, K)
+    rb, cb = (N, K) if tb == "T" else (K, N)
+    lda, ldb, ldc = -(-ra // 4) * 4 + pad, -(-rb // 4) * 4 + pad, M + pad
+    A = rng.uniform(-1, 1, (ca, lda)).astype(dt)   # torch row (ca, lda) = col-major (lda x ca)
+    B = rng.uniform(-1, 1, (cb, ldb)).astype(dt)
+    Cm = rng.uniform(-1, 1, (N, ldc)).astype(dt)
+    if kind == "tf32":
+        A, B = tf32_round(A), tf32_round(B)
+    Amat = A[:, :ra].T.astype(np.float64)  # stored matrix ra x ca
+    Bmat = B[:, :rb].T.astype(np.float64)
+    opA = Amat.T if ta == "T" else Amat
+    opB = Bmat.T if tb == "T" else Bmat
+    alpha, beta = 0.75, -0.5
+    ref = alpha * opA @ opB + beta * Cm[:, :M].T.astype(np.float64)
+    dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, Cm))
+    ct.gemm(kind, ta, tb, M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy()[:, :M].T.astype(np.float64)
+    scale = np.abs(opA) @ np.abs(opB) * abs(alpha) + abs(beta) * np.abs(Cm[:, :M].T)
+    eps = 2.0 ** -52 if kind == "fp64" else 2.0 ** -23
+    tol = 4 * (K + 2) * eps * scale + 1e-300
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), (np.argwhere(bad)[:5], got[bad][:5], ref[bad][:5])
+    # padding rows of C untouched
+    np.testing.assert_array_equal(dC.cpu().numpy()[:, M:], Cm[:, M:])

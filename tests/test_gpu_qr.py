@@ -1,0 +1,138 @@
+"""Householder QR + solve on the GPU against the oracle (Sec. 2 Eqs. 2-3).
+
+Tolerances (relative image error ||x - x_ref|| / ||x_ref||): FP64 path 1e-10,
+plain FP32 path 1e-4.  Factors are compared through R (LAPACK sign
+convention on both sides) and through invariants, since blockings differ."""
+import numpy as np
+import pytest
+
+from gpu_util import need_cuda, rel_err_cols
+from paper_2412_07631_b300 import synth
+
+
+def _case(O, ns, nv, nb, sl, k, noisy, seed0=1234):
+    g = O.Geometry(ns, nv, nb, sqrt_lambda=sl)
+    csr = O.siddon_csr(g)
+    X = synth.phantom_batch(ns, k, 8 if ns <= 32 else 10, seed0)
+    P = O.forward(csr, X)
+    B = synth.poisson_sinogram(P, ns, 1e4, seed=seed0) if noisy else P
+    return g, csr, X, B
+
+
+def _gpu_solve(torch, ct, g, B, precision, **kw):
+    storage = "fp64" if precision == "fp64" else "fp32"
+    sysg = ct.System(ct.make_geometry(g.n_side, g.n_views, g.n_bins, g.sqrt_lambda), storage)
+    F = sysg.factor(precision, **kw)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(dt).cuda()
+    X = F.solve(Bt, allow_noconv=True)
+    return sysg, F, X.double().cpu().numpy().T
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_c1_noiseless_matches_oracle(oracle_mod, precision, tol):
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, 32, 60, 46, 0.0, 3, False)
+    Xo, VR, tau = O.qr_solve(g, O.dense_system(g, csr), B)
+    sysg, F, Xg = _gpu_solve(torch, ct, g, B, precision)
+    assert rel_err_cols(Xg, Xo).max() <= tol
+    assert rel_err_cols(Xg, X).max() <= tol  # exact recovery from consistent data
+    if precision == "fp64":
+        VRg, taug = F.export()
+        n = g.n
+        Ro, Rg = np.triu(VR[:n]), np.triu(VRg[:n])
+        np.testing.assert_allclose(Rg, Ro, rtol=0, atol=1e-11 * np.abs(Ro).max())
+        np.testing.assert_allclose(taug, tau, rtol=0, atol=1e-11)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+@pytest.mark.parametrize("ns,nv,nb,sl", [(19, 31, 29, 0.05), (24, 40, 36, 0.05), (20, 37, 30, 0.0)])
+def test_ragged_noisy_matches_oracle(oracle_mod, precision, tol, ns, nv, nb, sl):
+    """Sizes that are not multiples of any tile or block (n = 361, 576, 400;
+    M' = 1260, 2016, 1110), noisy data, with and without regularisation."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, ns, nv, nb, sl, 5, True)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    for nb_outer in (0, 64):
+        _, _, Xg = _gpu_solve(torch, ct, g, B, precision, nb_outer=nb_outer)
+        assert rel_err_cols(Xg, Xo).max() <= tol
+
+
+@pytest.mark.gpu
+def test_tf32_direct_solve_is_tf32_accurate(oracle_mod):
+    """The TF32 tensor-core factorisation without refinement: error of the
+    order of kappa * 2^-10, far above FP32 and far below 1."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, 32, 60, 46, 0.0, 3, False)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    sysg = ct.System(ct.make_geometry(32, 60, 46), "fp32")
+    F = sysg.factor("tf32")
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    Xg = F.solve(Bt, max_iter=-1, allow_noconv=True).cpu().numpy().T
+    err = rel_err_cols(Xg, Xo).max()
+    print("tf32 direct error", err)
+    assert err < 0.5
+
+
+@pytest.mark.gpu
+def test_adjoint_identity_fp64(oracle_mod):
+    """<solve(b), y> = <b, adjoint(y)> (the adjoint is Q [R^-T y; 0] restricted
+    to the ray rows)."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    sysg = ct.System(ct.make_geometry(24, 40, 36, 0.05), "fp64")
+    F = sysg.factor("fp64")
+    rng = np.random.default_rng(1)
+    b = torch.from_numpy(rng.standard_normal((3, sysg.m))).cuda()
+    y = torch.from_numpy(rng.standard_normal((3, sysg.n))).cuda()
+    x = F.solve(b)
+    gb = F.adjoint(y)
+    lhs = (x * y).sum(1)
+    rhs = (b * gb).sum(1)
+    np.testing.assert_allclose(lhs.cpu().numpy(), rhs.cpu().numpy(), rtol=1e-12)
+
+
+@pytest.mark.gpu
+def test_adjoint_matches_oracle_gradient(oracle_mod):
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g = O.Geometry(24, 40, 36, sqrt_lambda=0.05)
+    VR, tau = O.householder_qr(O.dense_system(g))
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal((g.n, 2))
+    z = O.forwardsolve_rt(VR, y)
+    full = np.zeros((g.rows, 2), order="F")
+    full[: g.n] = z
+    want = O.apply_q(VR, tau, full)[: g.m]
+    sysg = ct.System(ct.make_geometry(24, 40, 36, 0.05), "fp64")
+    F = sysg.factor("fp64")
+    gb = F.adjoint(torch.from_numpy(np.ascontiguousarray(y.T)).cuda()).cpu().numpy().T
+    np.testing.assert_allclose(gb, want, rtol=0, atol=1e-10 * np.abs(want).max())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("ns,nv,nb,sl,noisy", [(32, 60, 46, 0.0, False), (24, 40, 36, 0.05, True),
+                                               (19, 31, 29, 0.05, True)])
+def test_tf32_refined_reaches_1e6(oracle_mod, ns, nv, nb, sl, noisy):
+    """TF32 tensor-core factors + FP64 refinement: relative image error
+    <= 1e-6 against the FP64 oracle solution."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, ns, nv, nb, sl, 4, noisy)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    sysg = ct.System(ct.make_geometry(ns, nv, nb, sl), "fp32")
+    F = sysg.factor("tf32")
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    Xg = F.solve(Bt, max_iter=30, tol=1e-9).cpu().numpy().T
+    print("refine info", F.last_info)
+    assert rel_err_cols(Xg, Xo).max() <= 1e-6
