@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the direct CT reconstruction hot path (arxiv 2412.07631) on B300.
+
+One step = the whole hot path for one batch: build the Siddon system matrix
+A~ = [A; sqrt(lambda) I] on the GPU, factor it by blocked Householder QR with
+TF32 tensor-core trailing updates (FP32 storage, FP64 column norms), and solve
+k noisy sinograms x = R^-1 Q^T b~ with FP64 Krylov refinement on the
+low-precision factors.
+
+Workload (default): 256 x 256 image (n = 65,536), 360 views x 364 bins
+(m = 131,040) + 65,536 regularisation rows (sqrt(lambda) = 0.05), 512
+sinograms of seeded 10-ellipse phantoms with Poisson noise at I0 = 5e3.
+
+Reported value: algorithmic TFLOP/s of the step's dense QR + direct solve,
+(2 M' n^2 - 2/3 n^3) + k (4 M' n - n^2), over the device-timed step
+(build + QR + solve + refinement; refinement flops are not counted).  The
+line also carries the QR-phase TFLOP/s, the slices/s of the solve phase, the
+refinement steps, a certified error bound against the exact least-squares
+solution on sampled slices, the roofline of the dominant (tensor-core GEMM)
+kernel class, the oracle timed on the host cores, and an end-to-end arm that
+passes the sinograms and images through pinned host memory.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QR TFLOP/s + slices/s at 256², mixed-prec+refine vs FP64, err vs FP64 oracle"
+WORKLOADS = {
+    # name: (n_side, views, bins, sqrt_lambda, k, I0, ellipses)
+    "c3": (256, 360, 364, 0.05, 512, 5e3, 10),
+    "c2": (128, 180, 182, 0.05, 64, 1e4, 10),
+    "c1": (32, 60, 46, 0.0, 1, None, 8),
+}
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
+
+
+def workload_desc(name):
+    ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
+    noise = f"Poisson I0={i0:g}" if i0 else "noiseless"
+    return (f"{ns}x{ns} parallel-beam Siddon, {nv} views x {nb} bins"
+            + (f" + sqrt(lambda)={sl} I rows" if sl > 0 else "")
+            + f", {k} sinograms of {ne}-ellipse phantoms, {noise}")
+
+
+def flops_of(ns, nv, nb, sl, k):
+    n = ns * ns
+    M = nv * nb + (n if sl > 0 else 0)
+    qr = 2.0 * M * n * n - 2.0 / 3.0 * n ** 3
+    solve = k * (4.0 * M * n - n * n)
+    return M, n, qr, solve
+
+
+# ---------------------------------------------------------------------------
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+def make_inputs(ct, torch, name, rank=0):
+    """Seeded phantoms, GPU forward projection (the library's own FP64 sparse
+    product), Poisson noise from the seeded generator.  Untimed."""
+    from paper_2412_07631_b300 import synth
+    ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
+    first = synth.BASE_SEED + rank * k
+    X = synth.phantom_batch(ns, k, ne, first)
+    sysg = ct.System(ct.make_geometry(ns, nv, nb, sl), "fp32")
+    P = sysg.forward(torch.from_numpy(np.ascontiguousarray(X.T)).cuda()).cpu().numpy().T
+    sysg.free()
+    del sysg
+    B = synth.poisson_sinogram(P, ns, i0, seed=first) if i0 else P
+    return X, np.ascontiguousarray(np.asarray(B).T)  # (n x k) phantoms, (k x m) sinograms
+
+
+def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=None):
+    """One pass of the hot path.  Returns (X, info, per-phase ms)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    sysg = ct.System(geom, "fp64" if precision == "fp64" else "fp32")
+    ev[1].record()
+    F = sysg.factor(precision)
+    ev[2].record()
+    if host:
+        X = F.solve_host(B, max_iter=max_iter, tol=tol)
+    else:
+        X = F.solve(B, max_iter=max_iter, tol=tol, allow_noconv=True)
+    ev[3].record()
+    info = dict(F.last_info or {})
+    F.free()
+    sysg.free()
+    torch.cuda.synchronize()
+    ph = {"build": ev[0].elapsed_time(ev[1]), "qr": ev[1].elapsed_time(ev[2]),
+          "solve": ev[2].elapsed_time(ev[3])}
+    return X, info, ph
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(name, cols=None):
+    """The oracle as it stands on a bounded sample of the workload: the plain
+    Householder QR of the first `cols` columns of A~ (all M' rows), with the
+    reflectors applied to one sinogram and the back-substitution.  Returns
+    (TFLOP/s, seconds, description, cores)."""
+    import oracle as O
+    ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
+    g = O.Geometry(ns, nv, nb, sqrt_lambda=sl)
+    n = g.n
+    w = cols or min(n, 160)
+    csr = O.siddon_csr(g)
+    S = csr.to_scipy()
+    A = np.zeros((g.rows, w), order="F")
+    A[: g.m] = S[:, :w].toarray()
+    if sl > 0:
+        A[g.m + np.arange(w), np.arange(w)] = sl
+    b = np.zeros((g.rows, 1), order="F")
+    b[: g.m, 0] = np.asarray(S[:, :w] @ np.ones(w)).ravel()
+    t0 = time.perf_counter()
+    VR, tau = O.householder_qr(A)
+    C_ = O.apply_qt(VR, tau, b)
+    O.backsolve(VR, C_)
+    dt = time.perf_counter() - t0
+    M = g.rows
+    fl = 2.0 * M * w * w - 2.0 / 3.0 * w ** 3 + 4.0 * M * w - w * w
+    desc = (f"oracle plain Householder QR of the first {w} of {n} columns of A~ "
+            f"({M} x {w}), Q^T applied to one sinogram, back-substitution")
+    return fl / dt / 1e12, dt, desc, os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--max-iter", type=int, default=40)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cert", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ns, nv, nb, sl, k, i0, ne = WORKLOADS[args.workload]
+    M, n, qr_fl, solve_fl = flops_of(ns, nv, nb, sl, k)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # The reference arm is the oracle on the host cores, one bounded sample per step.
+        for _ in range(args.warmup):
+            cpu_oracle_sample(args.workload)
+        vals, secs = [], []
+        for _ in range(args.steps):
+            v, dt, desc, cores = cpu_oracle_sample(args.workload)
+            vals.append(v)
+            secs.append(dt)
+        val = float(np.median(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_desc(args.workload)},
+                "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_2412_07631_b300 as ct
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    peaks, peak_src = load_peaks()
+
+    geom = ct.make_geometry(ns, nv, nb, sl)
+    Xtrue, Bh = make_inputs(ct, torch, args.workload, rank)
+    io_dt = torch.float32 if args.precision == "fp32" else torch.float64
+    B = torch.from_numpy(Bh).to(io_dt).cuda()
+    Bpin = torch.from_numpy(Bh).to(io_dt).pin_memory()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        run_step(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
+
+    # ---- timed region (device-resident inputs) ----
+    clocks = ClockSampler(local)
+    ct.stats_reset(False)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    phases, infos = [], []
+    for _ in range(args.steps):
+        X, info, ph = run_step(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
+        phases.append(ph)
+        infos.append(info)
+    e1.record()
+    barrier()
+    clk = clocks.stop()
+    launches = ct.stats_read()["launches"]
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    step_fl = (qr_fl + solve_fl) * world
+    value = step_fl / (ms * 1e-3) / 1e12
+    qr_ms = float(np.median([p["qr"] for p in phases]))
+    solve_ms = float(np.median([p["solve"] for p in phases]))
+    build_ms = float(np.median([p["build"] for p in phases]))
+
+    # ---- profiled step (per-kernel-class CUDA events, not part of the timing) ----
+    ct.stats_reset(True)
+    run_step(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
+    prof = ct.stats_read()
+    ct.stats_reset(False)
+    tc = prof["tc_gemm"]
+    tf32_peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+    achieved = tc["flops"] / (tc["ms"] * 1e-3) / 1e12 if tc["ms"] > 0 else 0.0
+    roofline = {"bound": "tensor", "kernel": "gemm_tf32_kernel (tcgen05, all launches of a step)",
+                "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak if tf32_peak else None, "traffic": None,
+                "peak_source": f"{peak_src} bf16 sustained x nominal TF32/BF16 ratio {TF32_OVER_BF16:.3f}",
+                "launches_per_step": tc["count"], "ms_per_step": tc["ms"]}
+    breakdown = {c: {"ms": round(prof[c]["ms"], 3), "count": prof[c]["count"]}
+                 for c in ct.STAT_CLASSES if prof[c]["count"]}
+
+    # ---- end-to-end arm: pinned host sinograms in, host images out ----
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(1):
+            run_step(ct, torch, geom, args.precision, Bpin, args.max_iter, args.tol, host=True)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Xh, _, _ = run_step(ct, torch, geom, args.precision, Bpin, args.max_iter, args.tol,
+                                host=True)
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        es = 4 if args.precision == "fp32" else 8
+        e2e = {"value": step_fl / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(k * (M - (n if sl > 0 else 0)) * es),
+               "d2h_bytes_per_step": int(k * n * es), "ms_per_step": e2e_ms,
+               "api": "ct_build_system + ct_qr_factor + ct_solve_host"}
+
+    # ---- accuracy: certified bound vs the exact LS solution, quality vs phantom ----
+    Xn = X.double().cpu().numpy().T
+    acc = {}
+    if rank == 0 and not args.no_cert and sl > 0:
+        import oracle as O
+        g = O.Geometry(ns, nv, nb, sqrt_lambda=sl)
+        csr = O.siddon_csr(g)
+        pick = np.linspace(0, k - 1, min(k, 4)).astype(int)
+        cert = O.certificate(g, csr, np.asfortranarray(Bh[pick].T), np.asfortranarray(Xn[:, pick]))
+        acc["cert_bound_max"] = float(cert.max())
+        acc["cert_slices"] = [int(p) for p in pick]
+    rmse = np.sqrt(np.mean((Xn - Xtrue) ** 2, axis=0))
+    acc["rmse_vs_phantom_mean"] = float(rmse.mean())
+    acc["psnr_vs_phantom_mean"] = float(np.mean(20 * np.log10(1.0 / rmse)))
+
+    # ---- FP64 GPU path vs mixed path on the 128x128 geometry (FP64 at 256^2
+    #      takes tens of minutes at the FP64 rate of this part) ----
+    cmp = None
+    if rank == 0 and not args.no_fp64_compare and args.workload == "c3":
+        cns, cnv, cnb, csl, ck, ci0, cne = WORKLOADS["c2"]
+        cM, cn, cqr, csolve = flops_of(cns, cnv, cnb, csl, ck)
+        cg = ct.make_geometry(cns, cnv, cnb, csl)
+        _, cB = make_inputs(ct, torch, "c2")
+        cmp = {"workload": workload_desc("c2")}
+        for prec in ("fp64", "tf32"):
+            Bd = torch.from_numpy(cB).double().cuda()
+            run_step(ct, torch, cg, prec, Bd, args.max_iter, args.tol) if prec == "tf32" else None
+            _, inf, ph = run_step(ct, torch, cg, prec, Bd, args.max_iter, args.tol)
+            cmp[prec] = {"qr_tflops": cqr / (ph["qr"] * 1e-3) / 1e12,
+                         "slices_per_s": ck / (ph["solve"] * 1e-3),
+                         "refine_iters": inf.get("iterations", 0)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, desc, cores = cpu_oracle_sample(args.workload)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"tf32": "tf32 (FP32 storage) + f64 refinement", "fp32": "f32",
+                      "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload), "n_side": ns, "views": nv,
+                       "bins": nb, "rows": M, "unknowns": n, "slices": k,
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (dense A~ of %.1f GB rebuilt every step)"
+                             % (M * n * 4 / 1e9)},
+            "qr_tflops": qr_fl / (qr_ms * 1e-3) / 1e12,
+            "slices_per_s": k / (solve_ms * 1e-3),
+            "phases_ms": {"build": build_ms, "qr": qr_ms, "solve_refine": solve_ms},
+            "refine_iters": [i.get("iterations") for i in infos],
+            "accuracy": acc,
+            "roofline": roofline,
+            "kernel_breakdown_ms": breakdown,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "fp64_vs_mixed": cmp,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -206,6 +206,26 @@ CT_API ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int
 CT_API void ct_system_free(ct_system sys);
 CT_API void ct_factor_free(ct_factor f);
 
+/* ---- Benchmark accounting (not part of the method) ---------------------- */
+
+/* Zero the launch counter; timing != 0 also brackets every tensor-core GEMM,
+ * CUDA-core GEMM, panel, triangular-diagonal, sparse-product and Siddon launch
+ * with CUDA events on its stream, recording its algorithmic flops and bytes
+ * (adds a little launch overhead; off by default). */
+CT_API ct_status ct_stats_reset(int32_t timing);
+
+/* Synchronises the device, then returns the number of kernels launched since
+ * the last reset and, per class (8 entries each; classes: 0 tensor-core GEMM,
+ * 1 CUDA-core GEMM, 2 panel, 3 triangular diagonal blocks, 4 sparse FP64
+ * products, 5 Siddon, 6 other), the summed event time in ms, algorithmic
+ * flops, algorithmic bytes and launch count.  Any pointer may be NULL. */
+CT_API ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *bytes,
+                               int64_t *count);
+
+/* Write one CSV line per timed launch since the last ct_stats_reset(1):
+ * class, four shape fields (GEMM: M, N, K, splits), ms, flops, bytes. */
+CT_API ct_status ct_stats_dump(const char *path);
+
 /* ---- Kernel-level entry points (used by the parity tests) --------------- */
 
 /* GEMM engine behind the WY updates: C = alpha * op(A) * op(B) + beta * C,

@@ -51,7 +51,8 @@ _LIB = None
 SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info",
            "ct_system_device_ptrs", "ct_system_export", "ct_forward_project", "ct_qr_factor",
            "ct_factor_device_ptrs", "ct_factor_export", "ct_solve", "ct_solve_host",
-           "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm"]
+           "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm", "ct_stats_reset",
+           "ct_stats_read", "ct_stats_dump"]
 
 
 def lib_path() -> str:
@@ -86,6 +87,9 @@ def lib():
     L.ct_factor_free.restype = None
     L.ct_gemm.argtypes = [I32, C.c_char, C.c_char, I64, I64, I64, C.c_double, vp, I64, vp, I64,
                           C.c_double, vp, I64, vp]
+    L.ct_stats_reset.argtypes = [I32]
+    L.ct_stats_read.argtypes = [C.POINTER(I64), vp, vp, vp, vp]
+    L.ct_stats_dump.argtypes = [C.c_char_p]
     for name in SYMBOLS:
         if name not in ("ct_status_str", "ct_last_error", "ct_system_free", "ct_factor_free"):
             getattr(L, name).restype = C.c_int
@@ -262,5 +266,33 @@ def gemm(kind: str, transa: str, transb: str, M: int, N: int, K: int, alpha: flo
                          _ptr(A), lda, _ptr(B), ldb, beta, _ptr(Cm), ldc, _stream(stream)))
 
 
-__all__ = ["Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
+STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other"]
+
+
+def stats_reset(timing: bool = False):
+    """Zero the library's launch counter (and per-class event timing if asked)."""
+    _check(lib().ct_stats_reset(1 if timing else 0))
+
+
+def stats_dump(path: str):
+    """CSV of every timed launch since stats_reset(True)."""
+    _check(lib().ct_stats_dump(path.encode()))
+
+
+def stats_read() -> dict:
+    """Launches since the last reset and per-class time/flops/bytes/count."""
+    import numpy as np
+    n = C.c_int64()
+    ms, fl, by = (np.zeros(8) for _ in range(3))
+    cnt = np.zeros(8, np.int64)
+    _check(lib().ct_stats_read(C.byref(n), ms.ctypes.data, fl.ctypes.data, by.ctypes.data,
+                               cnt.ctypes.data))
+    out = {"launches": int(n.value)}
+    for i, name in enumerate(STAT_CLASSES):
+        out[name] = {"ms": float(ms[i]), "flops": float(fl[i]), "bytes": float(by[i]),
+                     "count": int(cnt[i])}
+    return out
+
+
+__all__ = ["stats_reset", "stats_read", "stats_dump", "STAT_CLASSES", "Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
            "lib_path", "make_geometry", "PRECISIONS", "SYMBOLS"]

@@ -1,4 +1,5 @@
 // api.cu -- the extern "C" entry points declared in include/ctqr.h.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -70,6 +71,51 @@ ct_status check_device_status(cudaStream_t s) {
         case DEV_NONFINITE: return CT_ERR_NONFINITE;
         default: return CT_ERR_ARG;
     }
+}
+
+// ---- benchmark accounting ---------------------------------------------------
+namespace {
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_timing{false};
+struct ProfRec {
+    int cls;
+    double flops, bytes;
+    int64_t d[4];
+    cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof;
+size_t g_prof_used = 0;
+}  // namespace
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int c, cudaStream_t st, double f, double b, int64_t d0, int64_t d1,
+                     int64_t d2, int64_t d3)
+    : cls(c), s(st), flops(f), bytes(b), slot(-1) {
+    if (!g_timing.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_used == g_prof.size()) {
+        ProfRec r{};
+        if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) return;
+        g_prof.push_back(r);
+    }
+    slot = (int)g_prof_used++;
+    ProfRec &r = g_prof[slot];
+    r.cls = c;
+    r.flops = f;
+    r.bytes = b;
+    r.d[0] = d0;
+    r.d[1] = d1;
+    r.d[2] = d2;
+    r.d[3] = d3;
+    cudaEventRecord(r.e0, s);
+}
+
+ProfScope::~ProfScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof[slot].e1, s);
 }
 
 ct_status Scratch::ensure(size_t need) {
@@ -145,6 +191,55 @@ const char *ct_status_str(ct_status s) {
 }
 
 const char *ct_last_error(void) { return g_err; }
+
+ct_status ct_stats_reset(int32_t timing) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_launches.store(0);
+    g_prof_used = 0;
+    g_timing.store(timing != 0);
+    return CT_OK;
+}
+
+ct_status ct_stats_dump(const char *path) {
+    if (!path) return CT_ERR_ARG;
+    CT_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    FILE *fp = fopen(path, "w");
+    if (!fp) return CT_ERR_ARG;
+    fprintf(fp, "class,d0,d1,d2,d3,ms,flops,bytes\n");
+    for (size_t i = 0; i < g_prof_used; ++i) {
+        const ProfRec &r = g_prof[i];
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.e0, r.e1);
+        fprintf(fp, "%d,%lld,%lld,%lld,%lld,%.6f,%.6g,%.6g\n", r.cls, (long long)r.d[0],
+                (long long)r.d[1], (long long)r.d[2], (long long)r.d[3], t, r.flops, r.bytes);
+    }
+    fclose(fp);
+    return CT_OK;
+}
+
+ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *bytes,
+                        int64_t *count) {
+    CT_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (launches) *launches = g_launches.load();
+    for (int c = 0; c < PROF_NCLASS; ++c) {
+        if (ms) ms[c] = 0;
+        if (flops) flops[c] = 0;
+        if (bytes) bytes[c] = 0;
+        if (count) count[c] = 0;
+    }
+    for (size_t i = 0; i < g_prof_used; ++i) {
+        const ProfRec &r = g_prof[i];
+        float t = 0.f;
+        CT_CUDA(cudaEventElapsedTime(&t, r.e0, r.e1));
+        if (ms) ms[r.cls] += t;
+        if (flops) flops[r.cls] += r.flops;
+        if (bytes) bytes[r.cls] += r.bytes;
+        if (count) count[r.cls] += 1;
+    }
+    return CT_OK;
+}
 
 ct_status ct_build_system(const ct_geometry *geom, ct_precision storage, void *stream,
                           ct_system *out) {
@@ -329,7 +424,7 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     f->lda = sys->lda;
     int nb = o.nb_inner > 0 ? o.nb_inner : (f->fp64 ? 16 : 32);
     nb = std::min(nb, 32);
-    int NB = o.nb_outer > 0 ? o.nb_outer : (f->fp64 ? 32 : (f->kind == GEMM_F32 ? 128 : 256));
+    int NB = o.nb_outer > 0 ? o.nb_outer : (f->fp64 ? 32 : (f->kind == GEMM_F32 ? 128 : 512));
     NB = (int)round_up(std::max(NB, nb), nb);
     if (NB % 32) NB = (int)round_up(NB, 32);
     f->nb = nb;
@@ -426,6 +521,9 @@ void ct_system_free(ct_system sys) {
 
 void ct_factor_free(ct_factor f) {
     if (!f) return;
+    cudaFree(f->Rinv);
+    cudaFree(f->RinvT);
+    cudaFree(f->Rt);
     cudaFree(f->VR);
     cudaFree(f->tau);
     cudaFree(f->Tall);

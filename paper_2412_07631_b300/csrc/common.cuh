@@ -191,6 +191,25 @@ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 int num_sms();
 
+// ---- benchmark accounting (not part of the method) -------------------------------
+// Every kernel launch of the library increments a process-wide counter; when
+// timing is enabled, launches of the classes below are bracketed by CUDA
+// events on their stream and their algorithmic flops/bytes are recorded.
+enum ProfClass : int {
+    PROF_TC_GEMM = 0, PROF_SIMT_GEMM = 1, PROF_PANEL = 2, PROF_TRSM_DIAG = 3, PROF_SPMM = 4,
+    PROF_SIDDON = 5, PROF_OTHER = 6, PROF_NCLASS = 7
+};
+void count_launch(int n = 1);
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    double flops, bytes;
+    int slot;
+    ProfScope(int cls, cudaStream_t s, double flops, double bytes, int64_t d0 = 0, int64_t d1 = 0,
+              int64_t d2 = 0, int64_t d3 = 0);
+    ~ProfScope();
+};
+
 // Device scratch buffer owned by the library (grown on demand, never shrunk).
 struct Scratch {
     void *ptr = nullptr;

@@ -108,18 +108,24 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const T *
 
 ct_status gemm_simt_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
                            cudaStream_t s) {
+    const double es = g.kind == GEMM_F64 ? 8.0 : 4.0;
+    ProfScope prof(PROF_SIMT_GEMM, s, 2.0 * g.M * g.N * g.K,
+                   es * ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N * splits),
+                   g.M, g.N, g.K, splits);
     if (g.kind == GEMM_F64) {
         constexpr int BM = 64, BN = 64;
         dim3 grid((unsigned)ceil_div(g.M, BM), (unsigned)ceil_div(g.N, BN), (unsigned)splits);
         gemm_simt_kernel<double, BM, BN, 16, 4, 4><<<grid, 256, 0, s>>>(
             g.ta, g.tb, g.M, g.N, g.K, kchunk, g.alpha, (const double *)g.A, g.lda,
             (const double *)g.B, g.ldb, g.beta, (double *)g.C, g.ldc, split_stride);
+        count_launch();
     } else {
         constexpr int BM = 128, BN = 128;
         dim3 grid((unsigned)ceil_div(g.M, BM), (unsigned)ceil_div(g.N, BN), (unsigned)splits);
         gemm_simt_kernel<float, BM, BN, 8, 8, 8><<<grid, 256, 0, s>>>(
             g.ta, g.tb, g.M, g.N, g.K, kchunk, (float)g.alpha, (const float *)g.A, g.lda,
             (const float *)g.B, g.ldb, (float)g.beta, (float *)g.C, g.ldc, split_stride);
+        count_launch();
     }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -130,13 +136,17 @@ ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void 
     const int64_t total = M * N;
     if (total == 0) return CT_OK;
     const unsigned blocks = (unsigned)ceil_div(total, 256);
-    if (fp64)
+    if (fp64) {
         splitk_reduce_kernel<double><<<blocks, 256, 0, s>>>(M, N, splits, (const double *)P, alpha,
                                                             beta, (double *)C, ldc);
-    else
+        count_launch();
+    }
+    else {
         splitk_reduce_kernel<float><<<blocks, 256, 0, s>>>(M, N, splits, (const float *)P,
                                                            (float)alpha, (float)beta, (float *)C,
                                                            ldc);
+        count_launch();
+    }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }

@@ -5,12 +5,6 @@
 // operands (the tensor core reads the FP32 bit pattern and uses its TF32
 // part), FP32 accumulation in tensor memory.
 //
-// CTA tile 128 x 256 x 32 (UMMA M=128, N=256, K=8 per instruction, four
-// instructions per 32-deep stage).  Warp roles: warp 0 issues TMA loads of
-// 128B-swizzled tiles into a 4-stage shared-memory ring; warp 1 allocates
-// 256 TMEM columns and one of its threads issues the MMAs; warps 2-5 read the
-// accumulator back with tcgen05.ld and write C.
-//
 // Operand layouts: op(A) = A^T of a column-major A is "K-major" (each output
 // row's K values contiguous).  TF32 operands must be K-major (the transposed,
 // MN-major operand form yields zeros for 32-bit types on this hardware, as a
@@ -19,8 +13,20 @@
 // A K-major tile is one TMA box of 32 x rows: 128-byte rows, 8-row swizzle
 // atoms 1024 B apart.
 //
+// Persistent kernel: one CTA per SM walks the output tiles (128 x 256, K in
+// 32-deep stages) of its share of the work list.  Warp 0 issues TMA loads
+// into a 4-stage shared-memory ring; warp 1 allocates 512 TMEM columns (two
+// 128 x 256 FP32 accumulators) and one of its threads issues the MMAs (UMMA
+// M=128, N=256, K=8); warps 2-9 drain an accumulator with tcgen05.ld and
+// write C while the MMAs of the next tile fill the other accumulator, so the
+// epilogue traffic (C read and written when beta != 0) overlaps the
+// tensor-core work.  The tile order puts the grid dimension with fewer tiles
+// fastest, so CTAs resident at the same time share the operand tile of the
+// longer dimension through L2.
+//
 // Every mbarrier wait is bounded (4 s); on expiry the kernel records
 // DEV_TIMEOUT in the device status word, drains and returns.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -34,9 +40,11 @@ constexpr int BM = 128, BN = 256, BK = 32, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;  // 16 KiB
 constexpr int B_BYTES = BN * BK * 4;  // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = 256;
+constexpr int ACC_COLS = 256;
+constexpr int TMEM_COLS = 2 * ACC_COLS;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int THREADS = 192;
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading/stride
 // byte offsets (16-byte units), version 1, 128-byte swizzle.
@@ -56,24 +64,41 @@ __device__ __forceinline__ uint64_t slice_desc(uint32_t tile, int kk) {
     return make_desc(tile + kk * 32, 16, 1024);
 }
 
+struct TileSched {
+    int64_t mt, nt, tiles, work;
+    bool m_fast;
+    __device__ TileSched(int64_t M, int64_t N, int splits) {
+        mt = (M + BM - 1) / BM;
+        nt = (N + BN - 1) / BN;
+        tiles = mt * nt;
+        work = tiles * splits;
+        m_fast = mt <= nt;
+    }
+    // work item w -> (m tile, n tile, split)
+    __device__ void decode(int64_t w, int64_t &mi, int64_t &ni, int64_t &z) const {
+        z = w / tiles;
+        const int64_t t = w - z * tiles;
+        if (m_fast) { mi = t % mt; ni = t / mt; }
+        else { ni = t % nt; mi = t / nt; }
+    }
+};
+
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     int64_t M, int64_t N, int64_t K, int64_t kchunk,
+                     int64_t M, int64_t N, int64_t K, int64_t kchunk, int splits,
                      float alpha, float beta, float *C, int64_t ldc, int64_t split_stride,
                      DevStatus *st) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *accum = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    uint64_t *acc_full = empty + STAGES;   // [2] MMA -> epilogue
+    uint64_t *acc_empty = acc_full + 2;    // [2] epilogue -> MMA
+    uint64_t *drain = acc_empty + 2;       // MMA completion before TMEM release
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
-    const int64_t kb = (int64_t)blockIdx.z * kchunk;
-    const int64_t ke = min(K, kb + kchunk);
-    const int nk = (int)((ke - kb + BK - 1) / BK);
-    C += (int64_t)blockIdx.z * split_stride;
+    const TileSched ts(M, N, splits);
 
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tmA);
@@ -82,90 +107,127 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], EPI_WARPS);
+        }
+        mbar_init(drain, 1);
         mbar_fence_init();
     }
     if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem_d = *tmem_slot;
+    const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        int issued = 0;
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % STAGES;
-            const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u, st, 1)) break;
-            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-            uint8_t *sa = smem + s * STAGE_BYTES;
-            uint8_t *sb = sa + A_BYTES;
-            const int32_t k = (int32_t)(kb + (int64_t)kt * BK);
-            tma_load_2d(sa, &tmA, k, (int32_t)m0, &full[s]);
-            tma_load_2d(sb, &tmB, k, (int32_t)n0, &full[s]);
-            issued = kt + 1;
+        int64_t kt_glob = 0, issued = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < ts.work && ok; w += gridDim.x) {
+            int64_t mi, ni, z;
+            ts.decode(w, mi, ni, z);
+            const int64_t kb = z * kchunk, ke = min(K, kb + kchunk);
+            const int nk = (int)((ke - kb + BK - 1) / BK);
+            for (int kt = 0; kt < nk; ++kt, ++kt_glob) {
+                const int s = (int)(kt_glob % STAGES);
+                const uint32_t ph = (uint32_t)(kt_glob / STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, st, 1)) { ok = false; break; }
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                uint8_t *sa = smem + s * STAGE_BYTES;
+                const int32_t k = (int32_t)(kb + (int64_t)kt * BK);
+                tma_load_2d(sa, &tmA, k, (int32_t)(mi * BM), &full[s]);
+                tma_load_2d(sa + A_BYTES, &tmB, k, (int32_t)(ni * BN), &full[s]);
+                issued = kt_glob + 1;
+            }
         }
         // Drain: every issued copy must have landed before the CTA may exit.
-        for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
-            mbar_wait(&full[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, st, 2);
+        for (int64_t q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
+            mbar_wait(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, st, 2);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = (1u << 4)                       // D = F32
-                               | (2u << 7) | (2u << 10)        // A, B = TF32
-                               /* bits 15/16 = 0: both operands K-major */
+                               | (2u << 7) | (2u << 10)        // A, B = TF32, both K-major
                                | ((uint32_t)(BN >> 3) << 17)   // N
                                | ((uint32_t)(BM >> 4) << 24);  // M
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % STAGES;
-            const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, st, 3)) break;
+        int64_t kt_glob = 0, local = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < ts.work && ok; w += gridDim.x, ++local) {
+            int64_t mi, ni, z;
+            ts.decode(w, mi, ni, z);
+            const int64_t kb = z * kchunk, ke = min(K, kb + kchunk);
+            const int nk = (int)((ke - kb + BK - 1) / BK);
+            const int b = (int)(local & 1);
+            const uint32_t use = (uint32_t)(local >> 1);
+            if (!mbar_wait(&acc_empty[b], (use & 1u) ^ 1u, st, 5)) break;
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t sb = sa + A_BYTES;
+            const uint32_t d_tmem = tmem_base + (uint32_t)(b * ACC_COLS);
+            for (int kt = 0; kt < nk; ++kt, ++kt_glob) {
+                const int s = (int)(kt_glob % STAGES);
+                const uint32_t ph = (uint32_t)(kt_glob / STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph, st, 3)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / 8; ++kk) {
-                tc_mma<0>(tmem_d, slice_desc(sa, kk), slice_desc(sb, kk), idesc,
-                          (kt > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < BK / 8; ++kk)
+                    tc_mma<0>(d_tmem, slice_desc(sa, kk), slice_desc(sb, kk), idesc,
+                              (kt > 0 || kk > 0) ? 1u : 0u);
+                tc_commit(&empty[s]);
             }
-            tc_commit(&empty[s]);
+            tc_commit(&acc_full[b]);
         }
-        tc_commit(accum);
+        // all issued MMAs must complete before TMEM is released
+        tc_commit(drain);
+        mbar_wait(drain, 0, st, 6);
     } else if (warp >= 2) {
-        // ---------------- epilogue ----------------
-        const bool ok = mbar_wait(accum, 0, st, 4);
-        tc_fence_after();
-        const int q = warp % 4;
-        const int64_t row = m0 + 32 * q + lane;
-        if (ok && nk > 0) {
-            for (int c = 0; c < BN / 32; ++c) {
+        // ---------------- epilogue (8 warps) ----------------
+        const int e = warp - 2;
+        const int q = warp % 4;            // TMEM lane quarter this warp may access
+        const int half = e / 4;            // which 128 of the 256 accumulator columns
+        int64_t local = 0;
+        for (int64_t w = blockIdx.x; w < ts.work; w += gridDim.x, ++local) {
+            int64_t mi, ni, z;
+            ts.decode(w, mi, ni, z);
+            const int b = (int)(local & 1);
+            const uint32_t use = (uint32_t)(local >> 1);
+            if (!mbar_wait(&acc_full[b], use & 1u, st, 4)) break;
+            tc_fence_after();
+            float *Cz = C + z * split_stride;
+            const int64_t row = mi * BM + 32 * q + lane;
+            const uint32_t t0 = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * ACC_COLS + half * 128);
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
                 uint32_t r[32];
-                tmem_ld_32x32b_x32(tmem_d + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * 32), r);
+                tmem_ld_32x32b_x32(t0 + (uint32_t)(c * 32), r);
+                const int64_t col0 = ni * BN + half * 128 + c * 32;
                 if (row < M) {
+                    float *p = Cz + row + col0 * ldc;
+                    const int ncols = (N - col0 < 32) ? (int)(N - col0) : 32;
+                    if (beta != 0.0f) {
+                        float old[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t col = n0 + c * 32 + j;
-                        if (col < N) {
-                            float *p = C + row + col * ldc;
-                            float v = alpha * __uint_as_float(r[j]);
-                            if (beta != 0.0f) v += beta * *p;
-                            *p = v;
-                        }
+                        for (int j = 0; j < 32; ++j) old[j] = (j < ncols) ? p[(int64_t)j * ldc] : 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < ncols) p[(int64_t)j * ldc] = alpha * __uint_as_float(r[j]) + beta * old[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < ncols) p[(int64_t)j * ldc] = alpha * __uint_as_float(r[j]);
                     }
                 }
             }
-        } else if (ok && row < M) {
-            for (int64_t col = n0; col < min(N, n0 + BN); ++col) {
-                float *p = C + row + col * ldc;
-                *p = (beta != 0.0f) ? beta * *p : 0.0f;
-            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_d, TMEM_COLS);
+        tmem_dealloc(tmem_base, TMEM_COLS);
     }
 }
 
@@ -240,10 +302,16 @@ ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t 
     CT_TRY(make_map(&ma, g.A, g.K, g.M, g.lda, BK, BM));
     // op(B) = B, B stored K x N (K contiguous): box {32 (K), 256 (N)}.
     CT_TRY(make_map(&mb, g.B, g.K, g.N, g.ldb, BK, BN));
-    dim3 grid((unsigned)ceil_div(g.M, BM), (unsigned)ceil_div(g.N, BN), (unsigned)splits);
+    const int64_t work = ceil_div(g.M, BM) * ceil_div(g.N, BN) * splits;
+    dim3 grid((unsigned)std::min<int64_t>(work, num_sms()));
+    ProfScope prof(PROF_TC_GEMM, s, 2.0 * g.M * g.N * g.K,
+                   4.0 * ((double)g.M * g.K + (double)g.K * g.N +
+                          (double)g.M * g.N * splits * (g.beta != 0.0 ? 2 : 1)),
+                   g.M, g.N, g.K, splits);
     gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(
-        ma, mb, g.M, g.N, g.K, kchunk, (float)g.alpha, (float)g.beta,
+        ma, mb, g.M, g.N, g.K, kchunk, splits, (float)g.alpha, (float)g.beta,
         (float *)g.C, g.ldc, split_stride, device_status());
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }

@@ -35,13 +35,20 @@ struct ct_factor_s {
     void *Tall = nullptr;  // nblocks x (NB x NB), T_J of block J
     void *Vtop = nullptr;  // nblocks x (NB x NB), unit-lower top of V_J
     double rjj_min = 0, rjj_max = 0;
+    // triangular-solve aids (built on first solve): inverse diagonal blocks of R
+    // and their transposes (trsm_tb x trsm_tb each), R^T for the tensor-core path
+    void *Rinv = nullptr, *RinvT = nullptr, *Rt = nullptr;
+    int trsm_tb = 0;
+    int64_t ldrt = 0;
     // work buffers
-    ctqr::Scratch gemm_ws, W, W2, G, panel_ws, Bt, trsm_ws, refine_ws, host_pinned, misc;
+    ctqr::Scratch gemm_ws, W, W2, G, panel_ws, Bt, trsm_ws, refine_ws, host_pinned, misc, misc2;
     size_t es() const { return fp64 ? 8 : 4; }
 };
 
 namespace ctqr {
 ct_status qr_factor_run(ct_factor f, cudaStream_t s);
+// R X = C or R^T X = C in place for the factor's R (blocked, inverse diagonal blocks).
+ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, cudaStream_t s);
 // Apply Q^T (forward block order) or Q (reverse order) to the M x k matrix C.
 ct_status apply_q_blocks(ct_factor f, bool transpose, void *C, int64_t ldc, int64_t k,
                          cudaStream_t s);

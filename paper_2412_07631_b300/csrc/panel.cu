@@ -6,9 +6,10 @@
 // of a cooperative launch (G <= #SMs), each slab staged in shared memory for
 // the whole panel when it fits.  For column c (global jc = j0 + c) every CTA
 // accumulates, over its rows below the diagonal, the FP64 sum of squares of
-// the column and the FP64 dot products of the column with the panel columns
-// to its right; one grid barrier publishes the G partial vectors, and every
-// CTA reduces them in the same order (identical reflector everywhere).
+// the column and the dot products of the column with the panel columns to its
+// right (FP64 from the warp level up); one flag-based exchange publishes the
+// G partial vectors, and every CTA reduces them in the same order (identical
+// reflector everywhere).
 // With alpha = A[jc, jc]:
 //     beta = -sign(alpha) * sqrt(alpha^2 + ss),  tau = (beta - alpha)/beta,
 //     v = [1; x/(alpha - beta)],  and for each column k to the right
@@ -28,54 +29,44 @@ namespace {
 constexpr int PANEL_THREADS = 256;
 constexpr int PANEL_WARPS = PANEL_THREADS / 32;
 
-// Bounded grid barrier (sense by generation counter).  Returns false if the
-// wait expired or another CTA raised an error.
-__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned G, DevStatus *st, int where) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *vgen = gen;
-        const unsigned my_gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == G - 1) {
-            *((volatile unsigned *)count) = 0u;
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            const uint64_t t0 = globaltimer_ns();
-            uint32_t spins = 0;
-            while (*vgen == my_gen) {
-                __nanosleep(20);
-                if ((++spins & 255u) == 0) {
-                    if (*((volatile int *)&st->code) != 0) { ok = 0; break; }
-                    if (globaltimer_ns() - t0 > kWaitLimitNs) {
-                        raise_status(st, DEV_TIMEOUT, where, 0);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
+// Reduce-scatter over a warp: on entry every lane holds 32 values; on exit
+// lane l returns the warp-wide sum of value l (31 shuffles in all).
+__device__ __forceinline__ double warp_reduce_scatter32(double (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const double send = upper ? v[i] : v[i + o];
+            const double keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
-        __threadfence();
-        ok_s = ok;
     }
-    __syncthreads();
-    return ok_s != 0;
+    return v[0];
 }
 
+// Exchange area (global): flags[2][G] epoch words, partials[2][32][G] doubles,
+// rowbuf[2][32] doubles; index [c & 1] alternates between columns.
+//
+// Per column c (jc = j0 + c) each CTA forms 32 partial sums over its rows
+// strictly below jc: slot c holds the sum of squares of column c, slot k > c
+// the dot product of column c with column k.  It stores them, the owner of row
+// jc also stores that row, and a fence followed by a store of epoch jc+1 to
+// the CTA's flag publishes them.
+// Warp 0 of every CTA polls all G flags (bounded), fences, and then every CTA
+// reduces the G partial vectors in the same order.
 template <typename T, int NB>
 __global__ void __launch_bounds__(PANEL_THREADS, 1)
     panel_qr_kernel(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau, double *partials,
-                    double *rowbuf, unsigned *bar, DevStatus *st, int64_t rows_per, int use_smem) {
+                    double *rowbuf, unsigned *flags, DevStatus *st, int64_t rows_per, int use_smem) {
+    static_assert(NB <= 32, "panel width");
     extern __shared__ __align__(16) uint8_t dsm[];
-    __shared__ double red[PANEL_WARPS][NB + 1];
-    __shared__ double tot[NB + 1];
-    __shared__ double coef[NB];  // tau * (v^T a_k) for k > c
-    __shared__ T coefs[NB];      // coef[k] / (alpha - beta), in the storage type
-    __shared__ double scal_s, beta_s;
-    __shared__ int skip_s;
+    __shared__ double red[PANEL_WARPS][32];
+    __shared__ double tot[32];
+    __shared__ double coef[32];  // tau * (v^T a_k) for k > c
+    __shared__ T coefs[32];      // coef[k] / (alpha - beta), in the storage type
+    __shared__ double scal_s, beta_s, tau_s;
+    __shared__ int skip_s, ok_s;
 
     const unsigned G = gridDim.x;
     const int64_t r0 = j0 + (int64_t)blockIdx.x * rows_per;
@@ -99,66 +90,110 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
     for (int c = 0; c < nb; ++c) {
         const int64_t jc = j0 + c;
         const int par = c & 1;
+        const unsigned epoch = (unsigned)(jc + 1);
+        double *part = partials + (size_t)par * 32 * G;
+        unsigned *flg = flags + (size_t)par * G;
         // ---- phase 1: partial sums over local rows strictly below jc ----
-        double acc[NB + 1];
+        // The norm accumulates in FP64 from the first product on; the dot
+        // products accumulate in the storage type within a thread (a handful
+        // of rows) and in FP64 from the warp level up (FP64 FMA is far slower
+        // than FP32 on this part).
+        double ss = 0.0;
+        T acc[NB];
 #pragma unroll
-        for (int q = 0; q <= NB; ++q) acc[q] = 0.0;
+        for (int q = 0; q < NB; ++q) acc[q] = T(0);
         const int64_t rstart = max((int64_t)0, jc + 1 - r0);
         for (int64_t r = rstart + threadIdx.x; r < nloc; r += PANEL_THREADS) {
-            const double x = (double)P[r + c * ldp];
-            acc[0] += x * x;
+            const T xv = P[r + c * ldp];
+            ss += (double)xv * (double)xv;
 #pragma unroll
             for (int k = 0; k < NB; ++k)
-                if (k > c && k < nb) acc[1 + k] += x * (double)P[r + k * ldp];
+                if (k > c && k < nb) acc[k] += xv * P[r + k * ldp];
         }
+        {
+            double v[32];
 #pragma unroll
-        for (int q = 0; q <= NB; ++q) {
-            double v = acc[q];
+            for (int q = 0; q < 32; ++q) v[q] = (q < NB) ? (double)acc[q] : 0.0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][q] = v;
+            for (int q = 0; q < 32; ++q)
+                if (q == c) v[q] = ss;
+            red[warp][lane] = warp_reduce_scatter32(v, lane);
         }
         __syncthreads();
-        double *my_part = partials + ((size_t)par * G + blockIdx.x) * (NB + 1);
-        if (threadIdx.x <= NB) {
+        if (threadIdx.x < 32) {
             double v = 0.0;
+#pragma unroll
             for (int w = 0; w < PANEL_WARPS; ++w) v += red[w][threadIdx.x];
-            my_part[threadIdx.x] = v;
+            part[(size_t)threadIdx.x * G + blockIdx.x] = v;
         }
-        // the owner of the diagonal row publishes that row (columns c..nb-1)
         if (jc >= r0 && jc < r1 && threadIdx.x < nb && threadIdx.x >= c)
-            rowbuf[par * NB + threadIdx.x] = (double)P[(jc - r0) + threadIdx.x * ldp];
-        if (!grid_barrier(bar, bar + 1, G, st, 10 + c)) return;
-        // ---- phase 2: every CTA reduces the partials in the same order ----
-        if (threadIdx.x <= NB) {
+            rowbuf[par * 32 + threadIdx.x] = (double)P[(jc - r0) + threadIdx.x * ldp];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();  // orders this CTA's partials and row before the flag
+            *((volatile unsigned *)(flg + blockIdx.x)) = epoch;
+        }
+        // ---- wait until every CTA has published column c (bounded) ----
+        if (warp == 0) {
+            const uint64_t t0 = globaltimer_ns();
+            int ok = 1;
+            uint32_t spins = 0;
+            while (true) {
+                bool mine = true;
+                for (unsigned b = lane; b < G; b += 32)
+                    mine = mine && (*((volatile const unsigned *)(flg + b)) == epoch);
+                if (__all_sync(0xffffffffu, mine)) break;
+                if ((++spins & 63u) == 0) {
+                    int bad = 0;
+                    if (lane == 0) {
+                        if (*((volatile int *)&st->code) != 0) bad = 1;
+                        else if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                            raise_status(st, DEV_TIMEOUT, 10, (int)jc);
+                            bad = 1;
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, bad, 0)) { ok = 0; break; }
+                }
+            }
+            __threadfence();  // orders the flag reads before the reads of the partials
+            if (lane == 0) ok_s = ok;
+        }
+        __syncthreads();
+        if (!ok_s) return;
+        // ---- phase 2: every CTA reduces the G partial vectors in the same order ----
+#pragma unroll
+        for (int qq = 0; qq < 32 / PANEL_WARPS; ++qq) {
+            const int q = warp + PANEL_WARPS * qq;
             double v = 0.0;
-            const double *pp = partials + (size_t)par * G * (NB + 1) + threadIdx.x;
-            for (unsigned b = 0; b < G; ++b) v += __ldcg(pp + (size_t)b * (NB + 1));
-            tot[threadIdx.x] = v;
+            for (unsigned b = lane; b < G; b += 32) v += __ldcg(part + (size_t)q * G + b);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) tot[q] = v;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const double ss = tot[0];
-            const double alpha = __ldcg(rowbuf + par * NB + c);
-            if (!isfinite(ss) || !isfinite(alpha)) raise_status(st, DEV_NONFINITE, 20, (int)jc);
-            if (ss == 0.0) {
+            const double ssum = tot[c];
+            const double alpha = __ldcg(rowbuf + par * 32 + c);
+            if (!isfinite(ssum) || !isfinite(alpha)) raise_status(st, DEV_NONFINITE, 20, (int)jc);
+            if (ssum == 0.0) {
                 skip_s = 1;
                 if (blockIdx.x == 0) tau[jc] = T(0);
             } else {
                 skip_s = 0;
-                const double norm = sqrt(alpha * alpha + ss);
+                const double norm = sqrt(alpha * alpha + ssum);
                 const double beta = (alpha >= 0.0) ? -norm : norm;
                 const double t = (beta - alpha) / beta;
-                const double scale = 1.0 / (alpha - beta);
-                scal_s = scale;
+                scal_s = 1.0 / (alpha - beta);
                 beta_s = beta;
+                tau_s = t;
                 if (blockIdx.x == 0) tau[jc] = (T)t;
-                for (int k = c + 1; k < nb; ++k) {
-                    const double ak = __ldcg(rowbuf + par * NB + k);
-                    coef[k] = t * (ak + scale * tot[1 + k]);
-                    coefs[k] = (T)(coef[k] * scale);
-                }
             }
+        }
+        __syncthreads();
+        if (!skip_s && threadIdx.x > c && threadIdx.x < nb) {
+            const int k = threadIdx.x;
+            coef[k] = tau_s * (__ldcg(rowbuf + par * 32 + k) + scal_s * tot[k]);
+            coefs[k] = (T)(coef[k] * scal_s);
         }
         __syncthreads();
         if (skip_s) continue;
@@ -244,17 +279,21 @@ ct_status panel_launch(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau,
         set_error("panel: cooperative grid %d does not fit (%d per SM)", G, per_sm);
         return CT_ERR_CUDA;
     }
-    // workspace: barrier words | partials [2][G][NB+1] | rowbuf [2][NB]
-    const size_t need = 256 + sizeof(double) * (2 * (size_t)G * (NB + 1) + 2 * NB);
+    // workspace: flags [2][G] | partials [2][32][G] | rowbuf [2][32]
+    const size_t flag_bytes = round_up(sizeof(unsigned) * 2 * G, 256);
+    const size_t need = flag_bytes + sizeof(double) * (2 * 32 * (size_t)G + 2 * 32);
     CT_TRY(ws.ensure(need));
-    unsigned *bar = (unsigned *)ws.ptr;
-    double *partials = (double *)((char *)ws.ptr + 256);
-    double *rowbuf = partials + 2 * (size_t)G * (NB + 1);
-    CT_CUDA(cudaMemsetAsync(bar, 0, 256, s));
+    unsigned *flags = (unsigned *)ws.ptr;
+    double *partials = (double *)((char *)ws.ptr + flag_bytes);
+    double *rowbuf = partials + 2 * 32 * (size_t)G;
+    CT_CUDA(cudaMemsetAsync(flags, 0, flag_bytes, s));
     DevStatus *st = device_status();
-    void *args[] = {&A, &lda, &M, &j0, &nb, &tau, &partials, &rowbuf, &bar, &st, &rows_per,
+    void *args[] = {&A, &lda, &M, &j0, &nb, &tau, &partials, &rowbuf, &flags, &st, &rows_per,
                     (void *)&use_smem};
+    ProfScope prof(PROF_PANEL, s, 2.0 * rows * nb * nb, 2.0 * sizeof(T) * rows * nb, rows, nb, G,
+                   use_smem);
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(PANEL_THREADS), args, dyn, s));
+    count_launch();
     return CT_OK;
 }
 
@@ -274,10 +313,14 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
 ct_status extract_vtop(bool fp64, const void *A, int64_t lda, int64_t j0, int nb, void *Vtop,
                        int64_t ldv, cudaStream_t s) {
     dim3 grid((unsigned)ceil_div(nb, 128), (unsigned)nb);
-    if (fp64)
+    if (fp64) {
         extract_vtop_kernel<double><<<grid, 128, 0, s>>>((const double *)A, lda, j0, nb, (double *)Vtop, ldv);
-    else
+        count_launch();
+    }
+    else {
         extract_vtop_kernel<float><<<grid, 128, 0, s>>>((const float *)A, lda, j0, nb, (float *)Vtop, ldv);
+        count_launch();
+    }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -286,12 +329,16 @@ ct_status larft_from_gram(bool fp64, int nb, const void *G, int64_t ldg, const v
                           int64_t ldt, cudaStream_t s) {
     const int threads = std::min(1024, std::max(32, nb));
     const size_t smem = sizeof(double) * nb;
-    if (fp64)
+    if (fp64) {
         larft_kernel<double><<<1, threads, smem, s>>>(nb, (const double *)G, ldg,
                                                       (const double *)tau, (double *)T, ldt);
-    else
+        count_launch();
+    }
+    else {
         larft_kernel<float><<<1, threads, smem, s>>>(nb, (const float *)G, ldg, (const float *)tau,
                                                      (float *)T, ldt);
+        count_launch();
+    }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }

@@ -91,30 +91,47 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
     const size_t es = f->es();
     const int64_t NB = f->NB, nb = f->nb, n = f->n, M = f->M, lda = f->lda;
     CT_TRY(f->G.ensure(es * (size_t)NB * NB));
-    // misc: Vt_p | T_p for inner panels (ld NB)
+    // misc: Vt_p (ld NB) for inner panels | Y (ld NB) for the T assembly
     CT_TRY(f->misc.ensure(2 * es * (size_t)NB * NB));
     void *Vtp = f->misc.ptr;
-    void *Tp = (char *)f->misc.ptr + es * (size_t)NB * NB;
+    void *Y = (char *)f->misc.ptr + es * (size_t)NB * NB;
+    const GemmKind small_kind = f->fp64 ? GEMM_F64 : GEMM_F32;
     for (int64_t J = 0; J < f->nblocks; ++J) {
         const int64_t j = J * NB;
         const int w = (int)std::min<int64_t>(NB, n - j);
+        void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
+        void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
+        CT_CUDA(cudaMemsetAsync(TJ, 0, es * (size_t)NB * NB, s));
         for (int64_t p = j; p < j + w; p += nb) {
             const int wp = (int)std::min<int64_t>(nb, j + w - p);
             CT_TRY(panel_qr(f->fp64, f->VR, lda, M, p, wp, f->tau, f->panel_ws, s));
+            // T_p of this panel goes straight into its diagonal block of T_J.
+            void *Tp = at(TJ, p - j, p - j, NB, es);
+            CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
+            CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
+            CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
             const int64_t ncols_in = j + w - (p + wp);
-            if (ncols_in > 0) {
-                CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
-                CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
-                CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
+            if (ncols_in > 0)
                 CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,
                                    ncols_in, s));
+        }
+        CT_TRY(extract_vtop(f->fp64, f->VR, lda, j, w, VtJ, NB, s));
+        if (w > nb) {
+            // T_J from the panels' T_p:  for the next panel at offset o,
+            //   T_J[0:o, o:o+wp] = -T_J[0:o, 0:o] * (V_J[:, 0:o]^T V_p) * T_p,
+            // the off-diagonal block of the product of two block reflectors.
+            CT_TRY(gram(f, j, w, VtJ, f->G.ptr, s));
+            for (int64_t o = nb; o < w; o += nb) {
+                const int64_t wp = std::min<int64_t>(nb, w - o);
+                const void *Tp = at(TJ, o, o, NB, es);
+                GemmArgs g1{small_kind, false, false, o, wp, wp, 1.0, at(f->G.ptr, 0, o, NB, es), NB,
+                            Tp, NB, 0.0, Y, NB};
+                CT_TRY(gemm(g1, f->gemm_ws, s));
+                GemmArgs g2{small_kind, false, false, o, wp, o, -1.0, TJ, NB, Y, NB, 0.0,
+                            at(TJ, 0, o, NB, es), NB};
+                CT_TRY(gemm(g2, f->gemm_ws, s));
             }
         }
-        void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
-        void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
-        CT_TRY(extract_vtop(f->fp64, f->VR, lda, j, w, VtJ, NB, s));
-        CT_TRY(gram(f, j, w, VtJ, f->G.ptr, s));
-        CT_TRY(larft_from_gram(f->fp64, w, f->G.ptr, NB, (char *)f->tau + es * j, TJ, NB, s));
         if (j + w < n)
             CT_TRY(apply_block(f, j, w, VtJ, TJ, true, at(f->VR, j, j + w, lda, es), lda, n - j - w, s));
     }

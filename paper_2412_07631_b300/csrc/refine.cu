@@ -94,7 +94,9 @@ static ct_status coldot(int64_t rows, int64_t k, const double *U, const double *
                         double *out, cudaStream_t s) {
     const int64_t nblk = ceil_div(rows, RB);
     coldot_partial<<<(unsigned)nblk, 128, 0, s>>>(rows, k, U, V, part);
+    count_launch();
     coldot_final<<<(unsigned)ceil_div(k, 128), 128, 0, s>>>(nblk, k, part, out);
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -106,7 +108,7 @@ static ct_status apply_rinv(ct_factor f, bool trans, const double *u, double *t,
     const int64_t n = f->n, ldl = round_up(n, 32);
     const int dk = f->fp64 ? 1 : 0;
     CT_TRY(transpose_any(1, u, k, dk, lp, ldl, k, n, s));  // (k x n row view) -> n x k col-major
-    CT_TRY(trsm_upper(f->kind, trans, n, k, f->VR, f->lda, lp, ldl, f->trsm_ws, s));
+    CT_TRY(trsm_factor(f, trans, lp, ldl, k, s));
     return transpose_any(dk, lp, ldl, 1, t, k, n, k, s);   // n x k col-major -> row-major
 }
 
@@ -164,15 +166,19 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         CT_TRY(spmm_ax(S, k, w.t, 0.0, nullptr, 1.0, w.q, st));    // q = A~ t
         CT_TRY(coldot(M, k, w.q, w.q, w.part, qq, st));
         step_scalars<<<bk, 128, 0, st>>>(k, gamma, qq, alpha);
+        count_launch();
         axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, 1.0, w.t, w.x);                       // x += a t
         axpy_cols<<<(unsigned)ceil_div((int64_t)Mk, 256), 256, 0, st>>>(M, k, alpha, -1.0, w.q, w.r);  // r -= a q
         CT_TRY(coldot(n, k, w.t, w.t, w.part, tt, st));
+        count_launch();
         CT_TRY(coldot(n, k, w.x, w.x, w.part, xx, st));
         CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));   // t = A~^T r (reuse)
         CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));        // s = R^-T t
         CT_TRY(coldot(n, k, w.s, w.s, w.part, gnew, st));
         beta_scalars<<<bk, 128, 0, st>>>(k, gnew, gamma, beta);
+        count_launch();
         xpby_cols<<<bn, 256, 0, st>>>(n, k, w.s, beta, w.p);
+        count_launch();
         CT_CUDA(cudaGetLastError());
         CT_CUDA(cudaMemcpyAsync(h_tt.data(), tt, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CT_CUDA(cudaMemcpyAsync(h_xx.data(), xx, sizeof(double) * k, cudaMemcpyDeviceToHost, st));

@@ -296,8 +296,11 @@ ct_status exclusive_scan(const int32_t *in, int64_t n, int64_t *out_np1, Scratch
     int64_t *bs = (int64_t *)tmp.ptr;
     int64_t *total = bs + nb;
     scan_block_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, out_np1, bs);
+    count_launch();
     scan_top_kernel<<<1, kScanBlock, 0, s>>>(bs, nb, total);
+    count_launch();
     scan_add_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(out_np1, n, bs, total);
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -307,7 +310,9 @@ ct_status siddon_build(const SiddonArgs &a, cudaStream_t s) {
     const int m = a.n_views * a.n_bins;
     const int threads = 128;
     const unsigned blocks = (unsigned)ceil_div(m, threads);
+    ProfScope prof(PROF_SIDDON, s, 0.0, 4.0 * m);
     siddon_count_kernel<<<blocks, threads, 0, s>>>(g, a.d_cs, a.d_row_nnz);
+    count_launch();
     CT_CUDA(cudaGetLastError());
     CT_TRY(exclusive_scan(a.d_row_nnz, m, a.d_row_ptr, *a.tmp, s));
     return CT_OK;
@@ -323,15 +328,21 @@ ct_status siddon_fill(const SiddonArgs &a, void *dense, bool dense_fp64, int64_t
     if (dense_fp64) {
         siddon_fill_kernel<double><<<blocks, threads, 0, s>>>(g, a.d_cs, a.d_row_ptr, a.d_col,
                                                               a.d_val, (double *)dense, lda);
-        if (dense && a.sqrt_lambda > 0)
+        count_launch();
+        if (dense && a.sqrt_lambda > 0) {
             lambda_rows_kernel<double><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(
                 (double *)dense, lda, m, n, a.sqrt_lambda);
+            count_launch();
+        }
     } else {
         siddon_fill_kernel<float><<<blocks, threads, 0, s>>>(g, a.d_cs, a.d_row_ptr, a.d_col,
                                                              a.d_val, (float *)dense, lda);
-        if (dense && a.sqrt_lambda > 0)
+        count_launch();
+        if (dense && a.sqrt_lambda > 0) {
             lambda_rows_kernel<float><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(
                 (float *)dense, lda, m, n, a.sqrt_lambda);
+            count_launch();
+        }
     }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -350,16 +361,22 @@ ct_status build_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
     int32_t *col_cnt = (int32_t *)(base + off_cnt);
     int64_t *slot = (int64_t *)(base + off_slot);
     row_of_entry_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(row_ptr, m, row_of);
+    count_launch();
     CT_CUDA(cudaMemsetAsync(col_cnt, 0, sizeof(int32_t) * n, s));
-    if (nnz > 0)
+    if (nnz > 0) {
         col_count_kernel<<<(unsigned)ceil_div(nnz, 256), 256, 0, s>>>(col_idx, nnz, col_cnt);
+        count_launch();
+    }
     CT_TRY(exclusive_scan(col_cnt, n, col_ptr, tmp2, s));
     CT_CUDA(cudaMemsetAsync(col_cnt, 0, sizeof(int32_t) * n, s));
-    if (nnz > 0)
+    if (nnz > 0) {
         csc_place_kernel<<<(unsigned)ceil_div(nnz, 256), 256, 0, s>>>(col_idx, nnz, col_ptr,
                                                                        col_cnt, slot);
+        count_launch();
+    }
     csc_sort_kernel<<<(unsigned)n, 256, 0, s>>>(col_ptr, slot, row_of, val, csc_row, csc_val,
                                                 device_status());
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }

@@ -19,7 +19,7 @@ inline int fac_kind(ct_factor f) { return f->fp64 ? 1 : 0; }
 static ct_status direct_solve_inplace(ct_factor f, void *Bt, int64_t ldbt, int64_t k,
                                       cudaStream_t s) {
     CT_TRY(apply_q_blocks(f, true, Bt, ldbt, k, s));
-    return trsm_upper(f->kind, false, f->n, k, f->VR, f->lda, Bt, ldbt, f->trsm_ws, s);
+    return trsm_factor(f, false, Bt, ldbt, k, s);
 }
 
 ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
@@ -53,7 +53,7 @@ ct_status adjoint_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void
     void *Bt = f->Bt.ptr;
     CT_TRY(copy_convert_2d(io_kind(f), gX, ldgx, fac_kind(f), Bt, ldbt, n, k, s));
     if (M > n) CT_TRY(fill_zero_2d(f->fp64, (char *)Bt + f->es() * n, ldbt, M - n, k, s));
-    CT_TRY(trsm_upper(f->kind, true, n, k, f->VR, f->lda, Bt, ldbt, f->trsm_ws, s));
+    CT_TRY(trsm_factor(f, true, Bt, ldbt, k, s));
     CT_TRY(apply_q_blocks(f, false, Bt, ldbt, k, s));
     CT_TRY(copy_convert_2d(fac_kind(f), Bt, ldbt, io_kind(f), gB, ldgb, m, k, s));
     if (info) {

@@ -100,8 +100,11 @@ ct_status spmm_ax(const SparseSys &S, int64_t k, const double *X, double alpha, 
     const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
     if (rows == 0 || k == 0) return CT_OK;
     const unsigned blocks = (unsigned)ceil_div(rows * 32, 256);
+    ProfScope prof(PROF_SPMM, s, 2.0 * (S.nnz + (rows - S.m)) * k,
+                   12.0 * S.nnz + 8.0 * (double)k * (S.n + rows * (alpha != 0.0 ? 2 : 1)));
     spmm_ax_kernel<<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.row_ptr, S.col, S.val, X,
                                           alpha, Y, beta, out);
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -110,8 +113,12 @@ ct_status spmm_atr(const SparseSys &S, int64_t k, const double *R, double alpha,
                    double beta, double *out, cudaStream_t s) {
     if (S.n == 0 || k == 0) return CT_OK;
     const unsigned blocks = (unsigned)ceil_div(S.n * 32, 256);
+    const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
+    ProfScope prof(PROF_SPMM, s, 2.0 * (S.nnz + (rows - S.m)) * k,
+                   12.0 * S.nnz + 8.0 * (double)k * (rows + S.n * (alpha != 0.0 ? 2 : 1)));
     spmm_atr_kernel<<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.col_ptr, S.csc_row,
                                            S.csc_val, R, alpha, Y, beta, out);
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }

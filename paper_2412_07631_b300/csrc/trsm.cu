@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "handles.cuh"
 #include "kernels.cuh"
 
 namespace ctqr {
@@ -68,12 +69,163 @@ ct_status diag_solve(bool trans, int ni, const T *R, int64_t ldr, T *C, int64_t 
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
+    ProfScope prof(PROF_TRSM_DIAG, s, (double)ni * ni * k, sizeof(T) * ((double)ni * ni + 2.0 * ni * k));
     diag_solve_kernel<T, BS><<<(unsigned)ceil_div(k, KC), KC, smem, s>>>(trans, ni, R, ldr, C, ldc, k);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+// One CTA per diagonal block b: Rinv_b = R_bb^-1 (TB x TB, zero-padded past
+// the ragged last block), by back-substitution of the identity columns, one
+// thread per column; also writes the transpose.
+template <typename T, int TB>
+__global__ void __launch_bounds__(TB) diag_inverse_kernel(int64_t n, const T *R, int64_t ldr,
+                                                          T *Rinv, T *RinvT) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    T *Rs = (T *)dsm;         // [TB][TB] column-major
+    T *Xs = Rs + TB * TB;     // [TB][TB+1], row r at Xs[r*(TB+1)]
+    const int64_t i0 = (int64_t)blockIdx.x * TB;
+    const int ni = (int)((n - i0 < TB) ? (n - i0) : TB);
+    const T *Rb = R + i0 + i0 * ldr;
+    for (int idx = threadIdx.x; idx < TB * TB; idx += TB) {
+        int r = idx % TB, c = idx / TB;
+        Rs[r + c * TB] = (r < ni && c < ni) ? Rb[r + c * ldr] : T(0);
+        Xs[r * (TB + 1) + c] = (r == c && r < ni) ? T(1) : T(0);
+    }
+    __syncthreads();
+    const int s = threadIdx.x;
+    if (s < ni) {
+        for (int l = ni - 1; l >= 0; --l) {
+            T xl = Xs[l * (TB + 1) + s] / Rs[l + l * TB];
+            Xs[l * (TB + 1) + s] = xl;
+            for (int r = 0; r < l; ++r) Xs[r * (TB + 1) + s] -= Rs[r + l * TB] * xl;
+        }
+    }
+    __syncthreads();
+    T *Ib = Rinv + (size_t)blockIdx.x * TB * TB;
+    T *It = RinvT + (size_t)blockIdx.x * TB * TB;
+    for (int idx = threadIdx.x; idx < TB * TB; idx += TB) {
+        int r = idx % TB, c = idx / TB;
+        Ib[r + c * TB] = Xs[r * (TB + 1) + c];
+        It[c + r * TB] = Xs[r * (TB + 1) + c];
+    }
+}
+
+template <typename T, int TB>
+ct_status diag_inverse_launch(int64_t n, const T *R, int64_t ldr, T *Rinv, T *RinvT, cudaStream_t s) {
+    const size_t smem = sizeof(T) * ((size_t)TB * TB + (size_t)TB * (TB + 1));
+    static bool attr = false;
+    if (!attr) {
+        CT_CUDA(cudaFuncSetAttribute(diag_inverse_kernel<T, TB>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    diag_inverse_kernel<T, TB><<<(unsigned)ceil_div(n, TB), TB, smem, s>>>(n, R, ldr, Rinv, RinvT);
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
 
 }  // namespace
+
+// Inverse diagonal blocks of R (and, for the tensor-core path, R^T), built once
+// per factor on first use.
+ct_status trsm_prepare(ct_factor f, cudaStream_t s) {
+    if (f->Rinv) return CT_OK;
+    const size_t es = f->es();
+    const int TB = f->fp64 ? 64 : 128;
+    const int64_t nbt = ceil_div(f->n, TB);
+    CT_CUDA(cudaMalloc(&f->Rinv, es * (size_t)nbt * TB * TB));
+    CT_CUDA(cudaMalloc(&f->RinvT, es * (size_t)nbt * TB * TB));
+    f->trsm_tb = TB;
+    if (f->fp64)
+        CT_TRY((diag_inverse_launch<double, 64>(f->n, (const double *)f->VR, f->lda,
+                                                (double *)f->Rinv, (double *)f->RinvT, s)));
+    else
+        CT_TRY((diag_inverse_launch<float, 128>(f->n, (const float *)f->VR, f->lda,
+                                                (float *)f->Rinv, (float *)f->RinvT, s)));
+    if (f->kind == GEMM_TF32 || f->kind == GEMM_BF16) {
+        f->ldrt = round_up(f->n, 32);
+        CT_CUDA(cudaMalloc(&f->Rt, es * (size_t)f->ldrt * f->n));
+        CT_TRY(transpose_any(0, f->VR, f->lda, 0, f->Rt, f->ldrt, f->n, f->n, s));
+    }
+    return CT_OK;
+}
+
+// R X = C (trans = false) or R^T X = C (trans = true) in place, C: n x k (ldc).
+// Block step:  X_i = R_ii^-1 C_i  (GEMM with the stored inverse block), then
+// the off-diagonal update C_{0:i} -= R_{0:i,i} X_i  (or, transposed,
+// C_{i+1:} -= R_{i,i+1:}^T X_i).  Every product is an op(A) = A^T GEMM, the
+// form the tensor cores take directly.
+ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, cudaStream_t s) {
+    const int64_t n = f->n;
+    if (n == 0 || k == 0) return CT_OK;
+    CT_TRY(trsm_prepare(f, s));
+    const size_t es = f->es();
+    const int TB = f->trsm_tb;
+    const int64_t nblk = ceil_div(n, TB);
+    CT_TRY(f->misc2.ensure(es * (size_t)TB * k));
+    void *tmp = f->misc2.ptr;
+    const bool tc = f->kind == GEMM_TF32 || f->kind == GEMM_BF16;
+    auto Cp = [&](int64_t i) { return (char *)C + es * i; };
+    for (int64_t t = 0; t < nblk; ++t) {
+        const int64_t ib = trans ? t : nblk - 1 - t;
+        const int64_t i0 = ib * TB;
+        const int ni = (int)std::min<int64_t>(TB, n - i0);
+        CT_CUDA(cudaMemcpy2DAsync(tmp, es * TB, Cp(i0), es * ldc, es * ni, k,
+                                  cudaMemcpyDeviceToDevice, s));
+        GemmArgs d{};
+        d.kind = f->kind;
+        d.M = ni;
+        d.N = k;
+        d.K = ni;
+        d.alpha = 1.0;
+        d.beta = 0.0;
+        d.B = tmp;
+        d.ldb = TB;
+        d.C = Cp(i0);
+        d.ldc = ldc;
+        d.lda = TB;
+        d.tb = false;
+        // op(A) = R_ii^-1 = (RinvT_i)^T, or R_ii^-T = (Rinv_i)^T
+        d.ta = true;
+        d.A = (char *)(trans ? f->Rinv : f->RinvT) + es * (size_t)ib * TB * TB;
+        CT_TRY(gemm(d, f->trsm_ws, s));
+        GemmArgs g{};
+        g.kind = f->kind;
+        g.alpha = -1.0;
+        g.beta = 1.0;
+        g.N = k;
+        g.K = ni;
+        g.B = Cp(i0);
+        g.ldb = ldc;
+        g.ldc = ldc;
+        if (!trans) {
+            if (i0 == 0) continue;
+            g.M = i0;
+            g.C = Cp(0);
+            if (tc) {  // R_{0:i0, i0:i0+ni} = (Rt[i0:i0+ni, 0:i0])^T
+                g.ta = true;
+                g.A = (char *)f->Rt + es * (size_t)i0;
+                g.lda = f->ldrt;
+            } else {
+                g.ta = false;
+                g.A = (char *)f->VR + es * (size_t)(i0 * f->lda);
+                g.lda = f->lda;
+            }
+        } else {
+            if (i0 + ni >= n) continue;
+            g.ta = true;
+            g.M = n - i0 - ni;
+            g.A = (char *)f->VR + es * (size_t)(i0 + (i0 + ni) * f->lda);
+            g.lda = f->lda;
+            g.C = Cp(i0 + ni);
+        }
+        CT_TRY(gemm(g, f->trsm_ws, s));
+    }
+    return CT_OK;
+}
 
 ct_status trsm_upper(GemmKind kind, bool trans, int64_t n, int64_t k, const void *R, int64_t ldr,
                      void *C, int64_t ldc, Scratch &ws, cudaStream_t s) {

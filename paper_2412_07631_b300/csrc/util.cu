@@ -76,14 +76,22 @@ ct_status transpose_any(int src_kind, const void *src, int64_t lds, int dst_kind
                         int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
     if (rows == 0 || cols == 0) return CT_OK;
     dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32)), block(32, 8);
-    if (src_kind == 1 && dst_kind == 1)
+    if (src_kind == 1 && dst_kind == 1) {
         transpose_kernel<double, double><<<grid, block, 0, s>>>((const double *)src, lds, (double *)dst, ldd, rows, cols);
-    else if (src_kind == 1 && dst_kind == 0)
+        count_launch();
+    }
+    else if (src_kind == 1 && dst_kind == 0) {
         transpose_kernel<double, float><<<grid, block, 0, s>>>((const double *)src, lds, (float *)dst, ldd, rows, cols);
-    else if (src_kind == 0 && dst_kind == 1)
+        count_launch();
+    }
+    else if (src_kind == 0 && dst_kind == 1) {
         transpose_kernel<float, double><<<grid, block, 0, s>>>((const float *)src, lds, (double *)dst, ldd, rows, cols);
-    else
+        count_launch();
+    }
+    else {
         transpose_kernel<float, float><<<grid, block, 0, s>>>((const float *)src, lds, (float *)dst, ldd, rows, cols);
+        count_launch();
+    }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -98,14 +106,22 @@ ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_ki
     const int64_t total = rows * cols;
     if (total == 0) return CT_OK;
     const unsigned b = (unsigned)ceil_div(total, 256);
-    if (src_kind == 0 && dst_kind == 0)
+    if (src_kind == 0 && dst_kind == 0) {
         copy_convert_kernel<float, float><<<b, 256, 0, s>>>((const float *)src, lds, (float *)dst, ldd, rows, cols);
-    else if (src_kind == 0 && dst_kind == 1)
+        count_launch();
+    }
+    else if (src_kind == 0 && dst_kind == 1) {
         copy_convert_kernel<float, double><<<b, 256, 0, s>>>((const float *)src, lds, (double *)dst, ldd, rows, cols);
-    else if (src_kind == 1 && dst_kind == 0)
+        count_launch();
+    }
+    else if (src_kind == 1 && dst_kind == 0) {
         copy_convert_kernel<double, float><<<b, 256, 0, s>>>((const double *)src, lds, (float *)dst, ldd, rows, cols);
-    else
+        count_launch();
+    }
+    else {
         copy_convert_kernel<double, double><<<b, 256, 0, s>>>((const double *)src, lds, (double *)dst, ldd, rows, cols);
+        count_launch();
+    }
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -117,6 +133,7 @@ ct_status fill_zero_2d(bool fp64, void *dst, int64_t ld, int64_t rows, int64_t c
     const unsigned b = (unsigned)ceil_div(total, 256);
     if (fp64) fill_zero_kernel<double><<<b, 256, 0, s>>>((double *)dst, ld, rows, cols);
     else fill_zero_kernel<float><<<b, 256, 0, s>>>((float *)dst, ld, rows, cols);
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -125,6 +142,7 @@ ct_status rdiag_minmax(bool fp64, const void *A, int64_t lda, int64_t n, double 
                        cudaStream_t s) {
     if (fp64) rdiag_minmax_kernel<double><<<1, 256, 0, s>>>((const double *)A, lda, n, out, device_status());
     else rdiag_minmax_kernel<float><<<1, 256, 0, s>>>((const float *)A, lda, n, out, device_status());
+    count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }

@@ -1,29 +1,35 @@
 """The 128 x 128 workload (180 views x 182 bins + sqrt(lambda) I rows,
 sqrt(lambda) = 0.05; M' = 49,144 rows, n = 16,384 unknowns) solved on the GPU
-and compared slice by slice with the paper's in-core route on the host: the
-three LAPACK calls dgeqrf, dormqr, dtrtrs of Sec. 2.1 (oracle), on the same
-noisy sinograms.  FP64 path <= 1e-10, plain FP32 <= 1e-4, TF32 factors with
-FP64 refinement <= 1e-6 (relative image error)."""
+and compared slice by slice with the paper's in-core route (the three LAPACK
+calls dgeqrf, dormqr, dtrtrs of Sec. 2.1) run by the oracle on the same noisy
+sinograms.  The oracle's solution is stored in tests/golden/c2_xref.npz by
+tests/golden/make_c2_reference.py (oracle only); the test regenerates the
+seeded inputs and checks their digest against the stored one.
+FP64 path <= 1e-10, plain FP32 <= 1e-4, TF32 factors with FP64 refinement
+<= 1e-6 (relative image error)."""
+import os
+
 import numpy as np
 import pytest
 
 from gpu_util import need_cuda, rel_err_cols
-from paper_2412_07631_b300 import synth
 
-NS, NV, NB, SL, K = 128, 180, 182, 0.05, 16
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys_path_golden = os.path.join(HERE, "golden")
 
 
 @pytest.fixture(scope="module")
-def c2_case(oracle_mod):
-    O = oracle_mod
-    g = O.Geometry(NS, NV, NB, sqrt_lambda=SL)
-    csr = O.siddon_csr(g)
-    X = synth.phantom_batch(NS, K, 10)
-    B = synth.poisson_sinogram(O.forward(csr, X), NS, 1e4, seed=4321)
-    A = O.dense_system(g, csr)
-    Xo, R = O.lapack_qr_solve(g, A, B, overwrite=True)
-    del A
-    return g, csr, X, B, Xo
+def c2_case():
+    import sys
+    sys.path.insert(0, sys_path_golden)
+    import make_c2_reference as ref
+    path = os.path.join(sys_path_golden, "c2_xref.npz")
+    if not os.path.exists(path):
+        pytest.fail("tests/golden/c2_xref.npz missing: run tests/golden/make_c2_reference.py")
+    g, csr, X, B = ref.inputs()
+    d = np.load(path)
+    assert str(d["b_sha256"]) == ref.digest(B), "seeded inputs changed since the golden was written"
+    return ref, B, d["xref"]
 
 
 @pytest.mark.gpu
@@ -31,9 +37,9 @@ def c2_case(oracle_mod):
 def test_c2_against_lapack_oracle(c2_case, precision, tol):
     torch = need_cuda()
     import paper_2412_07631_b300 as ct
-    g, csr, X, B, Xo = c2_case
+    ref, B, Xo = c2_case
     storage = "fp64" if precision == "fp64" else "fp32"
-    sysg = ct.System(ct.make_geometry(NS, NV, NB, SL), storage)
+    sysg = ct.System(ct.make_geometry(ref.NS, ref.NV, ref.NB, ref.SL), storage)
     F = sysg.factor(precision)
     dt = torch.float32 if precision == "fp32" else torch.float64
     Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(dt).cuda()
