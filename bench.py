@@ -162,7 +162,7 @@ def cpu_oracle_sample(name, cols=None):
     ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
     g = O.Geometry(ns, nv, nb, sqrt_lambda=sl)
     n = g.n
-    w = cols or min(n, 160)
+    w = cols or min(n, 512)
     csr = O.siddon_csr(g)
     S = csr.to_scipy()
     A = np.zeros((g.rows, w), order="F")
