@@ -237,6 +237,27 @@ CT_API ct_status ct_gemm(int32_t kind, char transa, char transb, int64_t M, int6
                   double alpha, const void *A, int64_t lda, const void *B, int64_t ldb,
                   double beta, void *C, int64_t ldc, void *stream);
 
+/* ct_gemm for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ * ct_gemm keeps split-K partial products and K-major operand copies in
+ * scratch the library allocates; a caller whose device memory all belongs to
+ * its own pool, or that must not allocate at run time (cudaMalloc can fail
+ * under memory pressure and synchronises the device), uses this variant
+ * instead: same arguments, same kernels, same results within rounding, and
+ * the scratch is one fixed 16 MiB array in the library's static device
+ * memory, held by every GPU that loads the library until the process exits.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.
+ * A product whose K-major operand copies would not fit in the array is
+ * refused with CT_ERR_ARG (ct_last_error says how much it needs); split-K
+ * depth is reduced to what fits.  kind 3 (BF16) is not offered.
+ * Synchronises `stream` before returning. */
+CT_API ct_status ct_gemm_noalloc(int32_t kind, char transa, char transb, int64_t M, int64_t N,
+                                 int64_t K, double alpha, const void *A, int64_t lda,
+                                 const void *B, int64_t ldb, double beta, void *C, int64_t ldc,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

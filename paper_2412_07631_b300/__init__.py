@@ -52,7 +52,7 @@ SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info"
            "ct_system_device_ptrs", "ct_system_export", "ct_forward_project", "ct_qr_factor",
            "ct_factor_device_ptrs", "ct_factor_export", "ct_solve", "ct_solve_host",
            "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm", "ct_stats_reset",
-           "ct_stats_read", "ct_stats_dump"]
+           "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc"]
 
 
 def lib_path() -> str:
@@ -87,6 +87,7 @@ def lib():
     L.ct_factor_free.restype = None
     L.ct_gemm.argtypes = [I32, C.c_char, C.c_char, I64, I64, I64, C.c_double, vp, I64, vp, I64,
                           C.c_double, vp, I64, vp]
+    L.ct_gemm_noalloc.argtypes = list(L.ct_gemm.argtypes)
     L.ct_stats_reset.argtypes = [I32]
     L.ct_stats_read.argtypes = [C.POINTER(I64), vp, vp, vp, vp]
     L.ct_stats_dump.argtypes = [C.c_char_p]

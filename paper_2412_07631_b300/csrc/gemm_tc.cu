@@ -316,4 +316,28 @@ ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t 
     return CT_OK;
 }
 
+// Same kernel and tile choice as gemm_tc_launch, with the status word given by
+// the caller and no accounting scope; used by the allocation-free entry point.
+ct_status gemm_tc_launch_status(const GemmArgs &g, int splits, int64_t kchunk,
+                                int64_t split_stride, DevStatus *status, cudaStream_t s) {
+    if (g.kind != GEMM_TF32 || !g.ta || g.tb) return CT_ERR_ARG;
+    static bool attr_set_nb = false;
+    if (!attr_set_nb) {
+        CT_CUDA(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_BYTES));
+        attr_set_nb = true;
+    }
+    CUtensorMap ma, mb;
+    CT_TRY(make_map(&ma, g.A, g.K, g.M, g.lda, BK, BM));
+    CT_TRY(make_map(&mb, g.B, g.K, g.N, g.ldb, BK, BN));
+    const int64_t work = ceil_div(g.M, BM) * ceil_div(g.N, BN) * splits;
+    dim3 grid((unsigned)std::min<int64_t>(work, num_sms()));
+    gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(
+        ma, mb, g.M, g.N, g.K, kchunk, splits, (float)g.alpha, (float)g.beta,
+        (float *)g.C, g.ldc, split_stride, status);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
 }  // namespace ctqr

@@ -52,6 +52,9 @@ ct_status gemm_simt_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_
                            cudaStream_t s);
 ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
                          cudaStream_t s);
+// As gemm_tc_launch, with an explicit device status word and no accounting.
+ct_status gemm_tc_launch_status(const GemmArgs &g, int splits, int64_t kchunk,
+                                int64_t split_stride, DevStatus *status, cudaStream_t s);
 // C = alpha * sum_z P[z] + beta * C  (P: splits x (M x N) packed, ld = M)
 ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void *P, double alpha,
                         double beta, void *C, int64_t ldc, cudaStream_t s);
