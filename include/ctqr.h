@@ -89,15 +89,17 @@ typedef struct {
 
 typedef struct {
     ct_precision precision;
-    int32_t refine_max_iter; /* refinement step limit (<= 0: 10) */
-    double refine_tol;       /* stop when max_s ||dx_s||/||x_s|| <= tol (<= 0: 1e-7) */
+    int32_t refine_max_iter; /* refinement step limit (0: 10; < 0: no refinement) */
+    double refine_tol;       /* refinement stop (<= 0: 1e-7): with sqrt_lambda > 0, the certified
+                                bound max_s ||A~^T r_s|| / (lambda ||x_s||) >= ||x_s - x*_s||/||x_s||;
+                                without, the relative update max_s ||dx_s||/||x_s|| */
     int32_t nb_outer;        /* outer WY block width (0: automatic) */
     int32_t nb_inner;        /* panel width (0: automatic) */
 } ct_opts;
 
 typedef struct {
     int32_t iterations;       /* refinement steps taken (0 for CT_FP64 / CT_FP32) */
-    double last_rel_update;   /* max over slices of ||dx||/||x|| in the last step */
+    double stop_measure;      /* the stopping quantity (see refine_tol) after the last step */
     double rjj_min_abs;       /* min |R_jj| */
     double rjj_max_abs;       /* max |R_jj| */
 } ct_solve_info;
@@ -179,7 +181,7 @@ CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau)
  * ldx >= n.  Element type: float for a CT_FP32 factor, double otherwise.
  * For refining factors, FP64 iterative refinement follows the first solve
  * (residual and update in FP64, corrections from the low-precision factors)
- * until the relative update is below opts->refine_tol or refine_max_iter
+ * until the stopping quantity of opts->refine_tol is met or refine_max_iter
  * steps.  opts may be NULL (factor's precision, defaults).  info may be NULL.
  * Synchronises `stream` at the end (to read the convergence state).
  * Errors: CT_ERR_ARG, CT_ERR_NOCONV (X still holds the best iterate),

@@ -33,7 +33,7 @@ class Opts(C.Structure):
 
 
 class SolveInfo(C.Structure):
-    _fields_ = [("iterations", C.c_int32), ("last_rel_update", C.c_double),
+    _fields_ = [("iterations", C.c_int32), ("stop_measure", C.c_double),
                 ("rjj_min_abs", C.c_double), ("rjj_max_abs", C.c_double)]
 
     def as_dict(self):

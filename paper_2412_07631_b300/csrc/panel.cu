@@ -7,9 +7,9 @@
 // the whole panel when it fits.  For column c (global jc = j0 + c) every CTA
 // accumulates, over its rows below the diagonal, the FP64 sum of squares of
 // the column and the dot products of the column with the panel columns to its
-// right (FP64 from the warp level up); one flag-based exchange publishes the
-// G partial vectors, and every CTA reduces them in the same order (identical
-// reflector everywhere).
+// right (storage type); one flag-based exchange publishes the G partial
+// vectors, and every CTA reduces them in the same order (identical reflector
+// everywhere).
 // With alpha = A[jc, jc]:
 //     beta = -sign(alpha) * sqrt(alpha^2 + ss),  tau = (beta - alpha)/beta,
 //     v = [1; x/(alpha - beta)],  and for each column k to the right
@@ -31,41 +31,56 @@ constexpr int PANEL_WARPS = PANEL_THREADS / 32;
 
 // Reduce-scatter over a warp: on entry every lane holds 32 values; on exit
 // lane l returns the warp-wide sum of value l (31 shuffles in all).
-__device__ __forceinline__ double warp_reduce_scatter32(double (&v)[32], int lane) {
+template <typename D>
+__device__ __forceinline__ D warp_reduce_scatter32(D (&v)[32], int lane) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         const bool upper = (lane & o) != 0;
 #pragma unroll
         for (int i = 0; i < o; ++i) {
-            const double send = upper ? v[i] : v[i + o];
-            const double keep = upper ? v[i + o] : v[i];
+            const D send = upper ? v[i] : v[i + o];
+            const D keep = upper ? v[i + o] : v[i];
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
     return v[0];
 }
 
-// Exchange area (global): flags[2][G] epoch words, partials[2][32][G] doubles,
-// rowbuf[2][32] doubles; index [c & 1] alternates between columns.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Exchange area (global): flags[2][G] epoch words; sums of squares
+// ssq[2][G] (FP64); dot products dots[2][32][G] (storage type); the
+// diagonal row rowbuf[2][32] (FP64).  Index [c & 1] alternates between
+// columns.
 //
-// Per column c (jc = j0 + c) each CTA forms 32 partial sums over its rows
-// strictly below jc: slot c holds the sum of squares of column c, slot k > c
-// the dot product of column c with column k.  It stores them, the owner of row
-// jc also stores that row, and a fence followed by a store of epoch jc+1 to
-// the CTA's flag publishes them.
-// Warp 0 of every CTA polls all G flags (bounded), fences, and then every CTA
-// reduces the G partial vectors in the same order.
+// Per column c (jc = j0 + c) each CTA forms, over its rows strictly below
+// jc, the sum of squares of column c -- in FP64 from the first product
+// (the square of a storage value is exact in FP64) -- and the dot products
+// of column c with the columns k > c in the storage type (FP64 FMA runs at a
+// small fraction of the FP32 rate on this part, so only the norm uses it).
+// It stores them, the owner of row jc also stores that row, and a fence
+// followed by a store of epoch jc+1 to the CTA's flag publishes them.  Warp 0
+// of every CTA polls all G flags (bounded), fences, and then every CTA
+// reduces the G partials in the same order.
 template <typename T, int NB>
 __global__ void __launch_bounds__(PANEL_THREADS, 1)
-    panel_qr_kernel(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau, double *partials,
-                    double *rowbuf, unsigned *flags, DevStatus *st, int64_t rows_per, int use_smem) {
+    panel_qr_kernel(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau, double *ssq,
+                    T *dots, double *rowbuf, unsigned *flags, DevStatus *st, int64_t rows_per,
+                    int use_smem) {
     static_assert(NB <= 32, "panel width");
     extern __shared__ __align__(16) uint8_t dsm[];
-    __shared__ double red[PANEL_WARPS][32];
-    __shared__ double tot[32];
+    __shared__ T red[PANEL_WARPS][32];
+    __shared__ double red_ss[PANEL_WARPS];
+    __shared__ T tot[32];
+    __shared__ double tot_ss;
     __shared__ double coef[32];  // tau * (v^T a_k) for k > c
     __shared__ T coefs[32];      // coef[k] / (alpha - beta), in the storage type
     __shared__ double scal_s, beta_s, tau_s;
+    __shared__ T scal_t;
     __shared__ int skip_s, ok_s;
 
     const unsigned G = gridDim.x;
@@ -91,40 +106,51 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         const int64_t jc = j0 + c;
         const int par = c & 1;
         const unsigned epoch = (unsigned)(jc + 1);
-        double *part = partials + (size_t)par * 32 * G;
+        double *my_ssq = ssq + (size_t)par * G;
+        T *my_dots = dots + (size_t)par * 32 * G;
         unsigned *flg = flags + (size_t)par * G;
         // ---- phase 1: partial sums over local rows strictly below jc ----
-        // The norm accumulates in FP64 from the first product on; the dot
-        // products accumulate in the storage type within a thread (a handful
-        // of rows) and in FP64 from the warp level up (FP64 FMA is far slower
-        // than FP32 on this part).
         double ss = 0.0;
-        T acc[NB];
+        T acc[32];
 #pragma unroll
-        for (int q = 0; q < NB; ++q) acc[q] = T(0);
+        for (int q = 0; q < 32; ++q) acc[q] = T(0);
         const int64_t rstart = max((int64_t)0, jc + 1 - r0);
-        for (int64_t r = rstart + threadIdx.x; r < nloc; r += PANEL_THREADS) {
-            const T xv = P[r + c * ldp];
-            ss += (double)xv * (double)xv;
+        if (nb == NB) {
+            // Full-width panel: every column exists, so the products with the
+            // already-factored columns k <= c are formed too (and ignored) --
+            // a loop without per-column predicates runs several times faster.
+            for (int64_t r = rstart + threadIdx.x; r < nloc; r += PANEL_THREADS) {
+                const T xv = P[r + c * ldp];
+                const double xd = (double)xv;
+                ss += xd * xd;
 #pragma unroll
-            for (int k = 0; k < NB; ++k)
-                if (k > c && k < nb) acc[k] += xv * P[r + k * ldp];
+                for (int k = 0; k < NB; ++k) acc[k] += xv * P[r + k * ldp];
+            }
+        } else {
+            for (int64_t r = rstart + threadIdx.x; r < nloc; r += PANEL_THREADS) {
+                const T xv = P[r + c * ldp];
+                const double xd = (double)xv;
+                ss += xd * xd;
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (k > c && k < nb) acc[k] += xv * P[r + k * ldp];
+            }
         }
-        {
-            double v[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) v[q] = (q < NB) ? (double)acc[q] : 0.0;
-#pragma unroll
-            for (int q = 0; q < 32; ++q)
-                if (q == c) v[q] = ss;
-            red[warp][lane] = warp_reduce_scatter32(v, lane);
-        }
+        red[warp][lane] = warp_reduce_scatter32<T>(acc, lane);
+        ss = warp_sum(ss);
+        if (lane == 0) red_ss[warp] = ss;
         __syncthreads();
         if (threadIdx.x < 32) {
-            double v = 0.0;
+            T v = T(0);
 #pragma unroll
             for (int w = 0; w < PANEL_WARPS; ++w) v += red[w][threadIdx.x];
-            part[(size_t)threadIdx.x * G + blockIdx.x] = v;
+            my_dots[(size_t)threadIdx.x * G + blockIdx.x] = v;
+            if (threadIdx.x == 0) {
+                double v2 = 0.0;
+#pragma unroll
+                for (int w = 0; w < PANEL_WARPS; ++w) v2 += red_ss[w];
+                my_ssq[blockIdx.x] = v2;
+            }
         }
         if (jc >= r0 && jc < r1 && threadIdx.x < nb && threadIdx.x >= c)
             rowbuf[par * 32 + threadIdx.x] = (double)P[(jc - r0) + threadIdx.x * ldp];
@@ -160,19 +186,33 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         }
         __syncthreads();
         if (!ok_s) return;
-        // ---- phase 2: every CTA reduces the G partial vectors in the same order ----
+        // ---- phase 2: every CTA reduces the G partials in the same order ----
+        {
+            T v[32 / PANEL_WARPS];
 #pragma unroll
-        for (int qq = 0; qq < 32 / PANEL_WARPS; ++qq) {
-            const int q = warp + PANEL_WARPS * qq;
-            double v = 0.0;
-            for (unsigned b = lane; b < G; b += 32) v += __ldcg(part + (size_t)q * G + b);
+            for (int qq = 0; qq < 32 / PANEL_WARPS; ++qq) v[qq] = T(0);
+            for (unsigned b = lane; b < G; b += 32) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) tot[q] = v;
+                for (int qq = 0; qq < 32 / PANEL_WARPS; ++qq)
+                    v[qq] += __ldcg(my_dots + (size_t)(warp + PANEL_WARPS * qq) * G + b);
+            }
+#pragma unroll
+            for (int qq = 0; qq < 32 / PANEL_WARPS; ++qq) {
+                T x = v[qq];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) tot[warp + PANEL_WARPS * qq] = x;
+            }
+            if (warp == PANEL_WARPS - 1) {
+                double x = 0.0;
+                for (unsigned b = lane; b < G; b += 32) x += __ldcg(my_ssq + b);
+                x = warp_sum(x);
+                if (lane == 0) tot_ss = x;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const double ssum = tot[c];
+            const double ssum = tot_ss;
             const double alpha = __ldcg(rowbuf + par * 32 + c);
             if (!isfinite(ssum) || !isfinite(alpha)) raise_status(st, DEV_NONFINITE, 20, (int)jc);
             if (ssum == 0.0) {
@@ -184,25 +224,42 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
                 const double beta = (alpha >= 0.0) ? -norm : norm;
                 const double t = (beta - alpha) / beta;
                 scal_s = 1.0 / (alpha - beta);
+                scal_t = (T)scal_s;
                 beta_s = beta;
                 tau_s = t;
                 if (blockIdx.x == 0) tau[jc] = (T)t;
             }
         }
         __syncthreads();
-        if (!skip_s && threadIdx.x > c && threadIdx.x < nb) {
+        if (!skip_s && threadIdx.x < 32) {
             const int k = threadIdx.x;
-            coef[k] = tau_s * (__ldcg(rowbuf + par * 32 + k) + scal_s * tot[k]);
-            coefs[k] = (T)(coef[k] * scal_s);
+            if (k > c && k < nb) {
+                coef[k] = tau_s * (__ldcg(rowbuf + par * 32 + k) + scal_s * (double)tot[k]);
+                coefs[k] = (T)(coef[k] * scal_s);
+            } else {
+                coef[k] = 0.0;
+                coefs[k] = T(0);
+            }
         }
         __syncthreads();
         if (skip_s) continue;
-        const double scale = scal_s;
+        const T scale_t = scal_t;
         // rows strictly below the diagonal: a_rk -= coef_k * scale * x_r ; x_r <- scale*x_r
-        for (int64_t r = rstart + threadIdx.x; r < nloc; r += PANEL_THREADS) {
-            const T x = P[r + c * ldp];
-            for (int k = c + 1; k < nb; ++k) P[r + k * ldp] -= coefs[k] * x;
-            P[r + c * ldp] = (T)(scale * (double)x);
+        if (nb == NB) {
+            // coefs[k] = 0 for k <= c, so the unpredicated update leaves those
+            // columns as they are (column c is rewritten just after).
+            for (int64_t r = rstart + threadIdx.x; r < nloc; r += PANEL_THREADS) {
+                const T x = P[r + c * ldp];
+#pragma unroll
+                for (int k = 0; k < NB; ++k) P[r + k * ldp] -= coefs[k] * x;
+                P[r + c * ldp] = x * scale_t;
+            }
+        } else {
+            for (int64_t r = rstart + threadIdx.x; r < nloc; r += PANEL_THREADS) {
+                const T x = P[r + c * ldp];
+                for (int k = c + 1; k < nb; ++k) P[r + k * ldp] -= coefs[k] * x;
+                P[r + c * ldp] = x * scale_t;
+            }
         }
         // the diagonal row: a_k[jc] -= coef_k ; A[jc, jc] = beta
         if (jc >= r0 && jc < r1) {
@@ -279,16 +336,18 @@ ct_status panel_launch(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau,
         set_error("panel: cooperative grid %d does not fit (%d per SM)", G, per_sm);
         return CT_ERR_CUDA;
     }
-    // workspace: flags [2][G] | partials [2][32][G] | rowbuf [2][32]
+    // workspace: flags [2][G] | ssq [2][G] | rowbuf [2][32] | dots [2][32][G]
     const size_t flag_bytes = round_up(sizeof(unsigned) * 2 * G, 256);
-    const size_t need = flag_bytes + sizeof(double) * (2 * 32 * (size_t)G + 2 * 32);
+    const size_t ssq_bytes = round_up(sizeof(double) * (2 * (size_t)G + 64), 256);
+    const size_t need = flag_bytes + ssq_bytes + sizeof(T) * 2 * 32 * (size_t)G;
     CT_TRY(ws.ensure(need));
     unsigned *flags = (unsigned *)ws.ptr;
-    double *partials = (double *)((char *)ws.ptr + flag_bytes);
-    double *rowbuf = partials + 2 * 32 * (size_t)G;
+    double *ssq = (double *)((char *)ws.ptr + flag_bytes);
+    double *rowbuf = ssq + 2 * (size_t)G;
+    T *dots = (T *)((char *)ws.ptr + flag_bytes + ssq_bytes);
     CT_CUDA(cudaMemsetAsync(flags, 0, flag_bytes, s));
     DevStatus *st = device_status();
-    void *args[] = {&A, &lda, &M, &j0, &nb, &tau, &partials, &rowbuf, &flags, &st, &rows_per,
+    void *args[] = {&A, &lda, &M, &j0, &nb, &tau, &ssq, &dots, &rowbuf, &flags, &st, &rows_per,
                     (void *)&use_smem};
     ProfScope prof(PROF_PANEL, s, 2.0 * rows * nb * nb, 2.0 * sizeof(T) * rows * nb, rows, nb, G,
                    use_smem);

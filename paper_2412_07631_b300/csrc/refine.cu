@@ -16,8 +16,11 @@
 // Per step:  t = R~^-1 p,  q = A~ t,  alpha = gamma / ||q||^2,
 //            x += alpha t,  r -= alpha q,  s = R~^-T (A~^T r),
 //            gamma' = ||s||^2,  p = s + (gamma'/gamma) p.
-// Stop when max over slices of ||alpha t|| / ||x|| <= tol, or after
-// max_iter steps (CT_ERR_NOCONV, x holds the last iterate).
+// Stop (regularised systems) when the certified relative error bound
+// ||A~^T r|| / (lambda ||x||) is <= tol for every slice, verified on a
+// recomputed residual; without regularisation rows when the relative update
+// ||alpha t|| / ||x|| is <= tol; or after max_iter steps (CT_ERR_NOCONV, x
+// holds the last iterate).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -156,7 +159,35 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
     CT_CUDA(cudaMemcpyAsync(w.p, w.s, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
     CT_TRY(coldot(n, k, w.s, w.s, w.part, gamma, st));
 
-    std::vector<double> h_tt(k), h_xx(k), h_alpha(k);
+    // Stopping quantity.  Regularised systems (sqrt_lambda > 0): the certified
+    // bound ||x - x*|| / ||x|| <= ||A~^T r|| / (lambda ||x||) (every singular
+    // value of A~ is >= sqrt_lambda), with r the FP64 residual; once the
+    // recursively updated residual meets it, the residual is recomputed from
+    // scratch (r = b~ - A~ x) and the bound checked again, restarting CG from
+    // the true residual if it fails.  Otherwise the relative update.
+    const bool use_cert = S.sqrt_lambda > 0.0;
+    const double lam = S.sqrt_lambda * S.sqrt_lambda;
+    double *gg = w.vec + 7 * k;
+    std::vector<double> h_tt(k), h_xx(k), h_alpha(k), h_gg(k);
+    auto read_back = [&](bool with_update) -> ct_status {
+        if (with_update) {
+            CT_CUDA(cudaMemcpyAsync(h_tt.data(), tt, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            CT_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        }
+        CT_CUDA(cudaMemcpyAsync(h_xx.data(), xx, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaMemcpyAsync(h_gg.data(), gg, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaStreamSynchronize(st));
+        return CT_OK;
+    };
+    auto cert_of = [&]() {
+        double worst = 0.0;
+        for (int32_t q = 0; q < k; ++q) {
+            const double v = std::sqrt(h_gg[q]) / (lam * std::max(std::sqrt(h_xx[q]), 1e-300));
+            if (!std::isfinite(v)) return (double)INFINITY;
+            worst = std::max(worst, v);
+        }
+        return worst;
+    };
     int it = 0;
     double last = INFINITY;
     bool converged = false;
@@ -167,12 +198,14 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         CT_TRY(coldot(M, k, w.q, w.q, w.part, qq, st));
         step_scalars<<<bk, 128, 0, st>>>(k, gamma, qq, alpha);
         count_launch();
-        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, 1.0, w.t, w.x);                       // x += a t
-        axpy_cols<<<(unsigned)ceil_div((int64_t)Mk, 256), 256, 0, st>>>(M, k, alpha, -1.0, w.q, w.r);  // r -= a q
-        CT_TRY(coldot(n, k, w.t, w.t, w.part, tt, st));
+        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, 1.0, w.t, w.x);  // x += a t
         count_launch();
+        axpy_cols<<<(unsigned)ceil_div((int64_t)Mk, 256), 256, 0, st>>>(M, k, alpha, -1.0, w.q, w.r);  // r -= a q
+        count_launch();
+        CT_TRY(coldot(n, k, w.t, w.t, w.part, tt, st));
         CT_TRY(coldot(n, k, w.x, w.x, w.part, xx, st));
         CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));   // t = A~^T r (reuse)
+        CT_TRY(coldot(n, k, w.t, w.t, w.part, gg, st));
         CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));        // s = R^-T t
         CT_TRY(coldot(n, k, w.s, w.s, w.part, gnew, st));
         beta_scalars<<<bk, 128, 0, st>>>(k, gnew, gamma, beta);
@@ -180,31 +213,47 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         xpby_cols<<<bn, 256, 0, st>>>(n, k, w.s, beta, w.p);
         count_launch();
         CT_CUDA(cudaGetLastError());
-        CT_CUDA(cudaMemcpyAsync(h_tt.data(), tt, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        CT_CUDA(cudaMemcpyAsync(h_xx.data(), xx, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        CT_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        CT_CUDA(cudaStreamSynchronize(st));
+        CT_TRY(read_back(true));
         double worst = 0.0;
-        for (int32_t q = 0; q < k; ++q) {
-            const double xn = std::sqrt(h_xx[q]);
-            const double up = std::fabs(h_alpha[q]) * std::sqrt(h_tt[q]);
-            if (!std::isfinite(up)) { worst = INFINITY; break; }
-            worst = std::max(worst, xn > 0 ? up / xn : up);
+        if (use_cert) {
+            worst = cert_of();
+        } else {
+            for (int32_t q = 0; q < k; ++q) {
+                const double xn = std::sqrt(h_xx[q]);
+                const double up = std::fabs(h_alpha[q]) * std::sqrt(h_tt[q]);
+                if (!std::isfinite(up)) { worst = INFINITY; break; }
+                worst = std::max(worst, xn > 0 ? up / xn : up);
+            }
         }
         last = worst;
-        if (worst <= tol) {
+        if (!(worst <= tol)) continue;
+        if (!use_cert) {
             converged = true;
             break;
         }
+        // verify with the residual recomputed from x
+        CT_TRY(spmm_ax(S, k, w.x, 1.0, w.btil, -1.0, w.r, st));
+        CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));
+        CT_TRY(coldot(n, k, w.t, w.t, w.part, gg, st));
+        CT_TRY(read_back(false));
+        last = cert_of();
+        if (last <= tol) {
+            converged = true;
+            break;
+        }
+        // restart from the true residual
+        CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));
+        CT_CUDA(cudaMemcpyAsync(w.p, w.s, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
+        CT_TRY(coldot(n, k, w.s, w.s, w.part, gamma, st));
     }
     CT_TRY(transpose_any(1, w.x, k, 1, X, ldx, k, n, st));  // row-major -> X (n x k col-major)
     if (info) {
         info->iterations = it;
-        info->last_rel_update = last;
+        info->stop_measure = last;
     }
     CT_TRY(check_device_status(st));
     if (!converged) {
-        set_error("refinement: %d steps, last relative update %.3g > tol %.3g", it, last, tol);
+        set_error("refinement: %d steps, stopping measure %.3g > tol %.3g", it, last, tol);
         return CT_ERR_NOCONV;
     }
     return CT_OK;

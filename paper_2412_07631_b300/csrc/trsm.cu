@@ -154,75 +154,91 @@ ct_status trsm_prepare(ct_factor f, cudaStream_t s) {
 }
 
 // R X = C (trans = false) or R^T X = C (trans = true) in place, C: n x k (ldc).
-// Block step:  X_i = R_ii^-1 C_i  (GEMM with the stored inverse block), then
-// the off-diagonal update C_{0:i} -= R_{0:i,i} X_i  (or, transposed,
-// C_{i+1:} -= R_{i,i+1:}^T X_i).  Every product is an op(A) = A^T GEMM, the
-// form the tensor cores take directly.
+// Superblocks of SB = 4 TB rows, taken from the last (back-substitution) or
+// the first (forward substitution).  Inside a superblock, block by block:
+//   X_i = R_ii^-1 C_i  (GEMM with the stored inverse block),
+//   the rest of the superblock -= its coupling block times X_i;
+// then once per superblock the off-diagonal update of everything beyond it,
+//   C_{0:s0} -= R_{0:s0, s0:s1} X_s   or   C_{s1:n} -= R_{s0:s1, s1:n}^T X_s,
+// a GEMM with K = SB.  Every product is an op(A) = A^T GEMM on the
+// tensor-core path (R^T supplies the non-transposed couplings).
 ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, cudaStream_t s) {
     const int64_t n = f->n;
     if (n == 0 || k == 0) return CT_OK;
     CT_TRY(trsm_prepare(f, s));
     const size_t es = f->es();
     const int TB = f->trsm_tb;
+    const int64_t SB = 4 * (int64_t)TB;
     const int64_t nblk = ceil_div(n, TB);
+    const int64_t nsb = ceil_div(n, SB);
     CT_TRY(f->misc2.ensure(es * (size_t)TB * k));
     void *tmp = f->misc2.ptr;
     const bool tc = f->kind == GEMM_TF32 || f->kind == GEMM_BF16;
     auto Cp = [&](int64_t i) { return (char *)C + es * i; };
-    for (int64_t t = 0; t < nblk; ++t) {
-        const int64_t ib = trans ? t : nblk - 1 - t;
-        const int64_t i0 = ib * TB;
-        const int ni = (int)std::min<int64_t>(TB, n - i0);
-        CT_CUDA(cudaMemcpy2DAsync(tmp, es * TB, Cp(i0), es * ldc, es * ni, k,
-                                  cudaMemcpyDeviceToDevice, s));
-        GemmArgs d{};
-        d.kind = f->kind;
-        d.M = ni;
-        d.N = k;
-        d.K = ni;
-        d.alpha = 1.0;
-        d.beta = 0.0;
-        d.B = tmp;
-        d.ldb = TB;
-        d.C = Cp(i0);
-        d.ldc = ldc;
-        d.lda = TB;
-        d.tb = false;
-        // op(A) = R_ii^-1 = (RinvT_i)^T, or R_ii^-T = (Rinv_i)^T
-        d.ta = true;
-        d.A = (char *)(trans ? f->Rinv : f->RinvT) + es * (size_t)ib * TB * TB;
-        CT_TRY(gemm(d, f->trsm_ws, s));
+    // C[r0:r0+rows] -= R[r0:r0+rows, c0:c0+cols] X   with X = C[c0:c0+cols]   (back)
+    // C[r0:r0+rows] -= R[c0:c0+cols, r0:r0+rows]^T X with X = C[c0:c0+cols]   (forward)
+    auto couple = [&](int64_t r0, int64_t rows, int64_t c0, int64_t cols) -> ct_status {
+        if (rows <= 0 || cols <= 0) return CT_OK;
         GemmArgs g{};
         g.kind = f->kind;
         g.alpha = -1.0;
         g.beta = 1.0;
+        g.M = rows;
         g.N = k;
-        g.K = ni;
-        g.B = Cp(i0);
+        g.K = cols;
+        g.B = Cp(c0);
         g.ldb = ldc;
+        g.C = Cp(r0);
         g.ldc = ldc;
         if (!trans) {
-            if (i0 == 0) continue;
-            g.M = i0;
-            g.C = Cp(0);
-            if (tc) {  // R_{0:i0, i0:i0+ni} = (Rt[i0:i0+ni, 0:i0])^T
+            if (tc) {  // R[r0:, c0:] = (Rt[c0:c0+cols, r0:r0+rows])^T
                 g.ta = true;
-                g.A = (char *)f->Rt + es * (size_t)i0;
+                g.A = (char *)f->Rt + es * (size_t)(c0 + r0 * f->ldrt);
                 g.lda = f->ldrt;
             } else {
                 g.ta = false;
-                g.A = (char *)f->VR + es * (size_t)(i0 * f->lda);
+                g.A = (char *)f->VR + es * (size_t)(r0 + c0 * f->lda);
                 g.lda = f->lda;
             }
         } else {
-            if (i0 + ni >= n) continue;
             g.ta = true;
-            g.M = n - i0 - ni;
-            g.A = (char *)f->VR + es * (size_t)(i0 + (i0 + ni) * f->lda);
+            g.A = (char *)f->VR + es * (size_t)(c0 + r0 * f->lda);
             g.lda = f->lda;
-            g.C = Cp(i0 + ni);
         }
-        CT_TRY(gemm(g, f->trsm_ws, s));
+        return gemm(g, f->trsm_ws, s);
+    };
+    for (int64_t t = 0; t < nsb; ++t) {
+        const int64_t sbi = trans ? t : nsb - 1 - t;
+        const int64_t s0 = sbi * SB, s1 = std::min<int64_t>(n, s0 + SB);
+        const int64_t b_lo = s0 / TB, b_hi = ceil_div(s1, TB);  // base blocks [b_lo, b_hi)
+        for (int64_t u = 0; u < b_hi - b_lo; ++u) {
+            const int64_t ib = trans ? b_lo + u : b_hi - 1 - u;
+            const int64_t i0 = ib * TB;
+            const int ni = (int)std::min<int64_t>(TB, n - i0);
+            CT_CUDA(cudaMemcpy2DAsync(tmp, es * TB, Cp(i0), es * ldc, es * ni, k,
+                                      cudaMemcpyDeviceToDevice, s));
+            GemmArgs d{};
+            d.kind = f->kind;
+            d.M = ni;
+            d.N = k;
+            d.K = ni;
+            d.alpha = 1.0;
+            d.beta = 0.0;
+            d.B = tmp;
+            d.ldb = TB;
+            d.C = Cp(i0);
+            d.ldc = ldc;
+            d.lda = TB;
+            d.tb = false;
+            // op(A) = R_ii^-1 = (RinvT_i)^T, or R_ii^-T = (Rinv_i)^T
+            d.ta = true;
+            d.A = (char *)(trans ? f->Rinv : f->RinvT) + es * (size_t)ib * TB * TB;
+            CT_TRY(gemm(d, f->trsm_ws, s));
+            if (!trans) CT_TRY(couple(s0, i0 - s0, i0, ni));                 // rows above, in the superblock
+            else CT_TRY(couple(i0 + ni, s1 - (i0 + ni), i0, ni));          // rows below, in the superblock
+        }
+        if (!trans) CT_TRY(couple(0, s0, s0, s1 - s0));
+        else CT_TRY(couple(s1, n - s1, s0, s1 - s0));
     }
     return CT_OK;
 }
