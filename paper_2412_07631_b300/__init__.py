@@ -227,16 +227,21 @@ class Factor:
         self.last_info = info.as_dict()
         return X
 
-    def adjoint(self, gX, out=None, stream=None):
-        """gB = [Q [R^-T gX; 0]]_{0:m} for gX (k, n) -> (k, m)."""
+    def adjoint(self, gX, out=None, max_iter: int = 0, tol: float = 0.0, stream=None,
+                allow_noconv: bool = False):
+        """gB = [Q [R^-T gX; 0]]_{0:m} for gX (k, n) -> (k, m); with refining
+        factors, the same map refined in FP64 (gB = [A~ u]_{0:m},
+        A~^T A~ u = gX)."""
         import torch
         assert gX.is_cuda and gX.dtype == self.io_dtype and gX.is_contiguous()
         k = gX.shape[0]
         gB = out if out is not None else torch.empty((k, self.m), dtype=gX.dtype, device=gX.device)
         info = SolveInfo()
-        o = self._opts()
-        _check(lib().ct_solve_adjoint(self.h, _ptr(gX), self.n, k, _ptr(gB), self.m, C.byref(o),
-                                      _stream(stream), C.byref(info)))
+        o = self._opts(max_iter, tol)
+        st = lib().ct_solve_adjoint(self.h, _ptr(gX), self.n, k, _ptr(gB), self.m, C.byref(o),
+                                    _stream(stream), C.byref(info))
+        _check(st, allow=(5,) if allow_noconv else ())
+        self.last_info = info.as_dict()
         return gB
 
     def export(self):
@@ -267,6 +272,34 @@ def gemm(kind: str, transa: str, transb: str, M: int, N: int, K: int, alpha: flo
                          _ptr(A), lda, _ptr(B), ldb, beta, _ptr(Cm), ldc, _stream(stream)))
 
 
+class CTSolve:
+    """Differentiable reconstruction layer: X = solve(B) with the backward
+    pass grad_B = adjoint(grad_X) (Q R^-T grad_X on the ray rows, refined in
+    FP64 for refining factors).  Use CTSolve.apply(B, factor[, max_iter,
+    tol]); B is a CUDA tensor (k, m) of the factor's I/O dtype."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, B, factor, max_iter: int = 0, tol: float = 0.0):
+        if cls._fn is None:
+            import torch
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, B_, f_, it_, tol_):
+                    ctx.f, ctx.it, ctx.tol = f_, it_, tol_
+                    return f_.solve(B_.contiguous(), max_iter=it_, tol=tol_)
+
+                @staticmethod
+                def backward(ctx, gX):
+                    gB = ctx.f.adjoint(gX.contiguous(), max_iter=ctx.it, tol=ctx.tol)
+                    return gB, None, None, None
+
+            cls._fn = _Fn
+        return cls._fn.apply(B, factor, max_iter, tol)
+
+
 STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other"]
 
 
@@ -295,5 +328,5 @@ def stats_read() -> dict:
     return out
 
 
-__all__ = ["stats_reset", "stats_read", "stats_dump", "STAT_CLASSES", "Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
+__all__ = ["CTSolve", "stats_reset", "stats_read", "stats_dump", "STAT_CLASSES", "Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
            "lib_path", "make_geometry", "PRECISIONS", "SYMBOLS"]

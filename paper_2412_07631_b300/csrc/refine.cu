@@ -84,6 +84,12 @@ __global__ void beta_scalars(int64_t k, const double *gnew, double *gamma, doubl
     gamma[s] = gnew[s];
 }
 
+// out = A - B (elementwise)
+__global__ void sub_kernel(int64_t total, const double *A, const double *B, double *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) out[i] = A[i] - B[i];
+}
+
 struct Ws {
     double *x, *r, *p, *s, *t, *q, *btil;  // row-major FP64
     double *part, *vec;                    // reductions
@@ -91,6 +97,15 @@ struct Ws {
 };
 
 }  // namespace
+
+static ct_status residual_sub(int64_t rows, int64_t k, const double *A, const double *B,
+                              double *out, cudaStream_t s) {
+    const int64_t total = rows * k;
+    sub_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(total, A, B, out);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
 
 // Per-slice inner products of row-major k-column blocks (deterministic order).
 static ct_status coldot(int64_t rows, int64_t k, const double *U, const double *V, double *part,
@@ -254,6 +269,143 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
     CT_TRY(check_device_status(st));
     if (!converged) {
         set_error("refinement: %d steps, stopping measure %.3g > tol %.3g", it, last, tol);
+        return CT_ERR_NOCONV;
+    }
+    return CT_OK;
+}
+
+// Adjoint of the refined solve map b -> x*(b) = (A~^T A~)^-1 A~^T b~ (a linear
+// map once the refinement has converged): grad_b = [A~ u]_{0:m} with
+// A~^T A~ u = grad_x.  u is found by preconditioned CG on the normal
+// equations with M = R~^T R~ (two triangular solves with the low-precision
+// factor), every vector and inner product in FP64 and the products A~^T A~ p
+// formed with the sparse FP64 Siddon matrix.  Stop (sqrt_lambda > 0) when the
+// certified bound ||g - A~^T A~ u|| / (lambda ||u||) >= ||u - u*|| / ||u||
+// is <= tol for every slice, verified on a recomputed residual; without
+// regularisation rows when the relative update is <= tol.
+ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
+                             int64_t ldgb, const ct_opts *o, cudaStream_t st,
+                             ct_solve_info *info) {
+    const ct_system sys = f->sys;
+    const SparseSys S = sys->sparse();
+    const int64_t n = f->n, m = f->m, M = f->M;
+    const int max_iter = (o && o->refine_max_iter > 0) ? o->refine_max_iter : 10;
+    const double tol = (o && o->refine_tol > 0) ? o->refine_tol : 1e-7;
+    const int64_t nblk = ceil_div(std::max(M, n), RB);
+    const size_t nk = (size_t)n * k, Mk = (size_t)M * k;
+    const size_t ldl = round_up(n, 32);
+    const size_t bytes = sizeof(double) * (Mk + 6 * nk + (size_t)nblk * k + 8 * (size_t)k) +
+                         f->es() * ldl * k + 1024;
+    CT_TRY(f->refine_ws.ensure(bytes));
+    char *base = (char *)f->refine_ws.ptr;
+    auto take = [&](size_t b) { char *p = base; base += round_up((int64_t)b, 256); return p; };
+    double *q = (double *)take(sizeof(double) * Mk);   // A~ p (M' x k)
+    double *g = (double *)take(sizeof(double) * nk);   // right-hand side (row-major)
+    double *u = (double *)take(sizeof(double) * nk);
+    double *r = (double *)take(sizeof(double) * nk);
+    double *z = (double *)take(sizeof(double) * nk);
+    double *p = (double *)take(sizeof(double) * nk);
+    double *w = (double *)take(sizeof(double) * nk);   // A~^T A~ p
+    double *part = (double *)take(sizeof(double) * nblk * k);
+    double *vec = (double *)take(sizeof(double) * 8 * k);
+    void *lp = take(f->es() * ldl * k);
+    double *rho = vec, *pw = vec + k, *alpha = vec + 2 * k, *beta = vec + 3 * k,
+           *rnew = vec + 4 * k, *rr = vec + 5 * k, *uu = vec + 6 * k, *pp = vec + 7 * k;
+    const unsigned bn = (unsigned)ceil_div((int64_t)nk, 256), bk = (unsigned)ceil_div(k, 128);
+    const bool use_cert = S.sqrt_lambda > 0.0;
+    const double lam = S.sqrt_lambda * S.sqrt_lambda;
+
+    // normal-equations product: out = A~^T (A~ v)
+    auto normal = [&](const double *v, double *out) -> ct_status {
+        CT_TRY(spmm_ax(S, k, v, 0.0, nullptr, 1.0, q, st));
+        return spmm_atr(S, k, q, 0.0, nullptr, 1.0, out, st);
+    };
+    auto precond = [&](const double *v, double *out) -> ct_status {  // out = R^-1 R^-T v
+        CT_TRY(apply_rinv(f, true, v, out, k, lp, st));
+        return apply_rinv(f, false, out, out, k, lp, st);
+    };
+    CT_TRY(transpose_any(1, gX, ldgx, 1, g, k, n, k, st));
+    // u0 = M^-1 g ; r = g - A~^T A~ u0 ; z = M^-1 r ; p = z ; rho = <r, z>
+    CT_TRY(precond(g, u));
+    // r = g - w  (w = A~^T A~ u)
+    CT_TRY(normal(u, w));
+    CT_TRY(residual_sub(n, k, g, w, r, st));
+    CT_TRY(precond(r, z));
+    CT_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
+    CT_TRY(coldot(n, k, r, z, part, rho, st));
+
+    std::vector<double> h_rr(k), h_uu(k), h_pp(k), h_al(k);
+    auto measure = [&](bool with_update) -> ct_status {
+        CT_TRY(coldot(n, k, r, r, part, rr, st));
+        CT_TRY(coldot(n, k, u, u, part, uu, st));
+        CT_CUDA(cudaMemcpyAsync(h_rr.data(), rr, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaMemcpyAsync(h_uu.data(), uu, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        if (with_update) {
+            CT_TRY(coldot(n, k, p, p, part, pp, st));
+            CT_CUDA(cudaMemcpyAsync(h_pp.data(), pp, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            CT_CUDA(cudaMemcpyAsync(h_al.data(), alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        }
+        CT_CUDA(cudaStreamSynchronize(st));
+        return CT_OK;
+    };
+    auto stop_value = [&](bool with_update) {
+        double worst = 0.0;
+        for (int32_t s2 = 0; s2 < k; ++s2) {
+            const double un = std::max(std::sqrt(h_uu[s2]), 1e-300);
+            double v = use_cert ? std::sqrt(h_rr[s2]) / (lam * un)
+                                : (with_update ? std::fabs(h_al[s2]) * std::sqrt(h_pp[s2]) / un : INFINITY);
+            if (!std::isfinite(v)) return (double)INFINITY;
+            worst = std::max(worst, v);
+        }
+        return worst;
+    };
+    int it = 0;
+    double last = INFINITY;
+    bool converged = false;
+    while (it < max_iter) {
+        ++it;
+        CT_TRY(normal(p, w));                                 // w = A~^T A~ p
+        CT_TRY(coldot(n, k, p, w, part, pw, st));
+        step_scalars<<<bk, 128, 0, st>>>(k, rho, pw, alpha);  // alpha = rho / <p, w>
+        count_launch();
+        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, 1.0, p, u);   // u += a p
+        count_launch();
+        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, -1.0, w, r);  // r -= a w
+        count_launch();
+        CT_TRY(measure(true));
+        last = stop_value(true);
+        if (last <= tol) {
+            if (!use_cert) { converged = true; break; }
+            CT_TRY(normal(u, w));                              // verify on the true residual
+            CT_TRY(residual_sub(n, k, g, w, r, st));
+            CT_TRY(measure(false));
+            last = stop_value(false);
+            if (last <= tol) { converged = true; break; }
+            CT_TRY(precond(r, z));                             // restart from it
+            CT_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
+            CT_TRY(coldot(n, k, r, z, part, rho, st));
+            continue;
+        }
+        CT_TRY(precond(r, z));
+        CT_TRY(coldot(n, k, r, z, part, rnew, st));
+        beta_scalars<<<bk, 128, 0, st>>>(k, rnew, rho, beta);
+        count_launch();
+        xpby_cols<<<bn, 256, 0, st>>>(n, k, z, beta, p);      // p = z + b p
+        count_launch();
+        CT_CUDA(cudaGetLastError());
+    }
+    // grad_b = [A~ u]_{0:m}: the ray rows of the forward product
+    CT_TRY(spmm_ax(S, k, u, 0.0, nullptr, 1.0, q, st));
+    CT_TRY(transpose_any(1, q, k, 1, gB, ldgb, k, m, st));  // rows 0..m-1 (row-major) -> m x k
+    if (info) {
+        info->iterations = it;
+        info->stop_measure = last;
+        info->rjj_min_abs = f->rjj_min;
+        info->rjj_max_abs = f->rjj_max;
+    }
+    CT_TRY(check_device_status(st));
+    if (!converged) {
+        set_error("adjoint refinement: %d steps, stopping measure %.3g > tol %.3g", it, last, tol);
         return CT_ERR_NOCONV;
     }
     return CT_OK;

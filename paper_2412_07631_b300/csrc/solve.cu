@@ -45,9 +45,14 @@ ct_status solve_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X,
     return check_device_status(s);
 }
 
+ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
+                             int64_t ldgb, const ct_opts *o, cudaStream_t st, ct_solve_info *info);
+
 ct_status adjoint_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB, int64_t ldgb,
                       const ct_opts *o, cudaStream_t s, ct_solve_info *info) {
-    (void)o;
+    if ((f->prec == CT_TF32_REFINE || f->prec == CT_BF16_REFINE) &&
+        !(o && o->refine_max_iter < 0))
+        return adjoint_refine_run(f, gX, ldgx, k, gB, ldgb, o, s, info);
     const int64_t M = f->M, m = f->m, n = f->n, ldbt = f->lda;
     CT_TRY(f->Bt.ensure(f->es() * (size_t)ldbt * k));
     void *Bt = f->Bt.ptr;
