@@ -95,7 +95,15 @@ typedef struct {
                                 without, the relative update max_s ||dx_s||/||x_s|| */
     int32_t nb_outer;        /* outer WY block width (0: automatic) */
     int32_t nb_inner;        /* panel width (0: automatic) */
+    int32_t flags;           /* CT_OPT_* bits */
 } ct_opts;
+
+/* ct_opts.flags: by default the repeated parts of a solve (the Q^T sweep plus
+ * the triangular solve, and each refinement step) are captured once per
+ * batch size as CUDA graphs on a library-owned stream and replayed; this bit
+ * runs them as individual launches instead.  (Per-launch timing from
+ * ct_stats_reset(1) also disables graphs.) */
+#define CT_OPT_NO_GRAPHS 1
 
 typedef struct {
     int32_t iterations;       /* refinement steps taken (0 for CT_FP64 / CT_FP32) */

@@ -29,7 +29,8 @@ class Geometry(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("refine_max_iter", C.c_int32),
-                ("refine_tol", C.c_double), ("nb_outer", C.c_int32), ("nb_inner", C.c_int32)]
+                ("refine_tol", C.c_double), ("nb_outer", C.c_int32), ("nb_inner", C.c_int32),
+                ("flags", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -163,7 +164,7 @@ class System:
                stream=None) -> "Factor":
         if precision is None:
             precision = "fp64" if self.storage == "fp64" else "tf32"
-        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner)
+        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0)
         h = C.c_void_p()
         _check(lib().ct_qr_factor(self.h, C.byref(o), _stream(stream), C.byref(h)))
         return Factor(h, self, precision)
@@ -195,8 +196,10 @@ class Factor:
         import torch
         return torch.float32 if self.precision == "fp32" else torch.float64
 
+    graphs = True  # capture repeated solve work in CUDA graphs (library default)
+
     def _opts(self, max_iter=0, tol=0.0):
-        return Opts(PRECISIONS[self.precision], max_iter, tol, 0, 0)
+        return Opts(PRECISIONS[self.precision], max_iter, tol, 0, 0, 0 if self.graphs else 1)
 
     def solve(self, B, out=None, max_iter: int = 0, tol: float = 0.0, stream=None,
               allow_noconv: bool = False):

@@ -89,11 +89,36 @@ size_t g_prof_used = 0;
 }  // namespace
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+bool timing_enabled() { return g_timing.load(std::memory_order_relaxed); }
+
+// Graphs are used unless the caller turned them off or per-launch timing is on
+// (timed launches must run one by one to be measured).
+bool graphs_allowed(ct_factor f) { return f->graphs_enabled && !timing_enabled(); }
+
+uint64_t graph_key(ct_factor f, int64_t k, const void *extra) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        h ^= v;
+        h *= 1099511628211ull;
+    };
+    mix((uint64_t)k);
+    mix((uint64_t)(uintptr_t)extra);
+    const Scratch *all[] = {&f->gemm_ws, &f->W, &f->W2, &f->G, &f->Bt, &f->trsm_ws,
+                            &f->refine_ws, &f->misc, &f->misc2};
+    for (const Scratch *sc : all) {
+        mix((uint64_t)(uintptr_t)sc->ptr);
+        mix(sc->gen);
+    }
+    return h | 1ull;  // never 0 (0 = empty slot)
+}
 
 ProfScope::ProfScope(int c, cudaStream_t st, double f, double b, int64_t d0, int64_t d1,
                      int64_t d2, int64_t d3)
     : cls(c), s(st), flops(f), bytes(b), slot(-1) {
     if (!g_timing.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (g_prof_used == g_prof.size()) {
         ProfRec r{};
@@ -133,6 +158,7 @@ ct_status Scratch::ensure(size_t need) {
         return cuda_status(e, "cudaMalloc(scratch)", __FILE__, __LINE__);
     }
     bytes = sz;
+    ++gen;
     return CT_OK;
 }
 
@@ -480,6 +506,7 @@ ct_status ct_factor_device_ptrs(ct_factor f, void **VR, int64_t *lda, void **tau
 ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
                    const ct_opts *opts, void *stream, ct_solve_info *info) {
     if (!f || k < 0 || ldb < f->m || ldx < f->n) return CT_ERR_ARG;
+    f->graphs_enabled = !(opts && (opts->flags & CT_OPT_NO_GRAPHS));
     if (k == 0) return CT_OK;
     if (!B || !X) return CT_ERR_ARG;
     if (is_refine(f->prec) && !f->sys) return CT_ERR_STATE;
@@ -492,6 +519,7 @@ ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t k, void
     if (k == 0) return CT_OK;
     if (!B || !X) return CT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    f->graphs_enabled = !(opts && (opts->flags & CT_OPT_NO_GRAPHS));
     const size_t ies = f->prec == CT_FP32 ? 4 : 8;
     const size_t bbytes = ies * (size_t)f->m * k, xbytes = ies * (size_t)f->n * k;
     CT_TRY(f->host_pinned.ensure(bbytes + xbytes + 256));
@@ -508,6 +536,7 @@ ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t k, void
 ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
                            int64_t ldgb, const ct_opts *opts, void *stream, ct_solve_info *info) {
     if (!f || k < 0 || ldgx < f->n || ldgb < f->m) return CT_ERR_ARG;
+    f->graphs_enabled = !(opts && (opts->flags & CT_OPT_NO_GRAPHS));
     if (k == 0) return CT_OK;
     if (!gX || !gB) return CT_ERR_ARG;
     return adjoint_run(f, gX, ldgx, k, gB, ldgb, opts, (cudaStream_t)stream, info);
@@ -521,6 +550,12 @@ void ct_system_free(ct_system sys) {
 
 void ct_factor_free(ct_factor f) {
     if (!f) return;
+    if (f->g_direct.exec) cudaGraphExecDestroy(f->g_direct.exec);
+    if (f->g_iter.exec) cudaGraphExecDestroy(f->g_iter.exec);
+    if (f->side) cudaStreamDestroy(f->side);
+    if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+    if (f->ev_join) cudaEventDestroy(f->ev_join);
+    if (f->pinned) cudaFreeHost(f->pinned);
     cudaFree(f->Rinv);
     cudaFree(f->RinvT);
     cudaFree(f->Rt);

@@ -214,6 +214,7 @@ struct ProfScope {
 struct Scratch {
     void *ptr = nullptr;
     size_t bytes = 0;
+    uint64_t gen = 0;  // bumped whenever the buffer moves (captured graphs key on it)
     ct_status ensure(size_t need);
     ~Scratch();
 };

@@ -152,50 +152,35 @@ ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void 
 }
 
 // Split-K policy: enough CTAs to cover the machine about twice, each split
-// at least kMinChunk deep.
-ct_status gemm(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
-    if (g.M < 0 || g.N < 0 || g.K < 0) return CT_ERR_ARG;
-    if (g.M == 0 || g.N == 0) return CT_OK;
+// at least kMinChunk deep.  All scratch of one call (K-major operand copies
+// for the tensor cores, then split-K partial products) lives in `ws`, which
+// belongs to the caller; nothing process-wide is used, so a captured graph
+// that replays this call references only its caller's buffers.
+ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
+    if (g0.M < 0 || g0.N < 0 || g0.K < 0) return CT_ERR_ARG;
+    if (g0.M == 0 || g0.N == 0) return CT_OK;
+    GemmArgs g = g0;
     const bool fp64 = g.kind == GEMM_F64;
     bool tc = g.kind == GEMM_TF32 || g.kind == GEMM_BF16;
     if (tc && (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15) || (g.lda & 3) || (g.ldb & 3))) {
         // A TMA tile must start on a 16-byte boundary; ragged sub-blocks that
         // do not (only at the edges of odd-sized problems) use the FP32 SIMT path.
-        GemmArgs h = g;
-        h.kind = GEMM_F32;
-        return gemm(h, ws, s);
-    }
-    if (tc && (!g.ta || g.tb) && g.K > 0) {
-        // The tensor cores take TF32 operands K-major only (each output row's K
-        // values contiguous; the MN-major form is not available for 32-bit
-        // operands).  An operand stored the other way round is transposed
-        // into a K-major copy first.
-        static Scratch tws;
-        GemmArgs h = g;
-        const int64_t ldta = round_up(g.K, 32);
-        const size_t abytes = !g.ta ? sizeof(float) * (size_t)ldta * g.M : 0;
-        const size_t bbytes = g.tb ? sizeof(float) * (size_t)ldta * g.N : 0;
-        CT_TRY(tws.ensure(abytes + bbytes + 256));
-        if (!g.ta) {
-            CT_TRY(transpose_any(0, g.A, g.lda, 0, tws.ptr, ldta, g.M, g.K, s));  // A (M x K) -> K x M
-            h.A = tws.ptr;
-            h.lda = ldta;
-            h.ta = true;
-        }
-        if (g.tb) {
-            void *bt = (char *)tws.ptr + round_up((int64_t)abytes, 256);
-            CT_TRY(transpose_any(0, g.B, g.ldb, 0, bt, ldta, g.N, g.K, s));  // B (N x K) -> K x N
-            h.B = bt;
-            h.ldb = ldta;
-            h.tb = false;
-        }
-        return gemm(h, ws, s);
+        g.kind = GEMM_F32;
+        tc = false;
     }
     if (g.K == 0) {
         // C = beta * C
         if (g.beta == 1.0) return CT_OK;
         return splitk_reduce(fp64, g.M, g.N, 0, nullptr, 0.0, g.beta, g.C, g.ldc, s);
     }
+    // The tensor cores take TF32 operands K-major only (each output row's K
+    // values contiguous; the MN-major form is not available for 32-bit
+    // operands).  An operand stored the other way round is transposed into a
+    // K-major copy first.
+    const bool tra = tc && !g.ta, trb = tc && g.tb;
+    const int64_t ldt = round_up(g.K, 32);
+    const size_t abytes = tra ? (size_t)round_up((int64_t)(sizeof(float) * ldt * g.M), 256) : 0;
+    const size_t bbytes = trb ? (size_t)round_up((int64_t)(sizeof(float) * ldt * g.N), 256) : 0;
     const int64_t BM = tc ? 128 : (fp64 ? 64 : 128);
     const int64_t BN = tc ? 256 : (fp64 ? 64 : 128);
     const int64_t tiles = ceil_div(g.M, BM) * ceil_div(g.N, BN);
@@ -204,22 +189,40 @@ ct_status gemm(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
     int64_t splits = 1;
     if (tiles < target) splits = std::min(ceil_div(target, tiles), std::max<int64_t>(1, g.K / kMinChunk));
     splits = std::min<int64_t>(splits, 64);
+    int64_t kchunk = g.K;
+    if (splits > 1) {
+        const int64_t align = tc ? 32 : 16;
+        kchunk = round_up(ceil_div(g.K, splits), align);
+        splits = ceil_div(g.K, kchunk);
+    }
+    const size_t esz = fp64 ? 8 : 4;
+    const size_t pbytes = splits > 1 ? esz * (size_t)(g.M * g.N * splits) : 0;
+    if (abytes + bbytes + pbytes > 0) CT_TRY(ws.ensure(abytes + bbytes + pbytes));
+    if (tra) {
+        CT_TRY(transpose_any(0, g.A, g.lda, 0, ws.ptr, ldt, g.M, g.K, s));  // A (M x K) -> K x M
+        g.A = ws.ptr;
+        g.lda = ldt;
+        g.ta = true;
+    }
+    if (trb) {
+        void *bt = (char *)ws.ptr + abytes;
+        CT_TRY(transpose_any(0, g.B, g.ldb, 0, bt, ldt, g.N, g.K, s));  // B (N x K) -> K x N
+        g.B = bt;
+        g.ldb = ldt;
+        g.tb = false;
+    }
     if (splits <= 1) {
         return tc ? gemm_tc_launch(g, 1, g.K, 0, s) : gemm_simt_launch(g, 1, g.K, 0, s);
     }
-    const int64_t align = tc ? 32 : 16;
-    int64_t kchunk = round_up(ceil_div(g.K, splits), align);
-    splits = ceil_div(g.K, kchunk);
-    const size_t esz = fp64 ? 8 : 4;
-    CT_TRY(ws.ensure(esz * (size_t)(g.M * g.N * splits)));
+    void *part = (char *)ws.ptr + abytes + bbytes;
     GemmArgs p = g;
     p.alpha = 1.0;
     p.beta = 0.0;
-    p.C = ws.ptr;
+    p.C = part;
     p.ldc = g.M;
     CT_TRY(tc ? gemm_tc_launch(p, (int)splits, kchunk, g.M * g.N, s)
               : gemm_simt_launch(p, (int)splits, kchunk, g.M * g.N, s));
-    return splitk_reduce(fp64, g.M, g.N, (int)splits, ws.ptr, g.alpha, g.beta, g.C, g.ldc, s);
+    return splitk_reduce(fp64, g.M, g.N, (int)splits, part, g.alpha, g.beta, g.C, g.ldc, s);
 }
 
 }  // namespace ctqr

@@ -22,6 +22,17 @@ struct ct_system_s {
     }
 };
 
+// A captured CUDA graph for a repeated piece of the solve.  key identifies
+// everything the graph bakes in (batch size, buffer addresses, scratch
+// generations); a key seen once runs eagerly (sizing every scratch buffer),
+// seen again it is captured, then replayed.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t key = 0;      // key of exec
+    uint64_t warm = 0;     // key of the last eager run
+    int64_t kernels = 0;   // kernel launches inside the graph (for accounting)
+};
+
 struct ct_factor_s {
     ct_system sys = nullptr;  // borrowed (sparse rows for FP64 refinement)
     ct_precision prec = CT_FP64;
@@ -40,12 +51,25 @@ struct ct_factor_s {
     void *Rinv = nullptr, *RinvT = nullptr, *Rt = nullptr;
     int trsm_tb = 0;
     int64_t ldrt = 0;
+    // captured graphs of the solve, and the stream they run on
+    GraphSlot g_direct, g_iter;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    double *pinned = nullptr;  // host readback of per-slice scalars (pinned)
+    size_t pinned_count = 0;
+    bool graphs_enabled = true;
     // work buffers
     ctqr::Scratch gemm_ws, W, W2, G, panel_ws, Bt, trsm_ws, refine_ws, host_pinned, misc, misc2;
     size_t es() const { return fp64 ? 8 : 4; }
 };
 
 namespace ctqr {
+// Run body(stream) on `caller`, eagerly or through the captured graph of slot
+// `g` (see GraphSlot).  body must not synchronise or read device data.
+template <class Body>
+ct_status run_graphed(ct_factor f, GraphSlot &g, uint64_t key, cudaStream_t caller, Body body);
+uint64_t graph_key(ct_factor f, int64_t k, const void *extra);
+bool graphs_allowed(ct_factor f);
 ct_status qr_factor_run(ct_factor f, cudaStream_t s);
 // R X = C or R^T X = C in place for the factor's R (blocked, inverse diagonal blocks).
 ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, cudaStream_t s);
@@ -56,4 +80,57 @@ ct_status solve_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X,
                     const ct_opts *o, cudaStream_t s, ct_solve_info *info);
 ct_status adjoint_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB, int64_t ldgb,
                       const ct_opts *o, cudaStream_t s, ct_solve_info *info);
+}  // namespace ctqr
+
+// ---- graph slot implementation (header-only template) ----------------------
+namespace ctqr {
+int64_t launch_count();
+bool timing_enabled();
+
+template <class Body>
+ct_status run_graphed(ct_factor f, GraphSlot &g, uint64_t key, cudaStream_t caller, Body body) {
+    if (!graphs_allowed(f)) return body(caller);
+    if (!f->side) {
+        CT_CUDA(cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking));
+        CT_CUDA(cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming));
+        CT_CUDA(cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming));
+    }
+    if (!(g.exec && g.key == key)) {
+        if (g.warm != key) {  // first sight of this key: eager run sizes every buffer
+            g.warm = key;
+            return body(caller);
+        }
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        const int64_t before = launch_count();
+        CT_CUDA(cudaStreamBeginCapture(f->side, cudaStreamCaptureModeThreadLocal));
+        ct_status st = body(f->side);
+        cudaError_t e = cudaStreamEndCapture(f->side, &graph);
+        const int64_t kernels = launch_count() - before;
+        count_launch((int)-kernels);  // nothing ran during capture
+        if (st != CT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_status(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        }
+        g.key = key;
+        g.kernels = kernels;
+    }
+    CT_CUDA(cudaEventRecord(f->ev_fork, caller));
+    CT_CUDA(cudaStreamWaitEvent(f->side, f->ev_fork, 0));
+    CT_CUDA(cudaGraphLaunch(g.exec, f->side));
+    count_launch((int)g.kernels);
+    CT_CUDA(cudaEventRecord(f->ev_join, f->side));
+    CT_CUDA(cudaStreamWaitEvent(caller, f->ev_join, 0));
+    return CT_OK;
+}
 }  // namespace ctqr

@@ -183,15 +183,23 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
     const bool use_cert = S.sqrt_lambda > 0.0;
     const double lam = S.sqrt_lambda * S.sqrt_lambda;
     double *gg = w.vec + 7 * k;
-    std::vector<double> h_tt(k), h_xx(k), h_alpha(k), h_gg(k);
-    auto read_back = [&](bool with_update) -> ct_status {
+    // per-slice scalars come back through pinned host memory (tt, xx, alpha, gg)
+    if (f->pinned_count < 4 * (size_t)k) {
+        if (f->pinned) cudaFreeHost(f->pinned);
+        f->pinned = nullptr;
+        f->pinned_count = 0;
+        CT_CUDA(cudaMallocHost((void **)&f->pinned, sizeof(double) * 4 * (size_t)k));
+        f->pinned_count = 4 * (size_t)k;
+    }
+    double *h_tt = f->pinned, *h_xx = f->pinned + k, *h_alpha = f->pinned + 2 * k,
+           *h_gg = f->pinned + 3 * k;
+    auto read_back = [&](bool with_update, cudaStream_t s2) -> ct_status {
         if (with_update) {
-            CT_CUDA(cudaMemcpyAsync(h_tt.data(), tt, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-            CT_CUDA(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            CT_CUDA(cudaMemcpyAsync(h_tt, tt, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
+            CT_CUDA(cudaMemcpyAsync(h_alpha, alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
         }
-        CT_CUDA(cudaMemcpyAsync(h_xx.data(), xx, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        CT_CUDA(cudaMemcpyAsync(h_gg.data(), gg, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        CT_CUDA(cudaStreamSynchronize(st));
+        CT_CUDA(cudaMemcpyAsync(h_xx, xx, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
+        CT_CUDA(cudaMemcpyAsync(h_gg, gg, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
         return CT_OK;
     };
     auto cert_of = [&]() {
@@ -203,32 +211,38 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         }
         return worst;
     };
+    // One CGLS step (captured once as a CUDA graph and replayed).
+    auto step = [&](cudaStream_t s2) -> ct_status {
+        CT_TRY(apply_rinv(f, false, w.p, w.t, k, w.lp, s2));       // t = R^-1 p
+        CT_TRY(spmm_ax(S, k, w.t, 0.0, nullptr, 1.0, w.q, s2));    // q = A~ t
+        CT_TRY(coldot(M, k, w.q, w.q, w.part, qq, s2));
+        step_scalars<<<bk, 128, 0, s2>>>(k, gamma, qq, alpha);
+        count_launch();
+        axpy_cols<<<bn, 256, 0, s2>>>(n, k, alpha, 1.0, w.t, w.x);  // x += a t
+        count_launch();
+        axpy_cols<<<(unsigned)ceil_div((int64_t)Mk, 256), 256, 0, s2>>>(M, k, alpha, -1.0, w.q, w.r);  // r -= a q
+        count_launch();
+        CT_TRY(coldot(n, k, w.t, w.t, w.part, tt, s2));
+        CT_TRY(coldot(n, k, w.x, w.x, w.part, xx, s2));
+        CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, s2));   // t = A~^T r (reuse)
+        CT_TRY(coldot(n, k, w.t, w.t, w.part, gg, s2));
+        CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, s2));        // s = R^-T t
+        CT_TRY(coldot(n, k, w.s, w.s, w.part, gnew, s2));
+        beta_scalars<<<bk, 128, 0, s2>>>(k, gnew, gamma, beta);
+        count_launch();
+        xpby_cols<<<bn, 256, 0, s2>>>(n, k, w.s, beta, w.p);
+        count_launch();
+        CT_CUDA(cudaGetLastError());
+        return read_back(true, s2);
+    };
+    const uint64_t key = graph_key(f, k, w.r) ^ ((uint64_t)M << 20) ^ 0x5151ull;
     int it = 0;
     double last = INFINITY;
     bool converged = false;
     while (it < max_iter) {
         ++it;
-        CT_TRY(apply_rinv(f, false, w.p, w.t, k, w.lp, st));       // t = R^-1 p
-        CT_TRY(spmm_ax(S, k, w.t, 0.0, nullptr, 1.0, w.q, st));    // q = A~ t
-        CT_TRY(coldot(M, k, w.q, w.q, w.part, qq, st));
-        step_scalars<<<bk, 128, 0, st>>>(k, gamma, qq, alpha);
-        count_launch();
-        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, 1.0, w.t, w.x);  // x += a t
-        count_launch();
-        axpy_cols<<<(unsigned)ceil_div((int64_t)Mk, 256), 256, 0, st>>>(M, k, alpha, -1.0, w.q, w.r);  // r -= a q
-        count_launch();
-        CT_TRY(coldot(n, k, w.t, w.t, w.part, tt, st));
-        CT_TRY(coldot(n, k, w.x, w.x, w.part, xx, st));
-        CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));   // t = A~^T r (reuse)
-        CT_TRY(coldot(n, k, w.t, w.t, w.part, gg, st));
-        CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));        // s = R^-T t
-        CT_TRY(coldot(n, k, w.s, w.s, w.part, gnew, st));
-        beta_scalars<<<bk, 128, 0, st>>>(k, gnew, gamma, beta);
-        count_launch();
-        xpby_cols<<<bn, 256, 0, st>>>(n, k, w.s, beta, w.p);
-        count_launch();
-        CT_CUDA(cudaGetLastError());
-        CT_TRY(read_back(true));
+        CT_TRY(run_graphed(f, f->g_iter, key, st, step));
+        CT_CUDA(cudaStreamSynchronize(st));
         double worst = 0.0;
         if (use_cert) {
             worst = cert_of();
@@ -250,7 +264,8 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         CT_TRY(spmm_ax(S, k, w.x, 1.0, w.btil, -1.0, w.r, st));
         CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));
         CT_TRY(coldot(n, k, w.t, w.t, w.part, gg, st));
-        CT_TRY(read_back(false));
+        CT_TRY(read_back(false, st));
+        CT_CUDA(cudaStreamSynchronize(st));
         last = cert_of();
         if (last <= tol) {
             converged = true;

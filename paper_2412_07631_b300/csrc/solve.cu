@@ -32,7 +32,8 @@ ct_status solve_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X,
     void *Bt = f->Bt.ptr;
     CT_TRY(copy_convert_2d(io_kind(f), B, ldb, fac_kind(f), Bt, ldbt, m, k, s));
     if (M > m) CT_TRY(fill_zero_2d(f->fp64, (char *)Bt + f->es() * m, ldbt, M - m, k, s));
-    CT_TRY(direct_solve_inplace(f, Bt, ldbt, k, s));
+    CT_TRY(run_graphed(f, f->g_direct, graph_key(f, k, Bt), s,
+                       [&](cudaStream_t st) { return direct_solve_inplace(f, Bt, ldbt, k, st); }));
     CT_TRY(copy_convert_2d(fac_kind(f), Bt, ldbt, io_kind(f), X, ldx, n, k, s));
     if (info) {
         info->iterations = 0;

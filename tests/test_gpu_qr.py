@@ -136,3 +136,22 @@ def test_tf32_refined_reaches_1e6(oracle_mod, ns, nv, nb, sl, noisy):
     Xg = F.solve(Bt, max_iter=30, tol=1e-9).cpu().numpy().T
     print("refine info", F.last_info)
     assert rel_err_cols(Xg, Xo).max() <= 1e-6
+
+
+@pytest.mark.gpu
+def test_graph_replay_matches_eager(oracle_mod):
+    """Repeated solves replay captured CUDA graphs (warm-up, capture, replay):
+    the results equal the eager launches bit for bit."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, 24, 40, 36, 0.05, 5, True)
+    sysg = ct.System(ct.make_geometry(24, 40, 36, 0.05), "fp32")
+    F = sysg.factor("tf32")
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    F.graphs = False
+    ref = F.solve(Bt, max_iter=12, tol=1e-12, allow_noconv=True).clone()
+    F.graphs = True
+    outs = [F.solve(Bt, max_iter=12, tol=1e-12, allow_noconv=True).clone() for _ in range(4)]
+    for o in outs:
+        assert torch.equal(o, ref)
