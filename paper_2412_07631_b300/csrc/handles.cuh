@@ -1,6 +1,8 @@
 // handles.cuh -- the objects behind ct_system and ct_factor.
 #pragma once
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 struct ct_system_s {
@@ -61,6 +63,11 @@ struct ct_factor_s {
     // work buffers
     ctqr::Scratch gemm_ws, W, W2, G, panel_ws, Bt, trsm_ws, refine_ws, host_pinned, misc, misc2;
     size_t es() const { return fp64 ? 8 : 4; }
+    // One past the last row the reflectors of columns [0, col_end) can touch.
+    // Below the ray rows, A~ holds sqrt(lambda) I: row m+i is untouched until
+    // column i is reached, so reflectors up to column col_end-1 live in rows
+    // [.., m + col_end) and every row beyond keeps its initial content.
+    int64_t row_end(int64_t col_end) const { return M > m ? std::min(M, m + col_end) : M; }
 };
 
 namespace ctqr {

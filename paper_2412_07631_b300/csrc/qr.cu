@@ -10,7 +10,11 @@
 // with three GEMMs (two of them large, on the precision's GEMM engine).
 // V_J lives in place below the diagonal of A; only its NB x NB top triangle
 // (ones on the diagonal, R above it in A) is copied out, so the GEMMs split
-// V_J into that small top block and the in-place rows below it.
+// V_J into that small top block and the in-place rows below it.  With the
+// regularisation rows sqrt(lambda) I below A, the reflectors of block J have
+// no support below row m + j + w (row_end), so the panels, the Gram matrices
+// and both trailing-update GEMMs stop there: the skipped terms are exact
+// zeros, and on average a fifth of the rows drop out at 256x256.
 #include <algorithm>
 
 #include "handles.cuh"
@@ -48,7 +52,7 @@ GemmArgs mk(ct_factor f, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
 ct_status gram(ct_factor f, int64_t j, int w, const void *Vt, void *G, cudaStream_t s) {
     const int64_t NB = f->NB;
     CT_TRY(gemm(mk(f, true, false, w, w, w, 1.0, Vt, NB, Vt, NB, 0.0, G, NB), f->gemm_ws, s));
-    const int64_t kb = f->M - j - w;
+    const int64_t kb = f->row_end(j + w) - j - w;
     if (kb > 0) {
         const void *Vb = at(f->VR, j + w, j, f->lda, f->es());
         CT_TRY(gemm(mk(f, true, false, w, w, kb, 1.0, Vb, f->lda, Vb, f->lda, 1.0, G, NB),
@@ -67,7 +71,7 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     CT_TRY(f->W.ensure(es * (size_t)NB * ncols));
     CT_TRY(f->W2.ensure(es * (size_t)NB * ncols));
     void *W = f->W.ptr, *W2 = f->W2.ptr;
-    const int64_t kb = f->M - j - w;
+    const int64_t kb = f->row_end(j + w) - j - w;  // rows beyond: V is zero there
     const void *Vb = at(f->VR, j + w, j, f->lda, es);
     void *Cb = (char *)C + es * (size_t)w;
     // W = V^T C
@@ -89,7 +93,7 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
 
 ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
     const size_t es = f->es();
-    const int64_t NB = f->NB, nb = f->nb, n = f->n, M = f->M, lda = f->lda;
+    const int64_t NB = f->NB, nb = f->nb, n = f->n, lda = f->lda;
     CT_TRY(f->G.ensure(es * (size_t)NB * NB));
     // misc: Vt_p (ld NB) for inner panels | Y (ld NB) for the T assembly
     CT_TRY(f->misc.ensure(2 * es * (size_t)NB * NB));
@@ -104,7 +108,7 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
         CT_CUDA(cudaMemsetAsync(TJ, 0, es * (size_t)NB * NB, s));
         for (int64_t p = j; p < j + w; p += nb) {
             const int wp = (int)std::min<int64_t>(nb, j + w - p);
-            CT_TRY(panel_qr(f->fp64, f->VR, lda, M, p, wp, f->tau, f->panel_ws, s));
+            CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s));
             // T_p of this panel goes straight into its diagonal block of T_J.
             void *Tp = at(TJ, p - j, p - j, NB, es);
             CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
