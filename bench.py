@@ -146,13 +146,16 @@ def make_inputs(ct, torch, name, rank=0):
     return X, np.ascontiguousarray(np.asarray(B).T)  # (n x k) phantoms, (k x m) sinograms
 
 
+NB_OUTER = 0  # 0: the library's default outer block width
+
+
 def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=None):
     """One pass of the hot path.  Returns (X, info, per-phase ms)."""
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
     sysg = ct.System(geom, "fp64" if precision == "fp64" else "fp32")
     ev[1].record()
-    F = sysg.factor(precision)
+    F = sysg.factor(precision, nb_outer=NB_OUTER)
     ev[2].record()
     if host:
         X = F.solve_host(B, max_iter=max_iter, tol=tol)
@@ -214,7 +217,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cert", action="store_true")
+    ap.add_argument("--nb-outer", type=int, default=0, help="outer WY block width (0: default)")
     args = ap.parse_args()
+    global NB_OUTER
+    NB_OUTER = args.nb_outer
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -213,6 +213,25 @@ CT_API ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t 
 CT_API ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
                            int64_t ldgb, const ct_opts *opts, void *stream, ct_solve_info *info);
 
+/* Checkpoint of a factorisation: the paper recomputes A = QR only when A
+ * changes and reuses it for every sinogram of the same geometry (Sec. 2, text
+ * after Eq. 3; Sec. 3.1.2), so a factor can be written to a file and read
+ * back in another run.  The file holds the geometry, the precision and block
+ * sizes, VR (M' x n), tau, and the per-block T and unit-lower V tops, with an
+ * FNV-1a checksum of the payload.  Synchronous (staged through pinned host
+ * memory).  Errors: CT_ERR_ARG (bad path), CT_ERR_HOSTMEM, CT_ERR_CUDA. */
+CT_API ct_status ct_factor_save(ct_factor f, const char *path);
+
+/* Read a factor written by ct_factor_save into *out.  `sys` must have been
+ * built with the same geometry and storage precision; its sparse rows serve
+ * the refinement, so it must outlive the factor.  Like ct_qr_factor, the
+ * factor takes over the system's dense storage (overwritten by V and R); if
+ * another factor already holds it, fresh storage is allocated.  On failure
+ * the storage is handed back but its content is undefined.
+ * Errors: CT_ERR_ARG (missing file, wrong magic/version, checksum mismatch,
+ * geometry or precision mismatch), CT_ERR_OOM, CT_ERR_CUDA. */
+CT_API ct_status ct_factor_load(ct_system sys, const char *path, void *stream, ct_factor *out);
+
 CT_API void ct_system_free(ct_system sys);
 CT_API void ct_factor_free(ct_factor f);
 

@@ -53,7 +53,8 @@ SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info"
            "ct_system_device_ptrs", "ct_system_export", "ct_forward_project", "ct_qr_factor",
            "ct_factor_device_ptrs", "ct_factor_export", "ct_solve", "ct_solve_host",
            "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm", "ct_stats_reset",
-           "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc"]
+           "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc", "ct_factor_save",
+           "ct_factor_load"]
 
 
 def lib_path() -> str:
@@ -89,6 +90,8 @@ def lib():
     L.ct_gemm.argtypes = [I32, C.c_char, C.c_char, I64, I64, I64, C.c_double, vp, I64, vp, I64,
                           C.c_double, vp, I64, vp]
     L.ct_gemm_noalloc.argtypes = list(L.ct_gemm.argtypes)
+    L.ct_factor_save.argtypes = [vp, C.c_char_p]
+    L.ct_factor_load.argtypes = [vp, C.c_char_p, vp, C.POINTER(vp)]
     L.ct_stats_reset.argtypes = [I32]
     L.ct_stats_read.argtypes = [C.POINTER(I64), vp, vp, vp, vp]
     L.ct_stats_dump.argtypes = [C.c_char_p]
@@ -254,6 +257,21 @@ class Factor:
         tau = np.empty(self.n, dt)
         _check(lib().ct_factor_export(self.h, VR.ctypes.data, self.rows, tau.ctypes.data))
         return VR, tau
+
+    def save(self, path: str):
+        """Write this factorisation to a checkpoint file."""
+        _check(lib().ct_factor_save(self.h, path.encode()))
+
+    @classmethod
+    def load(cls, system: "System", path: str, stream=None) -> "Factor":
+        """Read a checkpoint written by save() for a system of the same geometry."""
+        h = C.c_void_p()
+        _check(lib().ct_factor_load(system.h, path.encode(), _stream(stream), C.byref(h)))
+        prec = {v: k for k, v in PRECISIONS.items()}
+        import struct
+        with open(path, "rb") as fh:
+            code = struct.unpack_from("<i", fh.read(16), 12)[0]
+        return cls(h, system, prec[code])
 
     def free(self):
         if getattr(self, "h", None):

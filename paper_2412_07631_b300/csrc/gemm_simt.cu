@@ -185,7 +185,7 @@ ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     const int64_t BN = tc ? 256 : (fp64 ? 64 : 128);
     const int64_t tiles = ceil_div(g.M, BM) * ceil_div(g.N, BN);
     const int64_t target = 2 * (int64_t)num_sms();
-    const int64_t kMinChunk = tc ? 1024 : 512;
+    const int64_t kMinChunk = tc ? 1024 : 128;
     int64_t splits = 1;
     if (tiles < target) splits = std::min(ceil_div(target, tiles), std::max<int64_t>(1, g.K / kMinChunk));
     splits = std::min<int64_t>(splits, 64);

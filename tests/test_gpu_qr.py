@@ -155,3 +155,36 @@ def test_graph_replay_matches_eager(oracle_mod):
     outs = [F.solve(Bt, max_iter=12, tol=1e-12, allow_noconv=True).clone() for _ in range(4)]
     for o in outs:
         assert torch.equal(o, ref)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["tf32", "fp64"])
+def test_factor_checkpoint_roundtrip(oracle_mod, tmp_path, precision):
+    """A factor written to a file and read back (for a freshly built system of
+    the same geometry) solves to the same bits; a corrupted file or another
+    geometry is refused."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, 19, 31, 29, 0.05, 3, True)
+    storage = "fp64" if precision == "fp64" else "fp32"
+    geom = ct.make_geometry(19, 31, 29, 0.05)
+    s1 = ct.System(geom, storage)
+    F1 = s1.factor(precision)
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    x1 = F1.solve(Bt, max_iter=20, tol=1e-10, allow_noconv=True).clone()
+    path = str(tmp_path / "factor.ctqr")
+    F1.save(path)
+    s2 = ct.System(geom, storage)
+    F2 = ct.Factor.load(s2, path)
+    assert F2.precision == precision
+    x2 = F2.solve(Bt, max_iter=20, tol=1e-10, allow_noconv=True)
+    assert torch.equal(x1, x2)
+    raw = bytearray(open(path, "rb").read())
+    raw[-5] ^= 0xFF
+    open(path + ".bad", "wb").write(bytes(raw))
+    with pytest.raises(ct.CTQRError):
+        ct.Factor.load(s2, path + ".bad")
+    s3 = ct.System(ct.make_geometry(19, 31, 30, 0.05), storage)
+    with pytest.raises(ct.CTQRError):
+        ct.Factor.load(s3, path)
