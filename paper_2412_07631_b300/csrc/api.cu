@@ -433,10 +433,6 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
         set_error("precision does not match the system's storage");
         return CT_ERR_ARG;
     }
-    if (o.precision == CT_BF16_REFINE) {
-        set_error("BF16 factorisation is not available in this build");
-        return CT_ERR_UNSUPPORTED;
-    }
     cudaStream_t s = (cudaStream_t)stream;
     ct_factor f = new (std::nothrow) ct_factor_s;
     if (!f) return CT_ERR_HOSTMEM;
@@ -444,6 +440,7 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     f->prec = o.precision;
     f->fp64 = o.precision == CT_FP64;
     f->kind = o.precision == CT_FP64 ? GEMM_F64 : (o.precision == CT_FP32 ? GEMM_F32 : GEMM_TF32);
+    f->upd_kind = o.precision == CT_BF16_REFINE ? GEMM_BF16 : f->kind;
     f->M = sys->rows;
     f->n = sys->n;
     f->m = sys->m;

@@ -155,6 +155,7 @@ extern "C" ct_status ct_factor_load(ct_system sys, const char *path, void *strea
     f->prec = (ct_precision)hd.precision;
     f->fp64 = fp64;
     f->kind = fp64 ? GEMM_F64 : (f->prec == CT_FP32 ? GEMM_F32 : GEMM_TF32);
+    f->upd_kind = f->prec == CT_BF16_REFINE ? GEMM_BF16 : f->kind;
     f->M = hd.M;
     f->n = hd.n;
     f->m = hd.m;

@@ -156,12 +156,82 @@ ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void 
 // for the tensor cores, then split-K partial products) lives in `ws`, which
 // belongs to the caller; nothing process-wide is used, so a captured graph
 // that replays this call references only its caller's buffers.
+// Split-K depth for a tile grid (enough CTAs to cover the machine about
+// twice, each split at least min_chunk deep, chunks multiples of align).
+static void plan_splits(int64_t tiles, int64_t K, int64_t min_chunk, int64_t align,
+                        int64_t *splits_out, int64_t *kchunk_out) {
+    const int64_t target = 2 * (int64_t)num_sms();
+    int64_t splits = 1;
+    if (tiles < target) splits = std::min(ceil_div(target, tiles), std::max<int64_t>(1, K / min_chunk));
+    splits = std::min<int64_t>(splits, 64);
+    int64_t kchunk = K;
+    if (splits > 1) {
+        kchunk = round_up(ceil_div(K, splits), align);
+        splits = ceil_div(K, kchunk);
+    }
+    *splits_out = splits;
+    *kchunk_out = kchunk;
+}
+
+// BF16 tensor-core product: both operands are rounded (to nearest even) into
+// K-major BF16 copies in `ws`, then multiplied with FP32 accumulation.  A
+// product whose B copy would exceed kBf16ChunkBytes is done in column slabs
+// of C, reusing the A copy.
+static ct_status gemm_bf16(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
+    constexpr size_t kBf16ChunkBytes = (size_t)4 << 30;
+    const int64_t ldt = round_up(g.K, 64);
+    const size_t abytes = (size_t)round_up(2 * ldt * g.M, 256);
+    int64_t nslab = g.N;
+    if ((size_t)(2 * ldt) * (size_t)g.N > kBf16ChunkBytes)
+        nslab = std::max<int64_t>(256, (int64_t)(kBf16ChunkBytes / (size_t)(2 * ldt)) / 256 * 256);
+    const size_t bbytes = (size_t)round_up(2 * ldt * nslab, 256);
+    const int64_t tiles = ceil_div(g.M, 128) * ceil_div(nslab, 256);
+    int64_t splits, kchunk;
+    plan_splits(tiles, g.K, 2048, 64, &splits, &kchunk);
+    const size_t pbytes = splits > 1 ? 4 * (size_t)(g.M * nslab * splits) : 0;
+    CT_TRY(ws.ensure(abytes + bbytes + pbytes));
+    void *Ab = ws.ptr, *Bb = (char *)ws.ptr + abytes, *part = (char *)ws.ptr + abytes + bbytes;
+    if (g.ta) CT_TRY(copy_convert_2d(0, g.A, g.lda, 2, Ab, ldt, g.K, g.M, s));
+    else CT_TRY(transpose_any(0, g.A, g.lda, 2, Ab, ldt, g.M, g.K, s));
+    for (int64_t n0 = 0; n0 < g.N; n0 += nslab) {
+        const int64_t nn = std::min(nslab, g.N - n0);
+        const size_t es = 4;
+        if (!g.tb) CT_TRY(copy_convert_2d(0, (const char *)g.B + es * (size_t)(n0 * g.ldb), g.ldb, 2, Bb, ldt, g.K, nn, s));
+        else CT_TRY(transpose_any(0, (const char *)g.B + es * (size_t)n0, g.ldb, 2, Bb, ldt, nn, g.K, s));
+        GemmArgs b = g;
+        b.ta = true;
+        b.tb = false;
+        b.A = Ab;
+        b.lda = ldt;
+        b.B = Bb;
+        b.ldb = ldt;
+        b.N = nn;
+        b.C = (char *)g.C + es * (size_t)(n0 * g.ldc);
+        int64_t sp = splits, kc = kchunk;
+        if (nn != nslab) plan_splits(ceil_div(g.M, 128) * ceil_div(nn, 256), g.K, 2048, 64, &sp, &kc);
+        if (sp <= 1) {
+            CT_TRY(gemm_tc_launch(b, 1, g.K, 0, s));
+            continue;
+        }
+        GemmArgs p = b;
+        p.alpha = 1.0;
+        p.beta = 0.0;
+        p.C = part;
+        p.ldc = g.M;
+        CT_TRY(gemm_tc_launch(p, (int)sp, kc, g.M * nn, s));
+        CT_TRY(splitk_reduce(false, g.M, nn, (int)sp, part, g.alpha, g.beta, b.C, g.ldc, s));
+    }
+    return CT_OK;
+}
+
 ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     if (g0.M < 0 || g0.N < 0 || g0.K < 0) return CT_ERR_ARG;
     if (g0.M == 0 || g0.N == 0) return CT_OK;
+    if (g0.kind == GEMM_BF16 && g0.K > 0) return gemm_bf16(g0, ws, s);
     GemmArgs g = g0;
     const bool fp64 = g.kind == GEMM_F64;
-    bool tc = g.kind == GEMM_TF32 || g.kind == GEMM_BF16;
+    if (g.kind == GEMM_BF16) g.kind = GEMM_F32;  // only reached with K == 0
+    bool tc = g.kind == GEMM_TF32;
     if (tc && (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15) || (g.lda & 3) || (g.ldb & 3))) {
         // A TMA tile must start on a 16-byte boundary; ragged sub-blocks that
         // do not (only at the edges of odd-sized problems) use the FP32 SIMT path.
@@ -184,17 +254,8 @@ ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     const int64_t BM = tc ? 128 : (fp64 ? 64 : 128);
     const int64_t BN = tc ? 256 : (fp64 ? 64 : 128);
     const int64_t tiles = ceil_div(g.M, BM) * ceil_div(g.N, BN);
-    const int64_t target = 2 * (int64_t)num_sms();
-    const int64_t kMinChunk = tc ? 1024 : 128;
-    int64_t splits = 1;
-    if (tiles < target) splits = std::min(ceil_div(target, tiles), std::max<int64_t>(1, g.K / kMinChunk));
-    splits = std::min<int64_t>(splits, 64);
-    int64_t kchunk = g.K;
-    if (splits > 1) {
-        const int64_t align = tc ? 32 : 16;
-        kchunk = round_up(ceil_div(g.K, splits), align);
-        splits = ceil_div(g.K, kchunk);
-    }
+    int64_t splits, kchunk;
+    plan_splits(tiles, g.K, tc ? 1024 : 128, tc ? 32 : 16, &splits, &kchunk);
     const size_t esz = fp64 ? 8 : 4;
     const size_t pbytes = splits > 1 ? esz * (size_t)(g.M * g.N * splits) : 0;
     if (abytes + bbytes + pbytes > 0) CT_TRY(ws.ensure(abytes + bbytes + pbytes));

@@ -1,33 +1,51 @@
 // gemm_tc.cu -- tensor-core GEMM for the WY trailing update and the Q^T
 // application (the dense contractions of the hot path), on sm_103a tcgen05.
 //
-// C = alpha * op(A) * op(B) + beta * C, column-major FP32 storage, TF32
-// operands (the tensor core reads the FP32 bit pattern and uses its TF32
-// part), FP32 accumulation in tensor memory.
+// C = alpha * op(A) * op(B) + beta * C, column-major FP32 C, FP32
+// accumulation in tensor memory.  Two operand forms:
+//   TF32: operands are FP32 in memory; the tensor core reads the FP32 bit
+//         pattern and uses its TF32 part (kind::tf32, K = 8 per MMA).
+//   BF16: operands are bfloat16 copies made by the dispatcher (kind::f16
+//         with BF16 inputs, K = 16 per MMA).
+// Either way one shared-memory stage row is 128 bytes of K (32 FP32 or 64
+// BF16 values), so the swizzled tile layout, the descriptors and the TMA
+// boxes are the same bytes; only the element count per row differs.
 //
 // Operand layouts: op(A) = A^T of a column-major A is "K-major" (each output
-// row's K values contiguous).  TF32 operands must be K-major (the transposed,
+// row's K values contiguous).  Operands must be K-major (the transposed,
 // MN-major operand form yields zeros for 32-bit types on this hardware, as a
 // layout probe showed), so the dispatcher hands this kernel K-major operands
 // only ('T','N' in column-major terms), transposing the other forms first.
-// A K-major tile is one TMA box of 32 x rows: 128-byte rows, 8-row swizzle
-// atoms 1024 B apart.
+// A K-major tile is one TMA box of 128 B x rows: 8-row swizzle atoms 1024 B
+// apart.
 //
 // Persistent kernel: one CTA per SM walks the output tiles (128 x 256, K in
-// 32-deep stages) of its share of the work list.  Warp 0 issues TMA loads
+// 128-byte stages) of its share of the work list.  Warp 0 issues TMA loads
 // into a 4-stage shared-memory ring; warp 1 allocates 512 TMEM columns (two
 // 128 x 256 FP32 accumulators) and one of its threads issues the MMAs (UMMA
-// M=128, N=256, K=8); warps 2-9 drain an accumulator with tcgen05.ld and
-// write C while the MMAs of the next tile fill the other accumulator, so the
-// epilogue traffic (C read and written when beta != 0) overlaps the
-// tensor-core work.  The tile order puts the grid dimension with fewer tiles
-// fastest, so CTAs resident at the same time share the operand tile of the
-// longer dimension through L2.
+// M=128, N=256); warps 2-9 drain an accumulator with tcgen05.ld and write C
+// while the MMAs of the next tile fill the other accumulator.  The tile order
+// puts the grid dimension with fewer tiles fastest, so CTAs resident at the
+// same time share the operand tile of the longer dimension through L2.
+//
+// Epilogue forms.  With beta = 0 (a plain product or a split-K partial) the
+// scaled accumulator is staged in shared memory and written by TMA tensor
+// stores.  With beta = 1 and a short K (the rank-32 panel updates, bound by
+// the C traffic) it is staged the same way and added to C by TMA reduce-add
+// stores, so C is read and written by the copy engine and the L2.
+// fl(c + alpha*acc) is the same rounding either way.  Other cases, or a C
+// that is not 16-byte aligned, use the thread epilogue (C loaded, scaled and
+// stored by threads): for deep products it measured faster than the staged
+// forms, whose shared-memory traffic competes with the MMA operand reads.
+// Each epilogue warp owns two 32 x 16 staging buffers and reuses one only
+// after the copy engine has finished reading it.
 //
 // Every mbarrier wait is bounded (4 s); on expiry the kernel records
 // DEV_TIMEOUT in the device status word, drains and returns.
 #include <algorithm>
 #include <mutex>
+
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -36,15 +54,59 @@ namespace ctqr {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 32, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 4;  // 16 KiB
-constexpr int B_BYTES = BN * BK * 4;  // 32 KiB
+constexpr int BM = 128, BN = 256, ROW_BYTES = 128, STAGES = 4;
+constexpr int A_BYTES = BM * ROW_BYTES;  // 16 KiB
+constexpr int B_BYTES = BN * ROW_BYTES;  // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int ACC_COLS = 256;
 constexpr int TMEM_COLS = 2 * ACC_COLS;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+// epilogue staging: per warp two 32-row x 16-column FP32 boxes
+constexpr int STG_ROWS = 32, STG_COLS = 16;
+constexpr int STG_FLOATS = STG_ROWS * STG_COLS;
+constexpr int STG_BYTES = EPI_WARPS * 2 * STG_FLOATS * 4;  // 32 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STG_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+// K elements per 128-byte stage row and per MMA, by operand form.
+template <int OP> struct OpTraits;
+template <> struct OpTraits<0> {  // TF32
+    static constexpr int BK = 32, MMA_K = 8;
+    static constexpr uint32_t FMT = 2;
+};
+template <> struct OpTraits<1> {  // BF16
+    static constexpr int BK = 64, MMA_K = 16;
+    static constexpr uint32_t FMT = 1;
+};
+
+enum EpiMode : int { EPI_THREADS = 0, EPI_TMA_STORE = 1, EPI_TMA_ADD = 2 };
+
+
+// ---- TMA stores from shared memory (bulk async-groups of the issuing thread) ----
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int32_t x,
+                                             int32_t y, int32_t z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_add_3d(const CUtensorMap *map, const void *src, int32_t x,
+                                           int32_t y, int32_t z) {
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one committed group of this thread still reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() {
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading/stride
 // byte offsets (16-byte units), version 1, 128-byte swizzle.
@@ -58,8 +120,9 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Descriptor of the kk-th K=8 slice of a K-major stage tile: the slice starts
-// kk*32 bytes into each 128-byte row; 8-row swizzle atoms are 1024 B apart.
+// Descriptor of the kk-th MMA slice of a K-major stage tile (8 TF32 or 16
+// BF16 values = 32 bytes): the slice starts kk*32 bytes into each 128-byte
+// row; 8-row swizzle atoms are 1024 B apart.
 __device__ __forceinline__ uint64_t slice_desc(uint32_t tile, int kk) {
     return make_desc(tile + kk * 32, 16, 1024);
 }
@@ -83,14 +146,18 @@ struct TileSched {
     }
 };
 
+template <int OP>
 __global__ void __launch_bounds__(THREADS, 1)
-    gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     int64_t M, int64_t N, int64_t K, int64_t kchunk, int splits,
-                     float alpha, float beta, float *C, int64_t ldc, int64_t split_stride,
-                     DevStatus *st) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, int epi,
+                   int64_t M, int64_t N, int64_t K, int64_t kchunk, int splits,
+                   float alpha, float beta, float *C, int64_t ldc, int64_t split_stride,
+                   DevStatus *st) {
+    constexpr int BK = OpTraits<OP>::BK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    float *stage_out = (float *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES + STG_BYTES);
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;   // [2] MMA -> epilogue
     uint64_t *acc_empty = acc_full + 2;    // [2] epilogue -> MMA
@@ -103,6 +170,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
+        if (epi != EPI_THREADS) tma_prefetch_desc(&tmC);
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
@@ -146,8 +214,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_wait(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, st, 2);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
+        constexpr uint32_t F = OpTraits<OP>::FMT;
         const uint32_t idesc = (1u << 4)                       // D = F32
-                               | (2u << 7) | (2u << 10)        // A, B = TF32, both K-major
+                               | (F << 7) | (F << 10)          // A, B = TF32 or BF16, K-major
                                | ((uint32_t)(BN >> 3) << 17)   // N
                                | ((uint32_t)(BM >> 4) << 24);  // M
         int64_t kt_glob = 0, local = 0;
@@ -170,8 +239,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
                 const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk)
-                    tc_mma<0>(d_tmem, slice_desc(sa, kk), slice_desc(sb, kk), idesc,
+                for (int kk = 0; kk < BK / OpTraits<OP>::MMA_K; ++kk)
+                    tc_mma<OP>(d_tmem, slice_desc(sa, kk), slice_desc(sb, kk), idesc,
                               (kt > 0 || kk > 0) ? 1u : 0u);
                 tc_commit(&empty[s]);
             }
@@ -186,6 +255,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int q = warp % 4;            // TMEM lane quarter this warp may access
         const int half = e / 4;            // which 128 of the 256 accumulator columns
         int64_t local = 0;
+        uint32_t nbox = 0;                 // staged boxes issued by this warp
         for (int64_t w = blockIdx.x; w < ts.work; w += gridDim.x, ++local) {
             int64_t mi, ni, z;
             ts.decode(w, mi, ni, z);
@@ -193,9 +263,43 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t use = (uint32_t)(local >> 1);
             if (!mbar_wait(&acc_full[b], use & 1u, st, 4)) break;
             tc_fence_after();
-            float *Cz = C + z * split_stride;
             const int64_t row = mi * BM + 32 * q + lane;
+            float *Cz = C + z * split_stride;
             const uint32_t t0 = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * ACC_COLS + half * 128);
+            if (epi != EPI_THREADS) {
+                // stage 32 x 16 boxes in shared memory; the copy engine stores or adds them
+                float *stg = stage_out + e * 2 * STG_FLOATS;
+                const int64_t row0 = mi * BM + 32 * q;
+                // buffers alternate by boxes issued, so the one group that
+                // wait_group.read 1 may leave in flight is the other buffer's
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(t0 + (uint32_t)(c * 32), r);
+#pragma unroll
+                    for (int hc = 0; hc < 2; ++hc) {
+                        const int64_t col0 = ni * BN + half * 128 + c * 32 + hc * STG_COLS;
+                        if (row0 >= M || col0 >= N) continue;  // box wholly outside C
+                        float *buf = stg + (nbox++ & 1) * STG_FLOATS;
+                        if (lane == 0) bulk_wait_read_1();
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < STG_COLS; ++j)
+                            buf[j * STG_ROWS + lane] = alpha * __uint_as_float(r[hc * STG_COLS + j]);
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            if (epi == EPI_TMA_ADD) tma_add_3d(&tmC, buf, (int32_t)row0, (int32_t)col0, (int32_t)z);
+                            else tma_store_3d(&tmC, buf, (int32_t)row0, (int32_t)col0, (int32_t)z);
+                            bulk_commit();
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[b]);
+                continue;
+            }
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 uint32_t r[32];
@@ -222,6 +326,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
+        // the staged boxes must be written out (and their buffers read) before exit
+        if (epi != EPI_THREADS && lane == 0) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
@@ -251,26 +357,28 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D FP32 tensor map over a column-major rows x cols matrix (ld elements),
-// box = box_rows (contiguous dim) x box_cols, 128-byte swizzle.
-ct_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld,
-                   uint32_t box_rows, uint32_t box_cols) {
+// 2-D tensor map over a column-major rows x cols matrix (ld elements) of
+// FP32 or BF16, box = box_rows (contiguous dim) x box_cols, 128-byte swizzle.
+ct_status make_map(CUtensorMap *map, bool bf16, const void *base, int64_t rows, int64_t cols,
+                   int64_t ld, uint32_t box_rows, uint32_t box_cols) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled unavailable");
         return CT_ERR_CUDA;
     }
-    if (((uintptr_t)base & 15) || ((ld * 4) & 15)) {
+    const int64_t es = bf16 ? 2 : 4;
+    if (((uintptr_t)base & 15) || ((ld * es) & 15)) {
         set_error("TMA operand not 16-byte aligned (base %p, ld %lld)", base, (long long)ld);
         return CT_ERR_ARG;
     }
     cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
     cuuint32_t box[2] = {box_rows, box_cols};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides,
-                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d) rows=%lld cols=%lld ld=%lld", (int)r,
                   (long long)rows, (long long)cols, (long long)ld);
@@ -279,65 +387,100 @@ ct_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t col
     return CT_OK;
 }
 
-}  // namespace
+// 3-D FP32 map over C (M x N, ld ldc) and its split-K copies (split_stride
+// apart), box 32 x 16 x 1 unswizzled: the epilogue's staging layout.
+ct_status make_map_c(CUtensorMap *map, const void *C, int64_t M, int64_t N, int64_t ldc,
+                     int splits, int64_t split_stride) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return CT_ERR_CUDA;
+    }
+    const int64_t s2 = splits > 1 ? split_stride : round_up(ldc * N, 4);
+    cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)N, (cuuint64_t)std::max(splits, 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)(ldc * 4), (cuuint64_t)(s2 * 4)};
+    cuuint32_t box[3] = {STG_ROWS, STG_COLS, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(C), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled (C) failed (%d)", (int)r);
+        return CT_ERR_CUDA;
+    }
+    return CT_OK;
+}
 
-ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
-                         cudaStream_t s) {
-    if (g.kind != GEMM_TF32) {
-        set_error("BF16 tensor-core GEMM not available in this build");
-        return CT_ERR_UNSUPPORTED;
-    }
-    static bool attr_set = false;
-    if (!attr_set) {
-        CT_CUDA(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     SMEM_BYTES));
-        attr_set = true;
-    }
-    if (!g.ta || g.tb) {
-        set_error("tensor-core GEMM takes K-major operands only");
-        return CT_ERR_ARG;
-    }
-    CUtensorMap ma, mb;
-    // op(A) = A^T, A stored K x M (K contiguous): box {32 (K), 128 (M)}.
-    CT_TRY(make_map(&ma, g.A, g.K, g.M, g.lda, BK, BM));
-    // op(B) = B, B stored K x N (K contiguous): box {32 (K), 256 (N)}.
-    CT_TRY(make_map(&mb, g.B, g.K, g.N, g.ldb, BK, BN));
+constexpr int64_t kTmaAddMaxK = 64;
+
+// Epilogue form for this call (see the file comment).
+int pick_epilogue(const GemmArgs &g, int splits, int64_t split_stride) {
+    const bool aligned = ((uintptr_t)g.C & 15) == 0 && (g.ldc & 3) == 0 &&
+                         (splits <= 1 || (split_stride & 3) == 0) && g.M < (1LL << 31) &&
+                         g.N < (1LL << 31);
+    if (!aligned) return EPI_THREADS;
+    if (g.beta == 0.0) return EPI_TMA_STORE;
+    // Reduce-add pays for short products (rank-32 panel updates), where C
+    // traffic dominates; for deep ones the thread epilogue measured faster.
+    if (g.beta == 1.0 && splits <= 1 && g.K <= kTmaAddMaxK) return EPI_TMA_ADD;
+    return EPI_THREADS;
+}
+
+template <int OP>
+ct_status launch_tc(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
+                    DevStatus *status, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(gemm_tc_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM_BYTES);
+    });
+    CT_CUDA(attr_err);
+    constexpr int BK = OpTraits<OP>::BK;
+    CUtensorMap ma, mb, mc;
+    // op(A) = A^T, A stored K x M (K contiguous): box {BK (K), 128 (M)}.
+    CT_TRY(make_map(&ma, OP == 1, g.A, g.K, g.M, g.lda, BK, BM));
+    // op(B) = B, B stored K x N (K contiguous): box {BK (K), 256 (N)}.
+    CT_TRY(make_map(&mb, OP == 1, g.B, g.K, g.N, g.ldb, BK, BN));
+    const int epi = pick_epilogue(g, splits, split_stride);
+    if (epi != EPI_THREADS) CT_TRY(make_map_c(&mc, g.C, g.M, g.N, g.ldc, splits, split_stride));
+    else memset(&mc, 0, sizeof(mc));
     const int64_t work = ceil_div(g.M, BM) * ceil_div(g.N, BN) * splits;
     dim3 grid((unsigned)std::min<int64_t>(work, num_sms()));
-    ProfScope prof(PROF_TC_GEMM, s, 2.0 * g.M * g.N * g.K,
-                   4.0 * ((double)g.M * g.K + (double)g.K * g.N +
-                          (double)g.M * g.N * splits * (g.beta != 0.0 ? 2 : 1)),
-                   g.M, g.N, g.K, splits);
-    gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(
-        ma, mb, g.M, g.N, g.K, kchunk, splits, (float)g.alpha, (float)g.beta,
-        (float *)g.C, g.ldc, split_stride, device_status());
+    gemm_tc_kernel<OP><<<grid, THREADS, SMEM_BYTES, s>>>(
+        ma, mb, mc, epi, g.M, g.N, g.K, kchunk, splits, (float)g.alpha, (float)g.beta,
+        (float *)g.C, g.ldc, split_stride, status);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
 }
 
-// Same kernel and tile choice as gemm_tc_launch, with the status word given by
-// the caller and no accounting scope; used by the allocation-free entry point.
+}  // namespace
+
+// K-major operands only: TF32 (FP32 in memory) or BF16 copies.
+ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
+                         cudaStream_t s) {
+    if (g.kind != GEMM_TF32 && g.kind != GEMM_BF16) return CT_ERR_ARG;
+    if (!g.ta || g.tb) {
+        set_error("tensor-core GEMM takes K-major operands only");
+        return CT_ERR_ARG;
+    }
+    const double ebytes = g.kind == GEMM_BF16 ? 2.0 : 4.0;
+    ProfScope prof(PROF_TC_GEMM, s, 2.0 * g.M * g.N * g.K,
+                   ebytes * ((double)g.M * g.K + (double)g.K * g.N) +
+                       4.0 * (double)g.M * g.N * splits * (g.beta != 0.0 ? 2 : 1),
+                   g.M, g.N, g.K, splits);
+    return g.kind == GEMM_BF16 ? launch_tc<1>(g, splits, kchunk, split_stride, device_status(), s)
+                               : launch_tc<0>(g, splits, kchunk, split_stride, device_status(), s);
+}
+
+// Same kernel and tile choice as gemm_tc_launch (TF32), with the status word
+// given by the caller and no accounting scope; used by the allocation-free
+// entry point.
 ct_status gemm_tc_launch_status(const GemmArgs &g, int splits, int64_t kchunk,
                                 int64_t split_stride, DevStatus *status, cudaStream_t s) {
     if (g.kind != GEMM_TF32 || !g.ta || g.tb) return CT_ERR_ARG;
-    static bool attr_set_nb = false;
-    if (!attr_set_nb) {
-        CT_CUDA(cudaFuncSetAttribute(gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     SMEM_BYTES));
-        attr_set_nb = true;
-    }
-    CUtensorMap ma, mb;
-    CT_TRY(make_map(&ma, g.A, g.K, g.M, g.lda, BK, BM));
-    CT_TRY(make_map(&mb, g.B, g.K, g.N, g.ldb, BK, BN));
-    const int64_t work = ceil_div(g.M, BM) * ceil_div(g.N, BN) * splits;
-    dim3 grid((unsigned)std::min<int64_t>(work, num_sms()));
-    gemm_tf32_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(
-        ma, mb, g.M, g.N, g.K, kchunk, splits, (float)g.alpha, (float)g.beta,
-        (float *)g.C, g.ldc, split_stride, status);
-    count_launch();
-    CT_CUDA(cudaGetLastError());
-    return CT_OK;
+    return launch_tc<0>(g, splits, kchunk, split_stride, status, s);
 }
 
 }  // namespace ctqr

@@ -39,7 +39,8 @@ struct ct_factor_s {
     ct_system sys = nullptr;  // borrowed (sparse rows for FP64 refinement)
     ct_precision prec = CT_FP64;
     bool fp64 = true;
-    ctqr::GemmKind kind = ctqr::GEMM_F64;
+    ctqr::GemmKind kind = ctqr::GEMM_F64;      // GEMMs of the solve, Gram and T
+    ctqr::GemmKind upd_kind = ctqr::GEMM_F64;  // the two large trailing-update GEMMs of the QR
     int64_t M = 0, n = 0, m = 0, lda = 0;
     void *VR = nullptr;   // owned: R above the diagonal, V below
     void *tau = nullptr;  // owned: n scalars

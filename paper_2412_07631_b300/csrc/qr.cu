@@ -63,8 +63,10 @@ ct_status gram(ct_factor f, int64_t j, int w, const void *Vt, void *G, cudaStrea
 
 // C[j:M, 0:ncols] <- (I - V op(T) V^T) C, op(T) = T^T for Q^T, T for Q.
 // C points at row j of the target; V is the block at column j of width w.
+// `big` is the engine of the two products over the rows below the top block
+// (V_b^T C_b and C_b -= V_b W2), the bulk of the flops.
 ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void *T, bool qt,
-                      void *C, int64_t ldc, int64_t ncols, cudaStream_t s) {
+                      void *C, int64_t ldc, int64_t ncols, cudaStream_t s, GemmKind big) {
     if (ncols <= 0) return CT_OK;
     const int64_t NB = f->NB;
     const size_t es = f->es();
@@ -76,16 +78,20 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     void *Cb = (char *)C + es * (size_t)w;
     // W = V^T C
     CT_TRY(gemm(mk(f, true, false, w, ncols, w, 1.0, Vt, NB, C, ldc, 0.0, W, NB), f->gemm_ws, s));
-    if (kb > 0)
-        CT_TRY(gemm(mk(f, true, false, w, ncols, kb, 1.0, Vb, f->lda, Cb, ldc, 1.0, W, NB),
-                    f->gemm_ws, s));
+    if (kb > 0) {
+        GemmArgs g = mk(f, true, false, w, ncols, kb, 1.0, Vb, f->lda, Cb, ldc, 1.0, W, NB);
+        g.kind = big;
+        CT_TRY(gemm(g, f->gemm_ws, s));
+    }
     // W2 = op(T) W
     CT_TRY(gemm(mk(f, qt, false, w, ncols, w, 1.0, T, NB, W, NB, 0.0, W2, NB), f->gemm_ws, s));
     // C -= V W2
     CT_TRY(gemm(mk(f, false, false, w, ncols, w, -1.0, Vt, NB, W2, NB, 1.0, C, ldc), f->gemm_ws, s));
-    if (kb > 0)
-        CT_TRY(gemm(mk(f, false, false, kb, ncols, w, -1.0, Vb, f->lda, W2, NB, 1.0, Cb, ldc),
-                    f->gemm_ws, s));
+    if (kb > 0) {
+        GemmArgs g = mk(f, false, false, kb, ncols, w, -1.0, Vb, f->lda, W2, NB, 1.0, Cb, ldc);
+        g.kind = big;
+        CT_TRY(gemm(g, f->gemm_ws, s));
+    }
     return CT_OK;
 }
 
@@ -117,7 +123,7 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
             const int64_t ncols_in = j + w - (p + wp);
             if (ncols_in > 0)
                 CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,
-                                   ncols_in, s));
+                                   ncols_in, s, f->upd_kind));
         }
         CT_TRY(extract_vtop(f->fp64, f->VR, lda, j, w, VtJ, NB, s));
         if (w > nb) {
@@ -137,7 +143,8 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
             }
         }
         if (j + w < n)
-            CT_TRY(apply_block(f, j, w, VtJ, TJ, true, at(f->VR, j, j + w, lda, es), lda, n - j - w, s));
+            CT_TRY(apply_block(f, j, w, VtJ, TJ, true, at(f->VR, j, j + w, lda, es), lda, n - j - w, s,
+                               f->upd_kind));
     }
     return CT_OK;
 }
@@ -152,7 +159,7 @@ ct_status apply_q_blocks(ct_factor f, bool transpose, void *C, int64_t ldc, int6
         const int w = (int)std::min<int64_t>(NB, f->n - j);
         const void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
         const void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
-        CT_TRY(apply_block(f, j, w, VtJ, TJ, transpose, (char *)C + es * (size_t)j, ldc, k, s));
+        CT_TRY(apply_block(f, j, w, VtJ, TJ, transpose, (char *)C + es * (size_t)j, ldc, k, s, f->kind));
     }
     return CT_OK;
 }

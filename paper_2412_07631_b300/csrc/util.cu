@@ -3,9 +3,19 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
 namespace ctqr {
 
 namespace {
+
+template <typename D> __device__ __forceinline__ D cvt(float v) { return (D)v; }
+template <typename D> __device__ __forceinline__ D cvt(double v) { return (D)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
 
 template <typename S, typename D>
 __global__ void copy_convert_kernel(const S *src, int64_t lds, D *dst, int64_t ldd, int64_t rows,
@@ -13,7 +23,28 @@ __global__ void copy_convert_kernel(const S *src, int64_t lds, D *dst, int64_t l
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * cols) return;
     int64_t i = idx % rows, j = idx / rows;
-    dst[i + j * ldd] = (D)src[i + j * lds];
+    dst[i + j * ldd] = cvt<D>(src[i + j * lds]);
+}
+
+// FP32 -> BF16 (round to nearest even), column by column: blockIdx.y strides
+// over columns, each thread converts 4 consecutive rows.
+__global__ void to_bf16_kernel(const float *src, int64_t lds, __nv_bfloat16 *dst, int64_t ldd,
+                               int64_t rows, int64_t cols) {
+    const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= rows) return;
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y) {
+        const float *sp = src + j * lds + i;
+        __nv_bfloat16 *dp = dst + j * ldd + i;
+        if (i + 4 <= rows) {
+            const float a = sp[0], b = sp[1], c = sp[2], d = sp[3];
+            dp[0] = __float2bfloat16_rn(a);
+            dp[1] = __float2bfloat16_rn(b);
+            dp[2] = __float2bfloat16_rn(c);
+            dp[3] = __float2bfloat16_rn(d);
+        } else {
+            for (int64_t r = i; r < rows; ++r) dst[j * ldd + r] = __float2bfloat16_rn(src[j * lds + r]);
+        }
+    }
 }
 
 template <typename T>
@@ -61,7 +92,7 @@ __global__ void transpose_kernel(const S *src, int64_t lds, D *dst, int64_t ldd,
     const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         int64_t i = i0 + threadIdx.x, j = j0 + r;
-        if (i < rows && j < cols) tile[r][threadIdx.x] = (D)src[i + j * lds];
+        if (i < rows && j < cols) tile[r][threadIdx.x] = cvt<D>(src[i + j * lds]);
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -76,7 +107,17 @@ ct_status transpose_any(int src_kind, const void *src, int64_t lds, int dst_kind
                         int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
     if (rows == 0 || cols == 0) return CT_OK;
     dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32)), block(32, 8);
-    if (src_kind == 1 && dst_kind == 1) {
+    if (dst_kind == 2) {  // FP32 -> BF16
+        if (src_kind != 0) return CT_ERR_ARG;
+        for (int64_t c0 = 0; c0 < cols; c0 += 32 * 65535LL) {  // grid.y limit
+            const int64_t cc = std::min<int64_t>(cols - c0, 32 * 65535LL);
+            dim3 g2((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cc, 32));
+            transpose_kernel<float, __nv_bfloat16><<<g2, block, 0, s>>>(
+                (const float *)src + c0 * lds, lds, (__nv_bfloat16 *)dst + c0, ldd, rows, cc);
+            count_launch();
+        }
+    }
+    else if (src_kind == 1 && dst_kind == 1) {
         transpose_kernel<double, double><<<grid, block, 0, s>>>((const double *)src, lds, (double *)dst, ldd, rows, cols);
         count_launch();
     }
@@ -106,7 +147,13 @@ ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_ki
     const int64_t total = rows * cols;
     if (total == 0) return CT_OK;
     const unsigned b = (unsigned)ceil_div(total, 256);
-    if (src_kind == 0 && dst_kind == 0) {
+    if (dst_kind == 2) {  // FP32 -> BF16
+        if (src_kind != 0) return CT_ERR_ARG;
+        dim3 g2((unsigned)ceil_div(ceil_div(rows, 4), 256), (unsigned)std::min<int64_t>(cols, 32768));
+        to_bf16_kernel<<<g2, 256, 0, s>>>((const float *)src, lds, (__nv_bfloat16 *)dst, ldd, rows, cols);
+        count_launch();
+    }
+    else if (src_kind == 0 && dst_kind == 0) {
         copy_convert_kernel<float, float><<<b, 256, 0, s>>>((const float *)src, lds, (float *)dst, ldd, rows, cols);
         count_launch();
     }

@@ -33,7 +33,8 @@ def c2_case():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4), ("tf32", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4), ("tf32", 1e-6),
+                                           ("bf16", 1e-6)])
 def test_c2_against_lapack_oracle(c2_case, precision, tol):
     torch = need_cuda()
     import paper_2412_07631_b300 as ct

@@ -1,7 +1,10 @@
 """GEMM engine behind the WY updates and the Q^T application (tcgen05 TF32
-tensor cores; CUDA-core FP32/FP64) against a float64 matmul of the same
-operands.  TF32 operands are pre-rounded to TF32 so the tensor-core products
-are exact and only FP32 accumulation error remains."""
+and BF16 tensor cores; CUDA-core FP32/FP64) against a float64 matmul of the
+same operands.  Tensor-core operands are pre-rounded to TF32 (truncation, as
+the hardware reads FP32) or BF16 (nearest even, as the engine converts), so
+the products are exact and only FP32 accumulation error remains.  beta = 0
+and beta = 1 select the TMA store and reduce-add epilogues when C is 16-byte
+aligned; other values the thread epilogue."""
 import numpy as np
 import pytest
 
@@ -16,11 +19,21 @@ def tf32_round(a):
     return b.view(np.float32)
 
 
+def bf16_round(a):
+    u = a.astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+CASES = ([(k, b) for k in ("tf32", "bf16") for b in (-0.5, 0.0, 1.0)] +
+         [("fp32", -0.5), ("fp64", -0.5)])
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("kind", ["tf32", "fp32", "fp64"])
+@pytest.mark.parametrize("kind,beta", CASES)
 @pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "N"), ("N", "T"), ("T", "T")])
 @pytest.mark.parametrize("M,N,K", SHAPES)
-def test_gemm_matches_float64(kind, ta, tb, M, N, K):
+def test_gemm_matches_float64(kind, beta, ta, tb, M, N, K):
     torch = need_cuda()
     import paper_2412_07631_b300 as ct
     rng = np.random.default_rng(M * 7 + N * 3 + K)
@@ -35,11 +48,13 @@ def test_gemm_matches_float64(kind, ta, tb, M, N, K):
     Cm = rng.uniform(-1, 1, (N, ldc)).astype(dt)
     if kind == "tf32":
         A, B = tf32_round(A), tf32_round(B)
+    elif kind == "bf16":
+        A, B = bf16_round(A), bf16_round(B)
     Amat = A[:, :ra].T.astype(np.float64)  # stored matrix ra x ca
     Bmat = B[:, :rb].T.astype(np.float64)
     opA = Amat.T if ta == "T" else Amat
     opB = Bmat.T if tb == "T" else Bmat
-    alpha, beta = 0.75, -0.5
+    alpha = 0.75
     ref = alpha * opA @ opB + beta * Cm[:, :M].T.astype(np.float64)
     dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, Cm))
     ct.gemm(kind, ta, tb, M, N, K, alpha, dA, lda, dB, ldb, beta, dC, ldc)

@@ -120,18 +120,20 @@ def test_adjoint_matches_oracle_gradient(oracle_mod):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
 @pytest.mark.parametrize("ns,nv,nb,sl,noisy", [(32, 60, 46, 0.0, False), (24, 40, 36, 0.05, True),
                                                (19, 31, 29, 0.05, True)])
-def test_tf32_refined_reaches_1e6(oracle_mod, ns, nv, nb, sl, noisy):
-    """TF32 tensor-core factors + FP64 refinement: relative image error
-    <= 1e-6 against the FP64 oracle solution."""
+def test_refined_reaches_1e6(oracle_mod, precision, ns, nv, nb, sl, noisy):
+    """TF32 or BF16 tensor-core factors + FP64 refinement: relative image
+    error <= 1e-6 against the FP64 oracle solution."""
     torch = need_cuda()
     import paper_2412_07631_b300 as ct
     O = oracle_mod
     g, csr, X, B = _case(O, ns, nv, nb, sl, 4, noisy)
     Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
     sysg = ct.System(ct.make_geometry(ns, nv, nb, sl), "fp32")
-    F = sysg.factor("tf32")
+    # small blocks so the BF16 trailing-update GEMMs run at these sizes
+    F = sysg.factor(precision, nb_outer=64 if precision == "bf16" else 0)
     Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
     Xg = F.solve(Bt, max_iter=30, tol=1e-9).cpu().numpy().T
     print("refine info", F.last_info)
