@@ -470,6 +470,11 @@ ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t 
                    ebytes * ((double)g.M * g.K + (double)g.K * g.N) +
                        4.0 * (double)g.M * g.N * splits * (g.beta != 0.0 ? 2 : 1),
                    g.M, g.N, g.K, splits);
+    // Deep products with enough 256 x 256 tiles to occupy the SM pairs run on
+    // the paired kernel (gemm_tc2.cu); short rank updates keep the one-SM
+    // kernel and its TMA epilogues.
+    if (g.K > kTmaAddMaxK && gemm_pair_tiles(g.M, g.N) * splits >= num_sms() / 2)
+        return gemm_pair_launch(g, splits, kchunk, split_stride, s);
     return g.kind == GEMM_BF16 ? launch_tc<1>(g, splits, kchunk, split_stride, device_status(), s)
                                : launch_tc<0>(g, splits, kchunk, split_stride, device_status(), s);
 }

@@ -52,6 +52,11 @@ ct_status gemm_simt_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_
                            cudaStream_t s);
 ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
                          cudaStream_t s);
+// The same product on SM pairs (2-CTA clusters, 256 x 256 tiles); and the
+// number of such tiles of an M x N output.
+ct_status gemm_pair_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
+                           cudaStream_t s);
+int64_t gemm_pair_tiles(int64_t M, int64_t N);
 // As gemm_tc_launch, with an explicit device status word and no accounting.
 ct_status gemm_tc_launch_status(const GemmArgs &g, int splits, int64_t kchunk,
                                 int64_t split_stride, DevStatus *status, cudaStream_t s);

@@ -67,3 +67,16 @@ def test_gemm_matches_float64(kind, beta, ta, tb, M, N, K):
     assert not bad.any(), (np.argwhere(bad)[:5], got[bad][:5], ref[bad][:5])
     # padding rows of C untouched
     np.testing.assert_array_equal(dC.cpu().numpy()[:, M:], Cm[:, M:])
+
+
+PAIR_SHAPES = [(4000, 3000, 300), (1024, 1024, 8192), (2000, 2600, 1500)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind,beta", [(k, b) for k in ("tf32", "bf16") for b in (-0.5, 0.0, 1.0)])
+@pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "T")])
+@pytest.mark.parametrize("M,N,K", PAIR_SHAPES)
+def test_gemm_pairs_match_float64(kind, beta, ta, tb, M, N, K):
+    """Products with enough 256 x 256 tiles run on SM pairs (2-CTA
+    clusters); ragged edges in both dimensions and a split-K case."""
+    test_gemm_matches_float64(kind, beta, ta, tb, M, N, K)
