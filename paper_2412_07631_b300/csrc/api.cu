@@ -556,6 +556,8 @@ void ct_factor_free(ct_factor f) {
     cudaFree(f->Rinv);
     cudaFree(f->RinvT);
     cudaFree(f->Rt);
+    cudaFree(f->RinvB);
+    cudaFree(f->RinvTB);
     cudaFree(f->VR);
     cudaFree(f->tau);
     cudaFree(f->Tall);

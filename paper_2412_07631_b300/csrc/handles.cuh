@@ -53,6 +53,10 @@ struct ct_factor_s {
     // and their transposes (trsm_tb x trsm_tb each), R^T for the tensor-core path
     void *Rinv = nullptr, *RinvT = nullptr, *Rt = nullptr;
     int trsm_tb = 0;
+    // tensor-core path: inverses of the trsm_sb x trsm_sb diagonal superblocks
+    // (and their transposes), so each superblock is one GEMM
+    void *RinvB = nullptr, *RinvTB = nullptr;
+    int trsm_sb = 0;
     int64_t ldrt = 0;
     // captured graphs of the solve, and the stream they run on
     GraphSlot g_direct, g_iter;

@@ -127,10 +127,72 @@ ct_status diag_inverse_launch(int64_t n, const T *R, int64_t ldr, T *Rinv, T *Ri
     return CT_OK;
 }
 
+// Copy the TB x TB inverse blocks onto the diagonals of the SB x SB superblock
+// inverses (zero elsewhere): block b at superblock (b*TB)/SB, local offset.
+template <typename T>
+__global__ void scatter_diag_kernel(int64_t nblk, int TB, int SB, const T *Rinv, T *RinvB) {
+    const int64_t b = blockIdx.x;
+    const int64_t g0 = b * TB;
+    const int64_t sb = g0 / SB, loc = g0 - sb * SB;
+    const T *src = Rinv + (size_t)b * TB * TB;
+    T *dst = RinvB + (size_t)sb * SB * SB + loc + loc * SB;
+    for (int idx = threadIdx.x; idx < TB * TB; idx += blockDim.x) {
+        const int r = idx % TB, c = idx / TB;
+        if (loc + r < SB && loc + c < SB) dst[r + (int64_t)c * SB] = src[r + c * TB];
+    }
+}
+
 }  // namespace
 
-// Inverse diagonal blocks of R (and, for the tensor-core path, R^T), built once
-// per factor on first use.
+// Tensor-core path: inverses of the SB x SB diagonal superblocks of R, by
+// doubling from the TB x TB inverses,
+//   inv([A B; 0 C]) = [inv(A), -inv(A) B inv(C); 0, inv(C)],
+// with the products on the FP32 CUDA cores (exact transposes of each other
+// are kept for R^-1 and R^-T, so the two applications stay adjoint).
+static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
+    const int TB = f->trsm_tb;
+    const int64_t n = f->n;
+    const int SB = (int)std::min<int64_t>(1024, round_up(n, TB));
+    const int64_t nsb = ceil_div(n, SB), nblk = ceil_div(n, TB);
+    const size_t es = f->es(), blk = (size_t)SB * SB;
+    CT_CUDA(cudaMalloc(&f->RinvB, es * nsb * blk));
+    CT_CUDA(cudaMalloc(&f->RinvTB, es * nsb * blk));
+    CT_CUDA(cudaMemsetAsync(f->RinvB, 0, es * nsb * blk, s));
+    scatter_diag_kernel<float><<<(unsigned)nblk, 256, 0, s>>>(nblk, TB, SB, (const float *)f->Rinv,
+                                                              (float *)f->RinvB);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    CT_TRY(f->misc2.ensure(es * blk));
+    void *Y = f->misc2.ptr;
+    auto inv_at = [&](int64_t t, int64_t r, int64_t c) {
+        return (char *)f->RinvB + es * (t * blk + (size_t)r + (size_t)c * SB);
+    };
+    for (int64_t b = TB; b < SB; b *= 2) {
+        for (int64_t t = 0; t < nsb; ++t) {
+            const int64_t s0 = t * SB, s1 = std::min<int64_t>(n, s0 + SB);
+            for (int64_t p = s0; p + b < s1; p += 2 * b) {
+                const int64_t bb = std::min<int64_t>(b, s1 - p - b);
+                // Y = R[p:p+b, p+b:p+b+bb] inv(C)
+                GemmArgs g1{GEMM_F32, false, false, b, bb, bb, 1.0,
+                            (char *)f->VR + es * (size_t)(p + (p + b) * f->lda), f->lda,
+                            inv_at(t, p + b - s0, p + b - s0), SB, 0.0, Y, SB};
+                CT_TRY(gemm(g1, f->trsm_ws, s));
+                // inv block (p, p+b) = -inv(A) Y
+                GemmArgs g2{GEMM_F32, false, false, b, bb, b, -1.0, inv_at(t, p - s0, p - s0), SB, Y, SB,
+                            0.0, inv_at(t, p - s0, p + b - s0), SB};
+                CT_TRY(gemm(g2, f->trsm_ws, s));
+            }
+        }
+    }
+    for (int64_t t = 0; t < nsb; ++t)
+        CT_TRY(transpose_any(0, (char *)f->RinvB + es * t * blk, SB, 0, (char *)f->RinvTB + es * t * blk,
+                             SB, SB, SB, s));
+    f->trsm_sb = SB;
+    return CT_OK;
+}
+
+// Inverse diagonal blocks of R (and, for the tensor-core path, R^T and the
+// superblock inverses), built once per factor on first use.
 ct_status trsm_prepare(ct_factor f, cudaStream_t s) {
     if (f->Rinv) return CT_OK;
     const size_t es = f->es();
@@ -149,6 +211,7 @@ ct_status trsm_prepare(ct_factor f, cudaStream_t s) {
         f->ldrt = round_up(f->n, 32);
         CT_CUDA(cudaMalloc(&f->Rt, es * (size_t)f->ldrt * f->n));
         CT_TRY(transpose_any(0, f->VR, f->lda, 0, f->Rt, f->ldrt, f->n, f->n, s));
+        CT_TRY(build_superblock_inverses(f, s));
     }
     return CT_OK;
 }
@@ -207,6 +270,38 @@ ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, 
         }
         return gemm(g, f->trsm_ws, s);
     };
+    if (f->trsm_sb > 0) {
+        // one GEMM per superblock with its stored inverse, then the coupling
+        const int64_t BS = f->trsm_sb, nbs = ceil_div(n, BS);
+        CT_TRY(f->misc2.ensure(es * (size_t)BS * k));
+        void *tmpB = f->misc2.ptr;
+        for (int64_t t = 0; t < nbs; ++t) {
+            const int64_t sbi = trans ? t : nbs - 1 - t;
+            const int64_t s0 = sbi * BS, s1 = std::min<int64_t>(n, s0 + BS), ns = s1 - s0;
+            CT_CUDA(cudaMemcpy2DAsync(tmpB, es * BS, Cp(s0), es * ldc, es * ns, k,
+                                      cudaMemcpyDeviceToDevice, s));
+            GemmArgs d{};
+            d.kind = f->kind;
+            d.M = ns;
+            d.N = k;
+            d.K = ns;
+            d.alpha = 1.0;
+            d.beta = 0.0;
+            d.B = tmpB;
+            d.ldb = BS;
+            d.C = Cp(s0);
+            d.ldc = ldc;
+            d.lda = BS;
+            d.tb = false;
+            // op(A) = inv(R_ss) = (RinvTB_s)^T, or inv(R_ss)^T = (RinvB_s)^T
+            d.ta = true;
+            d.A = (char *)(trans ? f->RinvB : f->RinvTB) + es * (size_t)sbi * BS * BS;
+            CT_TRY(gemm(d, f->trsm_ws, s));
+            if (!trans) CT_TRY(couple(0, s0, s0, ns));
+            else CT_TRY(couple(s1, n - s1, s0, ns));
+        }
+        return CT_OK;
+    }
     for (int64_t t = 0; t < nsb; ++t) {
         const int64_t sbi = trans ? t : nsb - 1 - t;
         const int64_t s0 = sbi * SB, s1 = std::min<int64_t>(n, s0 + SB);
