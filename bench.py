@@ -373,7 +373,8 @@ def main():
             _, inf, ph = run_step(ct, torch, cg, prec, Bd, args.max_iter, args.tol)
             cmp[prec] = {"qr_tflops": cqr / (ph["qr"] * 1e-3) / 1e12,
                          "slices_per_s": ck / (ph["solve"] * 1e-3),
-                         "refine_iters": inf.get("iterations", 0)}
+                         "refine_iters": inf.get("iterations", 0),
+                         "inner_iters": inf.get("inner_iterations", 0)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -400,6 +401,7 @@ def main():
             "slices_per_s": k / (solve_ms * 1e-3),
             "phases_ms": {"build": build_ms, "qr": qr_ms, "solve_refine": solve_ms},
             "refine_iters": [i.get("iterations") for i in infos],
+            "refine_inner_iters": [i.get("inner_iterations") for i in infos],
             "accuracy": acc,
             "roofline": roofline,
             "kernel_breakdown_ms": breakdown,

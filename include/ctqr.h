@@ -106,10 +106,13 @@ typedef struct {
 #define CT_OPT_NO_GRAPHS 1
 
 typedef struct {
-    int32_t iterations;       /* refinement steps taken (0 for CT_FP64 / CT_FP32) */
+    int32_t iterations;       /* refinement steps taken: FP64 residual + correction
+                                 (0 for CT_FP64 / CT_FP32) */
     double stop_measure;      /* the stopping quantity (see refine_tol) after the last step */
     double rjj_min_abs;       /* min |R_jj| */
     double rjj_max_abs;       /* max |R_jj| */
+    int32_t inner_iterations; /* FP32 inner CGLS steps over all refinement steps
+                                 (ct_solve; PCG steps for ct_solve_adjoint) */
 } ct_solve_info;
 
 typedef struct ct_system_s *ct_system;
@@ -187,10 +190,11 @@ CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau)
  * Sec. 2.1 'dormqr' + 'dtrsm').  B: device, m x k (ray rows only; the
  * library appends the zero rows of b~), ldb >= m.  X: device, n x k,
  * ldx >= n.  Element type: float for a CT_FP32 factor, double otherwise.
- * For refining factors, FP64 iterative refinement follows the first solve
- * (residual and update in FP64, corrections from the low-precision factors)
- * until the stopping quantity of opts->refine_tol is met or refine_max_iter
- * steps.  opts may be NULL (factor's precision, defaults).  info may be NULL.
+ * For refining factors, FP64 iterative refinement follows the first solve:
+ * each step computes the residual b~ - A~ x and A~^T of it in FP64 with the
+ * sparse Siddon matrix, then adds a correction found by FP32 CGLS on the
+ * problem preconditioned with R~ (the low-precision factor), until the
+ * stopping quantity of opts->refine_tol is met or refine_max_iter steps.  opts may be NULL (factor's precision, defaults).  info may be NULL.
  * Synchronises `stream` at the end (to read the convergence state).
  * Errors: CT_ERR_ARG, CT_ERR_NOCONV (X still holds the best iterate),
  * CT_ERR_NONFINITE, CT_ERR_TIMEOUT, CT_ERR_OOM, CT_ERR_CUDA. */
@@ -246,7 +250,8 @@ CT_API ct_status ct_stats_reset(int32_t timing);
 /* Synchronises the device, then returns the number of kernels launched since
  * the last reset and, per class (8 entries each; classes: 0 tensor-core GEMM,
  * 1 CUDA-core GEMM, 2 panel, 3 triangular diagonal blocks, 4 sparse FP64
- * products, 5 Siddon, 6 other), the summed event time in ms, algorithmic
+ * products, 5 Siddon, 6 other, 7 sparse FP32 products), the summed event
+ * time in ms, algorithmic
  * flops, algorithmic bytes and launch count.  Any pointer may be NULL. */
 CT_API ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *bytes,
                                int64_t *count);

@@ -35,7 +35,8 @@ class Opts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("stop_measure", C.c_double),
-                ("rjj_min_abs", C.c_double), ("rjj_max_abs", C.c_double)]
+                ("rjj_min_abs", C.c_double), ("rjj_max_abs", C.c_double),
+                ("inner_iterations", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -321,7 +322,8 @@ class CTSolve:
         return cls._fn.apply(B, factor, max_iter, tol)
 
 
-STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other"]
+STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other",
+                "spmm_fp32"]
 
 
 def stats_reset(timing: bool = False):

@@ -182,6 +182,8 @@ void free_system_storage(ct_system s) {
     cudaFree(s->col_ptr);
     cudaFree(s->csc_row);
     cudaFree(s->csc_val);
+    cudaFree(s->val32);
+    cudaFree(s->csc_val32);
 }
 
 template <typename T>

@@ -18,9 +18,10 @@ struct ct_system_s {
     int64_t *col_ptr = nullptr;
     int32_t *csc_row = nullptr;
     double *csc_val = nullptr;
+    float *val32 = nullptr, *csc_val32 = nullptr;  // FP32 copies (inner refinement solves)
     ctqr::Scratch tmp, tmp2;
     ctqr::SparseSys sparse() const {
-        return {m, n, nnz, geom.sqrt_lambda, row_ptr, col, val, col_ptr, csc_row, csc_val};
+        return {m, n, nnz, geom.sqrt_lambda, row_ptr, col, val, col_ptr, csc_row, csc_val, val32, csc_val32};
     }
 };
 

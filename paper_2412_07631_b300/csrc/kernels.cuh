@@ -109,6 +109,8 @@ struct SparseSys {
     const int64_t *col_ptr;
     const int32_t *csc_row;
     const double *csc_val;
+    const float *val32;      // FP32 copies of val / csc_val (NULL until made)
+    const float *csc_val32;
 };
 // Row-major (slice-fastest) k-column operands:  Y[i*k + s].
 // out = alpha*Y + beta*(A~ X)   (rows m+n if sqrt_lambda > 0, else m)
@@ -117,5 +119,10 @@ ct_status spmm_ax(const SparseSys &S, int64_t k, const double *X, double alpha, 
 // out = alpha*Y + beta*(A~^T Rv)  (n rows)
 ct_status spmm_atr(const SparseSys &S, int64_t k, const double *Rv, double alpha, const double *Y,
                    double beta, double *out, cudaStream_t s);
+// The same products in FP32 (values val32/csc_val32, FP32 vectors and sums).
+ct_status spmm_ax32(const SparseSys &S, int64_t k, const float *X, float alpha, const float *Y,
+                    float beta, float *out, cudaStream_t s);
+ct_status spmm_atr32(const SparseSys &S, int64_t k, const float *Rv, float alpha, const float *Y,
+                     float beta, float *out, cudaStream_t s);
 
 }  // namespace ctqr

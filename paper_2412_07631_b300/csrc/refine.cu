@@ -4,23 +4,34 @@
 // an error of order kappa(A~) * u_low, and for the regularised, noisy
 // problems kappa(A~) * u_low can exceed 1, where classical refinement
 // (x += R~^-1 Q~^T (b~ - A~ x)) has the wrong fixed point or diverges.  The
-// refinement here is Krylov-based: CGLS on the right-preconditioned problem
-//     min_y || A~ R~^-1 y - r0 ||,   r0 = b~ - A~ x0,   x = x0 + R~^-1 y,
-// whose convergence depends on kappa(A~ R~^-1) (close to 1 when R~ is a good
-// factor) rather than on kappa(A~).  The iterate x, the residual r, the
-// search directions and every inner product are FP64; the residual and the
-// back-projection use the exact sparse FP64 Siddon matrix (never the
-// low-precision dense copy); only the two triangular solves with R~ per step
-// run in the factor's precision.  Each slice has its own step lengths.
+// refinement here is two-level.
 //
-// Per step:  t = R~^-1 p,  q = A~ t,  alpha = gamma / ||q||^2,
-//            x += alpha t,  r -= alpha q,  s = R~^-T (A~^T r),
-//            gamma' = ||s||^2,  p = s + (gamma'/gamma) p.
-// Stop (regularised systems) when the certified relative error bound
-// ||A~^T r|| / (lambda ||x||) is <= tol for every slice, verified on a
-// recomputed residual; without regularisation rows when the relative update
-// ||alpha t|| / ||x|| is <= tol; or after max_iter steps (CT_ERR_NOCONV, x
-// holds the last iterate).
+// Outer steps (FP64, at most refine_max_iter):
+//     r = b~ - A~ x,  g = A~^T r        (exact sparse FP64 Siddon matrix)
+//     stop if the certified bound ||g|| / (lambda ||x||) <= tol for every
+//     slice (every singular value of A~ is >= sqrt_lambda, so it bounds
+//     ||x - x*|| / ||x||); without regularisation rows, once the last
+//     correction ||d|| / ||x|| was <= tol
+//     x += d,  d ~ argmin_d || A~ d - r ||   (inner solve)
+// Inner solve (FP32): conjugate gradients on the preconditioned normal
+// equations of the correction problem min_d || A~ d - r ||,
+//     (R~^-T A~^T A~ R~^-1) y = R~^-T g,   d = R~^-1 y,
+// whose convergence depends on kappa(A~ R~^-1) (close to 1 when R~ is a good
+// factor) rather than on kappa(A~).  The normal residual s is updated with
+// products of the search direction only (s -= alpha R~^-T A~^T A~ t), never
+// recomputed from r: for noisy data r keeps the large least-squares residual
+// r* = b~ - A~ x*, and A~^T r taken in FP32 would drown the small part that
+// the correction needs in r*'s rounding errors.  g = A~^T r itself comes from
+// the FP64 outer step.  Vectors and sparse products are FP32 (FP32 copies of
+// the Siddon values), inner products accumulate in FP64, triangular solves
+// use the factor.  The inner solve stops once ||s|| of every slice has dropped
+// by kInnerRed (or after kInnerMax steps).  An inexact correction only slows
+// the outer contraction; the outer residual and the certificate are always
+// FP64, so the FP32 inner arithmetic never limits the final accuracy.
+//
+// Inner step:  t = R~^-1 p,  q = A~ t,  alpha = gamma / ||q||^2,  d += alpha t,
+//              s -= alpha R~^-T (A~^T q),  gamma' = ||s||^2,
+//              p = s + (gamma'/gamma) p.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -31,16 +42,19 @@ namespace ctqr {
 
 namespace {
 
-constexpr int RB = 256;  // rows per reduction block
+constexpr int RB = 256;                // rows per reduction block
+constexpr double kInnerRed = 1e-4;     // inner CGLS: relative reduction of ||s||
+constexpr int kInnerMax = 40;          // inner CGLS: step limit per outer step
 
-// part[b*k + s] = sum over rows [b*RB, (b+1)*RB) of U[i,s]*V[i,s] (row-major, slice fastest)
-__global__ void coldot_partial(int64_t rows, int64_t k, const double *U, const double *V,
-                               double *part) {
+// part[b*k + s] = sum over rows [b*RB, (b+1)*RB) of U[i,s]*V[i,s] (row-major,
+// slice fastest), accumulated in FP64
+template <typename T>
+__global__ void coldot_partial(int64_t rows, int64_t k, const T *U, const T *V, double *part) {
     const int64_t r0 = (int64_t)blockIdx.x * RB;
     const int64_t r1 = min(rows, r0 + RB);
     for (int64_t s = threadIdx.x; s < k; s += blockDim.x) {
         double acc = 0.0;
-        for (int64_t i = r0; i < r1; ++i) acc += U[i * k + s] * V[i * k + s];
+        for (int64_t i = r0; i < r1; ++i) acc += (double)U[i * k + s] * (double)V[i * k + s];
         part[(int64_t)blockIdx.x * k + s] = acc;
     }
 }
@@ -53,24 +67,25 @@ __global__ void coldot_final(int64_t nblk, int64_t k, const double *part, double
     out[s] = acc;
 }
 
-// Y[i,s] += a[s] * X[i,s]   (a per slice)
-__global__ void axpy_cols(int64_t rows, int64_t k, const double *a, double sign, const double *X,
-                          double *Y) {
+// Y[i,s] += sign * a[s] * X[i,s]   (a per slice)
+template <typename T>
+__global__ void axpy_cols(int64_t rows, int64_t k, const double *a, double sign, const T *X, T *Y) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * k) return;
     int64_t s = idx % k;
-    Y[idx] += sign * a[s] * X[idx];
+    Y[idx] += (T)(sign * a[s]) * X[idx];
 }
 
 // P[i,s] = S[i,s] + b[s] * P[i,s]
-__global__ void xpby_cols(int64_t rows, int64_t k, const double *S, const double *b, double *P) {
+template <typename T>
+__global__ void xpby_cols(int64_t rows, int64_t k, const T *S, const double *b, T *P) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * k) return;
     int64_t s = idx % k;
-    P[idx] = S[idx] + b[s] * P[idx];
+    P[idx] = S[idx] + (T)b[s] * P[idx];
 }
 
-// alpha[s] = gamma[s] / qq[s] (0 if qq is 0);  upd[s] = alpha^2 * tt[s]
+// alpha[s] = gamma[s] / qq[s] (0 if qq is 0)
 __global__ void step_scalars(int64_t k, const double *gamma, const double *qq, double *alpha) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= k) return;
@@ -84,17 +99,34 @@ __global__ void beta_scalars(int64_t k, const double *gnew, double *gamma, doubl
     gamma[s] = gnew[s];
 }
 
+__global__ void to_f32_kernel(int64_t total, const double *src, float *dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) dst[i] = (float)src[i];
+}
+
 // out = A - B (elementwise)
 __global__ void sub_kernel(int64_t total, const double *A, const double *B, double *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < total) out[i] = A[i] - B[i];
 }
 
-struct Ws {
-    double *x, *r, *p, *s, *t, *q, *btil;  // row-major FP64
-    double *part, *vec;                    // reductions
-    void *lp;                              // low-precision column-major n x k
-};
+// x += (double) d
+__global__ void add_f32_kernel(int64_t total, const float *d, double *x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) x[i] += (double)d[i];
+}
+
+template <typename T>
+ct_status launch_coldot(int64_t rows, int64_t k, const T *U, const T *V, double *part, double *out,
+                        cudaStream_t s) {
+    const int64_t nblk = ceil_div(rows, RB);
+    coldot_partial<T><<<(unsigned)nblk, 128, 0, s>>>(rows, k, U, V, part);
+    count_launch();
+    coldot_final<<<(unsigned)ceil_div(k, 128), 128, 0, s>>>(nblk, k, part, out);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
 
 }  // namespace
 
@@ -110,80 +142,85 @@ static ct_status residual_sub(int64_t rows, int64_t k, const double *A, const do
 // Per-slice inner products of row-major k-column blocks (deterministic order).
 static ct_status coldot(int64_t rows, int64_t k, const double *U, const double *V, double *part,
                         double *out, cudaStream_t s) {
-    const int64_t nblk = ceil_div(rows, RB);
-    coldot_partial<<<(unsigned)nblk, 128, 0, s>>>(rows, k, U, V, part);
-    count_launch();
-    coldot_final<<<(unsigned)ceil_div(k, 128), 128, 0, s>>>(nblk, k, part, out);
-    count_launch();
-    CT_CUDA(cudaGetLastError());
-    return CT_OK;
+    return launch_coldot<double>(rows, k, U, V, part, out, s);
 }
 
-// t = R~^-1 u (trans = false) or R~^-T u (trans = true) for row-major FP64 u (n x k):
-// convert to the factor's column-major storage, triangular solve, convert back.
-static ct_status apply_rinv(ct_factor f, bool trans, const double *u, double *t, int64_t k,
+// t = R~^-1 u (trans = false) or R~^-T u (trans = true) for row-major u
+// (n x k, FP64 or FP32 by u_kind 1/0): to the factor's column-major storage,
+// triangular solve, back.
+static ct_status apply_rinv(ct_factor f, bool trans, int u_kind, const void *u, void *t, int64_t k,
                             void *lp, cudaStream_t s) {
     const int64_t n = f->n, ldl = round_up(n, 32);
     const int dk = f->fp64 ? 1 : 0;
-    CT_TRY(transpose_any(1, u, k, dk, lp, ldl, k, n, s));  // (k x n row view) -> n x k col-major
+    CT_TRY(transpose_any(u_kind, u, k, dk, lp, ldl, k, n, s));  // (k x n row view) -> n x k col-major
     CT_TRY(trsm_factor(f, trans, lp, ldl, k, s));
-    return transpose_any(dk, lp, ldl, 1, t, k, n, k, s);   // n x k col-major -> row-major
+    return transpose_any(dk, lp, ldl, u_kind, t, k, n, k, s);   // n x k col-major -> row-major
+}
+static ct_status apply_rinv(ct_factor f, bool trans, const double *u, double *t, int64_t k, void *lp,
+                            cudaStream_t s) {
+    return apply_rinv(f, trans, 1, u, t, k, lp, s);
+}
+
+// FP32 copies of the Siddon values for the inner solves (made once per system).
+static ct_status ensure_f32_values(ct_system sys, cudaStream_t s) {
+    if (sys->val32) return CT_OK;
+    const int64_t nnz = std::max<int64_t>(sys->nnz, 1);
+    float *a = nullptr, *b = nullptr;
+    CT_CUDA(cudaMalloc(&a, sizeof(float) * nnz));
+    if (cudaMalloc(&b, sizeof(float) * nnz) != cudaSuccess) {
+        cudaFree(a);
+        return CT_ERR_OOM;
+    }
+    const unsigned g = (unsigned)ceil_div(nnz, 256);
+    if (sys->nnz > 0) {
+        to_f32_kernel<<<g, 256, 0, s>>>(sys->nnz, sys->val, a);
+        count_launch();
+        to_f32_kernel<<<g, 256, 0, s>>>(sys->nnz, sys->csc_val, b);
+        count_launch();
+    }
+    CT_CUDA(cudaGetLastError());
+    sys->val32 = a;
+    sys->csc_val32 = b;
+    return CT_OK;
 }
 
 ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
                      const ct_opts *o, cudaStream_t st, ct_solve_info *info) {
     const ct_system sys = f->sys;
-    const SparseSys S = sys->sparse();
     const int64_t n = f->n, m = f->m, M = f->M;
-    const int max_iter = (o && o->refine_max_iter > 0) ? o->refine_max_iter : 10;
+    const int max_outer = (o && o->refine_max_iter > 0) ? o->refine_max_iter : 10;
     const double tol = (o && o->refine_tol > 0) ? o->refine_tol : 1e-7;
     if (o && o->refine_max_iter < 0) return check_device_status(st);  // refinement disabled
+    CT_TRY(ensure_f32_values(sys, st));
+    const SparseSys S = sys->sparse();
 
-    // workspace
+    // workspace: FP64 x, r, b~, g | FP32 q, d, p, s, t, u | reductions | factor-precision n x k
     const int64_t nblk = ceil_div(std::max(M, n), RB);
     const size_t nk = (size_t)n * k, Mk = (size_t)M * k;
     const size_t ldl = round_up(n, 32);
-    const size_t bytes = sizeof(double) * (3 * Mk + 4 * nk + (size_t)nblk * k + 8 * (size_t)k) +
-                         f->es() * ldl * k + 1024;
+    const size_t bytes = sizeof(double) * (2 * Mk + 2 * nk + (size_t)nblk * k + 12 * (size_t)k) +
+                         sizeof(float) * (Mk + 5 * nk) + f->es() * ldl * k + 4096;
     CT_TRY(f->refine_ws.ensure(bytes));
     char *base = (char *)f->refine_ws.ptr;
     auto take = [&](size_t b) { char *p = base; base += round_up((int64_t)b, 256); return p; };
-    Ws w;
-    w.r = (double *)take(sizeof(double) * Mk);
-    w.q = (double *)take(sizeof(double) * Mk);
-    w.btil = (double *)take(sizeof(double) * Mk);
-    w.x = (double *)take(sizeof(double) * nk);
-    w.p = (double *)take(sizeof(double) * nk);
-    w.s = (double *)take(sizeof(double) * nk);
-    w.t = (double *)take(sizeof(double) * nk);
-    w.part = (double *)take(sizeof(double) * nblk * k);
-    w.vec = (double *)take(sizeof(double) * 8 * k);
-    w.lp = take(f->es() * ldl * k);
-    double *gamma = w.vec, *qq = w.vec + k, *alpha = w.vec + 2 * k, *beta = w.vec + 3 * k,
-           *gnew = w.vec + 4 * k, *tt = w.vec + 5 * k, *xx = w.vec + 6 * k;
+    double *r = (double *)take(sizeof(double) * Mk);
+    double *btil = (double *)take(sizeof(double) * Mk);
+    double *x = (double *)take(sizeof(double) * nk);
+    double *g = (double *)take(sizeof(double) * nk);
+    float *q = (float *)take(sizeof(float) * Mk);
+    float *d = (float *)take(sizeof(float) * nk);
+    float *p = (float *)take(sizeof(float) * nk);
+    float *sv = (float *)take(sizeof(float) * nk);
+    float *t = (float *)take(sizeof(float) * nk);
+    float *u = (float *)take(sizeof(float) * nk);
+    double *part = (double *)take(sizeof(double) * nblk * k);
+    double *vec = (double *)take(sizeof(double) * 12 * k);
+    void *lp = take(f->es() * ldl * k);
+    double *gamma = vec, *qq = vec + k, *alpha = vec + 2 * k, *beta = vec + 3 * k, *gnew = vec + 4 * k,
+           *gg = vec + 5 * k, *xx = vec + 6 * k, *dd = vec + 7 * k;
     const unsigned bn = (unsigned)ceil_div((int64_t)nk, 256), bk = (unsigned)ceil_div(k, 128);
 
-    // b~ (row-major, zero sqrt(lambda) rows), x0 (row-major)
-    CT_CUDA(cudaMemsetAsync(w.btil, 0, sizeof(double) * Mk, st));
-    CT_TRY(transpose_any(1, B, ldb, 1, w.btil, k, m, k, st));
-    CT_TRY(transpose_any(1, X, ldx, 1, w.x, k, n, k, st));
-    // r = b~ - A~ x0 ; s = R^-T A~^T r ; p = s ; gamma = ||s||^2
-    CT_TRY(spmm_ax(S, k, w.x, 1.0, w.btil, -1.0, w.r, st));
-    CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));
-    CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));
-    CT_CUDA(cudaMemcpyAsync(w.p, w.s, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
-    CT_TRY(coldot(n, k, w.s, w.s, w.part, gamma, st));
-
-    // Stopping quantity.  Regularised systems (sqrt_lambda > 0): the certified
-    // bound ||x - x*|| / ||x|| <= ||A~^T r|| / (lambda ||x||) (every singular
-    // value of A~ is >= sqrt_lambda), with r the FP64 residual; once the
-    // recursively updated residual meets it, the residual is recomputed from
-    // scratch (r = b~ - A~ x) and the bound checked again, restarting CG from
-    // the true residual if it fails.  Otherwise the relative update.
-    const bool use_cert = S.sqrt_lambda > 0.0;
-    const double lam = S.sqrt_lambda * S.sqrt_lambda;
-    double *gg = w.vec + 7 * k;
-    // per-slice scalars come back through pinned host memory (tt, xx, alpha, gg)
+    // per-slice scalars come back through pinned host memory: gg, xx, dd, gamma
     if (f->pinned_count < 4 * (size_t)k) {
         if (f->pinned) cudaFreeHost(f->pinned);
         f->pinned = nullptr;
@@ -191,99 +228,109 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         CT_CUDA(cudaMallocHost((void **)&f->pinned, sizeof(double) * 4 * (size_t)k));
         f->pinned_count = 4 * (size_t)k;
     }
-    double *h_tt = f->pinned, *h_xx = f->pinned + k, *h_alpha = f->pinned + 2 * k,
-           *h_gg = f->pinned + 3 * k;
-    auto read_back = [&](bool with_update, cudaStream_t s2) -> ct_status {
-        if (with_update) {
-            CT_CUDA(cudaMemcpyAsync(h_tt, tt, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
-            CT_CUDA(cudaMemcpyAsync(h_alpha, alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
-        }
-        CT_CUDA(cudaMemcpyAsync(h_xx, xx, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
-        CT_CUDA(cudaMemcpyAsync(h_gg, gg, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
-        return CT_OK;
-    };
-    auto cert_of = [&]() {
-        double worst = 0.0;
-        for (int32_t q = 0; q < k; ++q) {
-            const double v = std::sqrt(h_gg[q]) / (lam * std::max(std::sqrt(h_xx[q]), 1e-300));
-            if (!std::isfinite(v)) return (double)INFINITY;
-            worst = std::max(worst, v);
-        }
-        return worst;
-    };
-    // One CGLS step (captured once as a CUDA graph and replayed).
-    auto step = [&](cudaStream_t s2) -> ct_status {
-        CT_TRY(apply_rinv(f, false, w.p, w.t, k, w.lp, s2));       // t = R^-1 p
-        CT_TRY(spmm_ax(S, k, w.t, 0.0, nullptr, 1.0, w.q, s2));    // q = A~ t
-        CT_TRY(coldot(M, k, w.q, w.q, w.part, qq, s2));
+    double *h_gg = f->pinned, *h_xx = f->pinned + k, *h_dd = f->pinned + 2 * k, *h_gamma = f->pinned + 3 * k;
+    std::vector<double> gamma0(k);
+
+    // b~ (row-major, zero sqrt(lambda) rows), x0 (row-major)
+    CT_CUDA(cudaMemsetAsync(btil, 0, sizeof(double) * Mk, st));
+    CT_TRY(transpose_any(1, B, ldb, 1, btil, k, m, k, st));
+    CT_TRY(transpose_any(1, X, ldx, 1, x, k, n, k, st));
+
+    const bool use_cert = S.sqrt_lambda > 0.0;
+    const double lam = S.sqrt_lambda * S.sqrt_lambda;
+
+    // One inner CG step (captured once as a CUDA graph and replayed).
+    auto inner_step = [&](cudaStream_t s2) -> ct_status {
+        CT_TRY(apply_rinv(f, false, 0, p, t, k, lp, s2));              // t = R^-1 p
+        CT_TRY(spmm_ax32(S, k, t, 0.0f, nullptr, 1.0f, q, s2));        // q = A~ t
+        CT_TRY(launch_coldot<float>(M, k, q, q, part, qq, s2));
         step_scalars<<<bk, 128, 0, s2>>>(k, gamma, qq, alpha);
         count_launch();
-        axpy_cols<<<bn, 256, 0, s2>>>(n, k, alpha, 1.0, w.t, w.x);  // x += a t
+        axpy_cols<float><<<bn, 256, 0, s2>>>(n, k, alpha, 1.0, t, d);   // d += a t
         count_launch();
-        axpy_cols<<<(unsigned)ceil_div((int64_t)Mk, 256), 256, 0, s2>>>(M, k, alpha, -1.0, w.q, w.r);  // r -= a q
+        CT_TRY(spmm_atr32(S, k, q, 0.0f, nullptr, 1.0f, u, s2));       // u = A~^T q
+        CT_TRY(apply_rinv(f, true, 0, u, u, k, lp, s2));               // w = R^-T u
+        axpy_cols<float><<<bn, 256, 0, s2>>>(n, k, alpha, -1.0, u, sv);  // s -= a w
         count_launch();
-        CT_TRY(coldot(n, k, w.t, w.t, w.part, tt, s2));
-        CT_TRY(coldot(n, k, w.x, w.x, w.part, xx, s2));
-        CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, s2));   // t = A~^T r (reuse)
-        CT_TRY(coldot(n, k, w.t, w.t, w.part, gg, s2));
-        CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, s2));        // s = R^-T t
-        CT_TRY(coldot(n, k, w.s, w.s, w.part, gnew, s2));
+        CT_TRY(launch_coldot<float>(n, k, sv, sv, part, gnew, s2));
         beta_scalars<<<bk, 128, 0, s2>>>(k, gnew, gamma, beta);
         count_launch();
-        xpby_cols<<<bn, 256, 0, s2>>>(n, k, w.s, beta, w.p);
+        xpby_cols<float><<<bn, 256, 0, s2>>>(n, k, sv, beta, p);
         count_launch();
         CT_CUDA(cudaGetLastError());
-        return read_back(true, s2);
+        CT_CUDA(cudaMemcpyAsync(h_gamma, gamma, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
+        return CT_OK;
     };
-    const uint64_t key = graph_key(f, k, w.r) ^ ((uint64_t)M << 20) ^ 0x5151ull;
-    int it = 0;
+    const uint64_t key = graph_key(f, k, r) ^ ((uint64_t)M << 20) ^ 0x5152ull;
+
+    int outer = 0, inner_total = 0;
     double last = INFINITY;
-    bool converged = false;
-    while (it < max_iter) {
-        ++it;
-        CT_TRY(run_graphed(f, f->g_iter, key, st, step));
+    bool converged = false, have_dd = false;
+    while (true) {
+        // FP64 residual, back-projection and the stopping quantity
+        CT_TRY(spmm_ax(S, k, x, 1.0, btil, -1.0, r, st));        // r = b~ - A~ x
+        CT_TRY(spmm_atr(S, k, r, 0.0, nullptr, 1.0, g, st));    // g = A~^T r
+        CT_TRY(coldot(n, k, g, g, part, gg, st));
+        CT_TRY(coldot(n, k, x, x, part, xx, st));
+        CT_CUDA(cudaMemcpyAsync(h_gg, gg, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CT_CUDA(cudaMemcpyAsync(h_xx, xx, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        if (have_dd) CT_CUDA(cudaMemcpyAsync(h_dd, dd, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CT_CUDA(cudaStreamSynchronize(st));
         double worst = 0.0;
-        if (use_cert) {
-            worst = cert_of();
-        } else {
-            for (int32_t q = 0; q < k; ++q) {
-                const double xn = std::sqrt(h_xx[q]);
-                const double up = std::fabs(h_alpha[q]) * std::sqrt(h_tt[q]);
-                if (!std::isfinite(up)) { worst = INFINITY; break; }
-                worst = std::max(worst, xn > 0 ? up / xn : up);
-            }
+        for (int32_t sl = 0; sl < k; ++sl) {
+            const double xn = std::max(std::sqrt(h_xx[sl]), 1e-300);
+            double v;
+            if (use_cert) v = std::sqrt(h_gg[sl]) / (lam * xn);
+            else v = have_dd ? std::sqrt(h_dd[sl]) / xn : INFINITY;
+            if (!std::isfinite(v)) { worst = INFINITY; break; }
+            worst = std::max(worst, v);
         }
         last = worst;
-        if (!(worst <= tol)) continue;
-        if (!use_cert) {
+        if (worst <= tol) {
             converged = true;
             break;
         }
-        // verify with the residual recomputed from x
-        CT_TRY(spmm_ax(S, k, w.x, 1.0, w.btil, -1.0, w.r, st));
-        CT_TRY(spmm_atr(S, k, w.r, 0.0, nullptr, 1.0, w.t, st));
-        CT_TRY(coldot(n, k, w.t, w.t, w.part, gg, st));
-        CT_TRY(read_back(false, st));
+        if (outer >= max_outer) break;
+        ++outer;
+        // inner CG from y = 0: s = R^-T g with the FP64 back-projection g = A~^T r
+        to_f32_kernel<<<bn, 256, 0, st>>>((int64_t)nk, g, u);
+        count_launch();
+        CT_CUDA(cudaGetLastError());
+        CT_CUDA(cudaMemsetAsync(d, 0, sizeof(float) * nk, st));
+        CT_TRY(apply_rinv(f, true, 0, u, sv, k, lp, st));       // s = R^-T g
+        CT_CUDA(cudaMemcpyAsync(p, sv, sizeof(float) * nk, cudaMemcpyDeviceToDevice, st));
+        CT_TRY(launch_coldot<float>(n, k, sv, sv, part, gamma, st));
+        CT_CUDA(cudaMemcpyAsync(h_gamma, gamma, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CT_CUDA(cudaStreamSynchronize(st));
-        last = cert_of();
-        if (last <= tol) {
-            converged = true;
-            break;
+        for (int32_t sl = 0; sl < k; ++sl) gamma0[sl] = h_gamma[sl];
+        for (int it = 0; it < kInnerMax; ++it) {
+            CT_TRY(run_graphed(f, f->g_iter, key, st, inner_step));
+            ++inner_total;
+            CT_CUDA(cudaStreamSynchronize(st));
+            double red = 0.0;
+            for (int32_t sl = 0; sl < k; ++sl) {
+                const double v = gamma0[sl] > 0.0 ? std::sqrt(h_gamma[sl] / gamma0[sl]) : 0.0;
+                if (!std::isfinite(v)) { red = INFINITY; break; }
+                red = std::max(red, v);
+            }
+            if (red <= kInnerRed) break;
         }
-        // restart from the true residual
-        CT_TRY(apply_rinv(f, true, w.t, w.s, k, w.lp, st));
-        CT_CUDA(cudaMemcpyAsync(w.p, w.s, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
-        CT_TRY(coldot(n, k, w.s, w.s, w.part, gamma, st));
+        // x += d (FP64 accumulation); ||d|| for the unregularised stop
+        add_f32_kernel<<<bn, 256, 0, st>>>((int64_t)nk, d, x);
+        count_launch();
+        CT_CUDA(cudaGetLastError());
+        CT_TRY(launch_coldot<float>(n, k, d, d, part, dd, st));
+        have_dd = true;
     }
-    CT_TRY(transpose_any(1, w.x, k, 1, X, ldx, k, n, st));  // row-major -> X (n x k col-major)
+    CT_TRY(transpose_any(1, x, k, 1, X, ldx, k, n, st));  // row-major -> X (n x k col-major)
     if (info) {
-        info->iterations = it;
+        info->iterations = outer;
+        info->inner_iterations = inner_total;
         info->stop_measure = last;
     }
     CT_TRY(check_device_status(st));
     if (!converged) {
-        set_error("refinement: %d steps, stopping measure %.3g > tol %.3g", it, last, tol);
+        set_error("refinement: %d steps, stopping measure %.3g > tol %.3g", outer, last, tol);
         return CT_ERR_NOCONV;
     }
     return CT_OK;
@@ -383,9 +430,9 @@ ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t 
         CT_TRY(coldot(n, k, p, w, part, pw, st));
         step_scalars<<<bk, 128, 0, st>>>(k, rho, pw, alpha);  // alpha = rho / <p, w>
         count_launch();
-        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, 1.0, p, u);   // u += a p
+        axpy_cols<double><<<bn, 256, 0, st>>>(n, k, alpha, 1.0, p, u);   // u += a p
         count_launch();
-        axpy_cols<<<bn, 256, 0, st>>>(n, k, alpha, -1.0, w, r);  // r -= a w
+        axpy_cols<double><<<bn, 256, 0, st>>>(n, k, alpha, -1.0, w, r);  // r -= a w
         count_launch();
         CT_TRY(measure(true));
         last = stop_value(true);
@@ -405,7 +452,7 @@ ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t 
         CT_TRY(coldot(n, k, r, z, part, rnew, st));
         beta_scalars<<<bk, 128, 0, st>>>(k, rnew, rho, beta);
         count_launch();
-        xpby_cols<<<bn, 256, 0, st>>>(n, k, z, beta, p);      // p = z + b p
+        xpby_cols<double><<<bn, 256, 0, st>>>(n, k, z, beta, p);      // p = z + b p
         count_launch();
         CT_CUDA(cudaGetLastError());
     }
@@ -414,6 +461,7 @@ ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t 
     CT_TRY(transpose_any(1, q, k, 1, gB, ldgb, k, m, st));  // rows 0..m-1 (row-major) -> m x k
     if (info) {
         info->iterations = it;
+        info->inner_iterations = it;
         info->stop_measure = last;
         info->rjj_min_abs = f->rjj_min;
         info->rjj_max_abs = f->rjj_max;

@@ -37,6 +37,7 @@ ct_status solve_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X,
     CT_TRY(copy_convert_2d(fac_kind(f), Bt, ldbt, io_kind(f), X, ldx, n, k, s));
     if (info) {
         info->iterations = 0;
+        info->inner_iterations = 0;
         info->stop_measure = 0.0;
         info->rjj_min_abs = f->rjj_min;
         info->rjj_max_abs = f->rjj_max;
@@ -64,6 +65,7 @@ ct_status adjoint_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void
     CT_TRY(copy_convert_2d(fac_kind(f), Bt, ldbt, io_kind(f), gB, ldgb, m, k, s));
     if (info) {
         info->iterations = 0;
+        info->inner_iterations = 0;
         info->stop_measure = 0.0;
         info->rjj_min_abs = f->rjj_min;
         info->rjj_max_abs = f->rjj_max;

@@ -1,7 +1,8 @@
-// spmm.cu -- FP64 sparse products with the Siddon matrix for k images at
-// once: the forward projection A X, the regularised residual b~ - A~ X and the
+// spmm.cu -- sparse products with the Siddon matrix for k images at once:
+// the forward projection A X, the regularised residual b~ - A~ X and the
 // back-projection A~^T R.  The refinement computes its residuals here, in
-// FP64, from the exact sparse A rather than from the low-precision dense copy.
+// FP64, from the exact sparse A rather than from the low-precision dense
+// copy; its inner correction solves use the same kernels in FP32.
 //
 // Operands are row-major with the slice index fastest (element (i, s) at
 // Y[i*k + s]) so that the k values a nonzero multiplies are one contiguous,
@@ -15,19 +16,20 @@ namespace {
 
 // out[i, :] = alpha*Y[i, :] + beta * sum_q val[q] * X[col[q], :]   (ray rows)
 // and for the sqrt(lambda) rows i = m + j:  (A~ X)[m+j, :] = sl * X[j, :].
-__global__ void spmm_ax_kernel(int64_t m, int64_t n, int64_t k, double sl, const int64_t *row_ptr,
-                               const int32_t *col, const double *val, const double *X, double alpha,
-                               const double *Y, double beta, double *out) {
+template <typename T>
+__global__ void spmm_ax_kernel(int64_t m, int64_t n, int64_t k, T sl, const int64_t *row_ptr,
+                               const int32_t *col, const T *val, const T *X, T alpha,
+                               const T *Y, T beta, T *out) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
-    const int64_t rows = m + (sl > 0.0 ? n : 0);
+    const int64_t rows = m + (sl > T(0) ? n : 0);
     if (row >= rows) return;
     for (int64_t s0 = 0; s0 < k; s0 += 32 * 4) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        T acc[4] = {T(0), T(0), T(0), T(0)};
         if (row < m) {
             for (int64_t q = row_ptr[row]; q < row_ptr[row + 1]; ++q) {
-                const double a = val[q];
-                const double *xr = X + (int64_t)col[q] * k;
+                const T a = val[q];
+                const T *xr = X + (int64_t)col[q] * k;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int64_t s = s0 + lane + 32 * u;
@@ -35,7 +37,7 @@ __global__ void spmm_ax_kernel(int64_t m, int64_t n, int64_t k, double sl, const
                 }
             }
         } else {
-            const double *xr = X + (row - m) * k;
+            const T *xr = X + (row - m) * k;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t s = s0 + lane + 32 * u;
@@ -46,8 +48,8 @@ __global__ void spmm_ax_kernel(int64_t m, int64_t n, int64_t k, double sl, const
         for (int u = 0; u < 4; ++u) {
             const int64_t s = s0 + lane + 32 * u;
             if (s < k) {
-                double v = beta * acc[u];
-                if (alpha != 0.0) v += alpha * Y[row * k + s];
+                T v = beta * acc[u];
+                if (alpha != T(0)) v += alpha * Y[row * k + s];
                 out[row * k + s] = v;
             }
         }
@@ -56,25 +58,26 @@ __global__ void spmm_ax_kernel(int64_t m, int64_t n, int64_t k, double sl, const
 
 // out[j, :] = alpha*Y[j, :] + beta * (sum_{q in col j} csc_val[q] * R[csc_row[q], :]
 //                                     + sl * R[m + j, :])
-__global__ void spmm_atr_kernel(int64_t m, int64_t n, int64_t k, double sl, const int64_t *col_ptr,
-                                const int32_t *csc_row, const double *csc_val, const double *R,
-                                double alpha, const double *Y, double beta, double *out) {
+template <typename T>
+__global__ void spmm_atr_kernel(int64_t m, int64_t n, int64_t k, T sl, const int64_t *col_ptr,
+                                const int32_t *csc_row, const T *csc_val, const T *R,
+                                T alpha, const T *Y, T beta, T *out) {
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (j >= n) return;
     for (int64_t s0 = 0; s0 < k; s0 += 32 * 4) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        T acc[4] = {T(0), T(0), T(0), T(0)};
         for (int64_t q = col_ptr[j]; q < col_ptr[j + 1]; ++q) {
-            const double a = csc_val[q];
-            const double *rr = R + (int64_t)csc_row[q] * k;
+            const T a = csc_val[q];
+            const T *rr = R + (int64_t)csc_row[q] * k;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t s = s0 + lane + 32 * u;
                 if (s < k) acc[u] += a * rr[s];
             }
         }
-        if (sl > 0.0) {
-            const double *rr = R + (m + j) * k;
+        if (sl > T(0)) {
+            const T *rr = R + (m + j) * k;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t s = s0 + lane + 32 * u;
@@ -85,8 +88,8 @@ __global__ void spmm_atr_kernel(int64_t m, int64_t n, int64_t k, double sl, cons
         for (int u = 0; u < 4; ++u) {
             const int64_t s = s0 + lane + 32 * u;
             if (s < k) {
-                double v = beta * acc[u];
-                if (alpha != 0.0) v += alpha * Y[j * k + s];
+                T v = beta * acc[u];
+                if (alpha != T(0)) v += alpha * Y[j * k + s];
                 out[j * k + s] = v;
             }
         }
@@ -102,8 +105,8 @@ ct_status spmm_ax(const SparseSys &S, int64_t k, const double *X, double alpha, 
     const unsigned blocks = (unsigned)ceil_div(rows * 32, 256);
     ProfScope prof(PROF_SPMM, s, 2.0 * (S.nnz + (rows - S.m)) * k,
                    12.0 * S.nnz + 8.0 * (double)k * (S.n + rows * (alpha != 0.0 ? 2 : 1)));
-    spmm_ax_kernel<<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.row_ptr, S.col, S.val, X,
-                                          alpha, Y, beta, out);
+    spmm_ax_kernel<double><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.row_ptr, S.col, S.val,
+                                                  X, alpha, Y, beta, out);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -116,8 +119,38 @@ ct_status spmm_atr(const SparseSys &S, int64_t k, const double *R, double alpha,
     const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
     ProfScope prof(PROF_SPMM, s, 2.0 * (S.nnz + (rows - S.m)) * k,
                    12.0 * S.nnz + 8.0 * (double)k * (rows + S.n * (alpha != 0.0 ? 2 : 1)));
-    spmm_atr_kernel<<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.col_ptr, S.csc_row,
-                                           S.csc_val, R, alpha, Y, beta, out);
+    spmm_atr_kernel<double><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.col_ptr, S.csc_row,
+                                                   S.csc_val, R, alpha, Y, beta, out);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status spmm_ax32(const SparseSys &S, int64_t k, const float *X, float alpha, const float *Y,
+                    float beta, float *out, cudaStream_t s) {
+    const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
+    if (rows == 0 || k == 0) return CT_OK;
+    if (!S.val32) return CT_ERR_ARG;
+    const unsigned blocks = (unsigned)ceil_div(rows * 32, 256);
+    ProfScope prof(PROF_SPMM32, s, 2.0 * (S.nnz + (rows - S.m)) * k,
+                   8.0 * S.nnz + 4.0 * (double)k * (S.n + rows * (alpha != 0.0f ? 2 : 1)));
+    spmm_ax_kernel<float><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.row_ptr, S.col,
+                                                 S.val32, X, alpha, Y, beta, out);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status spmm_atr32(const SparseSys &S, int64_t k, const float *R, float alpha, const float *Y,
+                     float beta, float *out, cudaStream_t s) {
+    if (S.n == 0 || k == 0) return CT_OK;
+    if (!S.csc_val32) return CT_ERR_ARG;
+    const unsigned blocks = (unsigned)ceil_div(S.n * 32, 256);
+    const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
+    ProfScope prof(PROF_SPMM32, s, 2.0 * (S.nnz + (rows - S.m)) * k,
+                   8.0 * S.nnz + 4.0 * (double)k * (rows + S.n * (alpha != 0.0f ? 2 : 1)));
+    spmm_atr_kernel<float><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.col_ptr,
+                                                  S.csc_row, S.csc_val32, R, alpha, Y, beta, out);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
