@@ -278,6 +278,275 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
     }
 }
 
+// ---- register-resident variant (FP32, full 32-column panels) ----------------
+//
+// Same reflectors as panel_qr_kernel, for slabs of up to RPT rows per thread
+// (RPT x 256 rows per CTA): each thread keeps its RPT rows of the 32 panel
+// columns in registers for the whole panel, so the per-column passes touch
+// no shared memory.  Per column, every CTA writes its partial record (dot
+// products, sum of squares, and the diagonal row if it owns it), fences, and
+// takes a ticket from a counter; the CTA that draws the last ticket sums the
+// G records in a fixed order (records split over its warps by index, then
+// the warps in order) and publishes the totals as self-validating words
+// (epoch << 32 | 32 value bits), which every CTA polls without a fence.  One
+// reducer and one published total replace G x G reads of partials, and the
+// fixed order keeps the reflector identical in every CTA and run.  The norm
+// is accumulated per thread in FP64 and summed across threads in FP32; the
+// reflector scalars are FP32 (beta - alpha and alpha - beta never cancel).
+constexpr int RP_THREADS = 256;
+constexpr int RP_WARPS = RP_THREADS / 32;
+constexpr int RP_REC = 72;   // partial record: dots[32] | row[32] | ss  (floats, padded)
+constexpr int RP_TOT = 72;   // total record (64-bit words): dots[32] | row[32] | ss
+
+__device__ __forceinline__ void st_word(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_word(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t tag(unsigned epoch, float v) {
+    return ((uint64_t)epoch << 32) | __float_as_uint(v);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(RP_THREADS, 1)
+    panel_qr_regs_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec,
+                         uint64_t *tot, unsigned *counter, DevStatus *st, int64_t rows_per) {
+    __shared__ float red[RP_WARPS][32];
+    __shared__ float red_ss[RP_WARPS];
+    __shared__ float rowsm[32];
+    __shared__ float coefs_sm[32];
+    __shared__ float coef_row[32];
+    __shared__ float scal_sm, beta_sm;
+    __shared__ int skip_sm, ok_sm, last_sm;
+
+    const unsigned G = gridDim.x;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t r0 = j0 + (int64_t)blockIdx.x * rows_per;
+    const int64_t r1 = min(M, r0 + rows_per);
+    const int64_t nloc = max((int64_t)0, r1 - r0);
+
+    float a[RPT][32];
+    float xc[RPT];  // column c of each row
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int64_t lr = threadIdx.x + (int64_t)i * RP_THREADS;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a[i][k] = (lr < nloc) ? A[(r0 + lr) + (j0 + k) * lda] : 0.0f;
+    }
+    if (threadIdx.x == 0) ok_sm = 1;
+    __syncthreads();
+
+    for (int c = 0; c < 32; ++c) {
+        const int64_t jc = j0 + c;
+        const int par = c & 1;
+        const unsigned epoch = (unsigned)(jc + 1);
+        float *rec_par = rec + (size_t)par * G * RP_REC;
+        uint64_t *tot_par = tot + (size_t)par * RP_TOT;
+        // ---- local partials over rows strictly below jc ----
+        float acc[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] = 0.0f;
+        double ssd = 0.0;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            float xv = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) xv = (k == c) ? a[i][k] : xv;
+            xc[i] = xv;
+        }
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int64_t lr = threadIdx.x + (int64_t)i * RP_THREADS;
+            const int64_t gr = r0 + lr;
+            if (lr < nloc && gr > jc) {
+                const float x = xc[i];
+                ssd += (double)x * (double)x;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) acc[k] += x * a[i][k];
+            }
+            if (lr < nloc && gr == jc) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) rowsm[k] = a[i][k];
+            }
+        }
+        red[warp][lane] = warp_reduce_scatter32<float>(acc, lane);
+        float ss = (float)ssd;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) red_ss[warp] = ss;
+        __syncthreads();
+        const bool owner = jc >= r0 && jc < r1;
+        const unsigned b_own = (unsigned)((jc - j0) / rows_per);
+        // ---- publish the partial record, take a ticket ----
+        if (warp == 0) {
+            float v = 0.0f;
+#pragma unroll
+            for (int w = 0; w < RP_WARPS; ++w) v += red[w][lane];
+            float *mine = rec_par + (size_t)blockIdx.x * RP_REC;
+            mine[lane] = v;
+            if (owner) mine[32 + lane] = rowsm[lane];
+            if (lane == 0) {
+                float t = 0.0f;
+#pragma unroll
+                for (int w = 0; w < RP_WARPS; ++w) t += red_ss[w];
+                mine[64] = t;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();  // the record before the ticket
+                const unsigned ticket = atomicAdd(counter + par, 1u);
+                last_sm = ticket == G - 1;
+                if (ticket == G - 1) __threadfence();  // every record before the reads below
+            }
+        }
+        __syncthreads();
+        if (last_sm) {
+            // ---- the last CTA sums the G records in a fixed order ----
+            float v = 0.0f, sv = 0.0f;
+            for (unsigned b = warp; b < G; b += RP_WARPS) {
+                const float *r = rec_par + (size_t)b * RP_REC;
+                v += __ldcg(r + lane);
+                if (lane == 0) sv += __ldcg(r + 64);
+            }
+            red[warp][lane] = v;
+            if (lane == 0) red_ss[warp] = sv;
+            __syncthreads();
+            if (warp == 0) {
+                float t = 0.0f, ts = 0.0f;
+#pragma unroll
+                for (int w = 0; w < RP_WARPS; ++w) {
+                    t += red[w][lane];
+                    ts += red_ss[w];
+                }
+                const float rowv = __ldcg(rec_par + (size_t)b_own * RP_REC + 32 + lane);
+                if (lane == 0) counter[par] = 0u;  // no CTA takes a ticket for this parity before the total
+                st_word(tot_par + lane, tag(epoch, t));
+                st_word(tot_par + 32 + lane, tag(epoch, rowv));
+                if (lane == 0) st_word(tot_par + 64, tag(epoch, ts));
+            }
+        }
+        // ---- every CTA reads the published totals (warp 0, bounded) ----
+        if (warp == 0) {
+            const uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            uint64_t wd, wr, ws;
+            while (true) {
+                wd = ld_word(tot_par + lane);
+                wr = ld_word(tot_par + 32 + lane);
+                ws = ld_word(tot_par + 64);
+                const bool here = (unsigned)(wd >> 32) == epoch && (unsigned)(wr >> 32) == epoch &&
+                                  (unsigned)(ws >> 32) == epoch;
+                if (__all_sync(0xffffffffu, here)) break;
+                if ((++spins & 15u) == 0) {
+                    int bad = 0;
+                    if (lane == 0) {
+                        if (*((volatile int *)&st->code) != 0) bad = 1;
+                        else if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                            raise_status(st, DEV_TIMEOUT, 21, (int)jc);
+                            bad = 1;
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, bad, 0)) {
+                        if (lane == 0) ok_sm = 0;
+                        break;
+                    }
+                }
+            }
+            if (ok_sm) {
+                // ---- reflector scalars and coefficients (FP32) ----
+                const float totk = __uint_as_float((uint32_t)wd);
+                const float rowk = __uint_as_float((uint32_t)wr);
+                const float ssum = __uint_as_float((uint32_t)ws);
+                const float alpha = __shfl_sync(0xffffffffu, rowk, c);
+                if (lane == 0 && (!isfinite(ssum) || !isfinite(alpha))) raise_status(st, DEV_NONFINITE, 23, (int)jc);
+                if (ssum == 0.0f) {
+                    if (lane == 0) {
+                        skip_sm = 1;
+                        if (blockIdx.x == 0) tau[jc] = 0.0f;
+                    }
+                } else {
+                    const float norm = sqrtf(fmaf(alpha, alpha, ssum));
+                    const float beta = (alpha >= 0.0f) ? -norm : norm;
+                    const float t = (beta - alpha) / beta;
+                    const float scal = 1.0f / (alpha - beta);
+                    const float cf = (lane > c) ? t * fmaf(scal, totk, rowk) : 0.0f;
+                    coef_row[lane] = cf;
+                    coefs_sm[lane] = cf * scal;
+                    if (lane == 0) {
+                        skip_sm = 0;
+                        scal_sm = scal;
+                        beta_sm = beta;
+                        if (blockIdx.x == 0) tau[jc] = t;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (!ok_sm) return;
+        if (skip_sm) continue;
+        // ---- update the rows in registers ----
+        {
+            const float scal_t = scal_sm, beta_t = beta_sm;
+            int kind[RPT];  // 1: below the diagonal, 2: the diagonal row, 0: untouched
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const int64_t lr = threadIdx.x + (int64_t)i * RP_THREADS;
+                const int64_t gr = r0 + lr;
+                kind[i] = (lr < nloc && gr > jc) ? 1 : ((lr < nloc && gr == jc) ? 2 : 0);
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const float cs = coefs_sm[k], cr = coef_row[k];
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) {
+                    if (kind[i] == 1) a[i][k] = (k == c) ? xc[i] * scal_t : a[i][k] - cs * xc[i];
+                    else if (kind[i] == 2) a[i][k] = (k == c) ? beta_t : a[i][k] - cr;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int64_t lr = threadIdx.x + (int64_t)i * RP_THREADS;
+        if (lr < nloc) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) A[(r0 + lr) + (j0 + k) * lda] = a[i][k];
+        }
+    }
+}
+
+template <int RPT>
+ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, Scratch &ws,
+                            int G, int64_t rows_per, cudaStream_t s) {
+    const int64_t rows = M - j0;
+    auto fn = panel_qr_regs_kernel<RPT>;
+    int per_sm = 0;
+    CT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RP_THREADS, 0));
+    if (per_sm * num_sms() < G) {
+        set_error("panel: cooperative grid %d does not fit (%d per SM)", G, per_sm);
+        return CT_ERR_CUDA;
+    }
+    // workspace: totals [2][RP_TOT] words | counters [2] | records [2][G][RP_REC] floats
+    const size_t tot_bytes = sizeof(uint64_t) * 2 * RP_TOT;
+    const size_t cnt_bytes = 256;
+    const size_t need = tot_bytes + cnt_bytes + sizeof(float) * 2 * (size_t)G * RP_REC;
+    CT_TRY(ws.ensure(need));
+    uint64_t *tot = (uint64_t *)ws.ptr;
+    unsigned *counter = (unsigned *)((char *)ws.ptr + tot_bytes);
+    float *rec = (float *)((char *)ws.ptr + tot_bytes + cnt_bytes);
+    CT_CUDA(cudaMemsetAsync(ws.ptr, 0, tot_bytes + cnt_bytes, s));
+    DevStatus *st = device_status();
+    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &counter, &st, &rows_per};
+    ProfScope prof(PROF_PANEL, s, 2.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32, G,
+                   2 + RPT);
+    CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(RP_THREADS), args, 0, s));
+    count_launch();
+    return CT_OK;
+}
+
 template <typename T>
 __global__ void extract_vtop_kernel(const T *A, int64_t lda, int64_t j0, int nb, T *Vt, int64_t ldv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;  // row
@@ -366,6 +635,20 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
         return panel_launch<double, 32>((double *)A, lda, M, j0, nb, (double *)tau, ws, s);
     }
     if (nb <= 16) return panel_launch<float, 16>((float *)A, lda, M, j0, nb, (float *)tau, ws, s);
+    if (nb == 32) {
+        // register-resident slabs when each CTA's share fits 4 rows per thread
+        const int64_t rows = M - j0;
+        int G = (int)std::min<int64_t>(num_sms(), std::max<int64_t>(1, ceil_div(rows, 256)));
+        int64_t rows_per = ceil_div(rows, G);
+        G = (int)ceil_div(rows, rows_per);
+        const int64_t rpt = ceil_div(rows_per, RP_THREADS);
+        if (rows >= 32 && rpt <= 4) {
+            if (rpt <= 1) return panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
+            if (rpt <= 2) return panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
+            if (rpt <= 3) return panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
+            return panel_regs_launch<4>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
+        }
+    }
     return panel_launch<float, 32>((float *)A, lda, M, j0, nb, (float *)tau, ws, s);
 }
 
