@@ -297,6 +297,7 @@ constexpr int RP_THREADS = 256;
 constexpr int RP_WARPS = RP_THREADS / 32;
 constexpr int RP_REC = 72;   // partial record: dots[32] | row[32] | ss  (floats, padded)
 constexpr int RP_TOT = 72;   // total record (64-bit words): dots[32] | row[32] | ss
+constexpr int RP_MAX_PER_WARP = 19;  // records per warp of the reducing CTA: G <= 152
 
 __device__ __forceinline__ void st_word(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -405,11 +406,20 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
         __syncthreads();
         if (last_sm) {
             // ---- the last CTA sums the G records in a fixed order ----
-            float v = 0.0f, sv = 0.0f;
-            for (unsigned b = warp; b < G; b += RP_WARPS) {
+            // all loads of a warp's records are issued before the first add
+            float dv[RP_MAX_PER_WARP], sv2[RP_MAX_PER_WARP];
+#pragma unroll
+            for (int q = 0; q < RP_MAX_PER_WARP; ++q) {
+                const unsigned b = warp + q * RP_WARPS;
                 const float *r = rec_par + (size_t)b * RP_REC;
-                v += __ldcg(r + lane);
-                if (lane == 0) sv += __ldcg(r + 64);
+                dv[q] = (b < G) ? __ldcg(r + lane) : 0.0f;
+                sv2[q] = (b < G && lane == 0) ? __ldcg(r + 64) : 0.0f;
+            }
+            float v = 0.0f, sv = 0.0f;
+#pragma unroll
+            for (int q = 0; q < RP_MAX_PER_WARP; ++q) {
+                v += dv[q];
+                sv += sv2[q];
             }
             red[warp][lane] = v;
             if (lane == 0) red_ss[warp] = sv;
@@ -490,21 +500,26 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
         // ---- update the rows in registers ----
         {
             const float scal_t = scal_sm, beta_t = beta_sm;
-            int kind[RPT];  // 1: below the diagonal, 2: the diagonal row, 0: untouched
+            // rows below the diagonal: a_k -= coefs_k x, column c <- scal x;
+            // the diagonal row: a_k -= coef_k, column c <- beta; others as they are.
+            // Branch-free: m1 = x below the diagonal (else 0), m2 = 1 on the
+            // diagonal row (else 0); cs and cr are 0 for k <= c.
+            float m1[RPT], m2[RPT], newc[RPT];
 #pragma unroll
             for (int i = 0; i < RPT; ++i) {
                 const int64_t lr = threadIdx.x + (int64_t)i * RP_THREADS;
                 const int64_t gr = r0 + lr;
-                kind[i] = (lr < nloc && gr > jc) ? 1 : ((lr < nloc && gr == jc) ? 2 : 0);
+                const bool below = lr < nloc && gr > jc, diag = lr < nloc && gr == jc;
+                m1[i] = below ? xc[i] : 0.0f;
+                m2[i] = diag ? 1.0f : 0.0f;
+                newc[i] = below ? xc[i] * scal_t : (diag ? beta_t : xc[i]);
             }
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
                 const float cs = coefs_sm[k], cr = coef_row[k];
 #pragma unroll
-                for (int i = 0; i < RPT; ++i) {
-                    if (kind[i] == 1) a[i][k] = (k == c) ? xc[i] * scal_t : a[i][k] - cs * xc[i];
-                    else if (kind[i] == 2) a[i][k] = (k == c) ? beta_t : a[i][k] - cr;
-                }
+                for (int i = 0; i < RPT; ++i)
+                    a[i][k] = (k == c) ? newc[i] : fmaf(-cr, m2[i], fmaf(-cs, m1[i], a[i][k]));
             }
         }
     }
@@ -642,7 +657,7 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
         int64_t rows_per = ceil_div(rows, G);
         G = (int)ceil_div(rows, rows_per);
         const int64_t rpt = ceil_div(rows_per, RP_THREADS);
-        if (rows >= 32 && rpt <= 4) {
+        if (rows >= 32 && rpt <= 4 && G <= RP_WARPS * RP_MAX_PER_WARP) {
             if (rpt <= 1) return panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
             if (rpt <= 2) return panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
             if (rpt <= 3) return panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
