@@ -188,7 +188,12 @@ static ct_status gemm_bf16(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
     const int64_t tiles = ceil_div(g.M, 128) * ceil_div(nslab, 256);
     int64_t splits, kchunk;
     plan_splits(tiles, g.K, 2048, 64, &splits, &kchunk);
-    const size_t pbytes = splits > 1 ? 4 * (size_t)(g.M * nslab * splits) : 0;
+    // the last, narrower slab may split K further: size the partials for both
+    const int64_t nlast = g.N - (g.N - 1) / nslab * nslab;
+    int64_t sp_last, kc_last;
+    plan_splits(ceil_div(g.M, 128) * ceil_div(nlast, 256), g.K, 2048, 64, &sp_last, &kc_last);
+    const size_t pbytes = std::max(splits > 1 ? 4 * (size_t)(g.M * nslab * splits) : (size_t)0,
+                                   sp_last > 1 ? 4 * (size_t)(g.M * nlast * sp_last) : (size_t)0);
     CT_TRY(ws.ensure(abytes + bbytes + pbytes));
     void *Ab = ws.ptr, *Bb = (char *)ws.ptr + abytes, *part = (char *)ws.ptr + abytes + bbytes;
     if (g.ta) CT_TRY(copy_convert_2d(0, g.A, g.lda, 2, Ab, ldt, g.K, g.M, s));
@@ -208,7 +213,10 @@ static ct_status gemm_bf16(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
         b.N = nn;
         b.C = (char *)g.C + es * (size_t)(n0 * g.ldc);
         int64_t sp = splits, kc = kchunk;
-        if (nn != nslab) plan_splits(ceil_div(g.M, 128) * ceil_div(nn, 256), g.K, 2048, 64, &sp, &kc);
+        if (nn != nslab) {
+            sp = sp_last;
+            kc = kc_last;
+        }
         if (sp <= 1) {
             CT_TRY(gemm_tc_launch(b, 1, g.K, 0, s));
             continue;
