@@ -75,6 +75,10 @@ ct_status extract_vtop(bool fp64, const void *A, int64_t lda, int64_t j0, int nb
                        int64_t ldv, cudaStream_t s);
 // T (nb x nb, upper triangular, leading dimension ldt) of the block reflector
 // H = I - V T V^T from the Gram matrix G = V^T V (leading dimension ldg) and tau.
+// T[0:o, o:o+wp] of an outer block reflector from its panel T_p and Gram
+// matrix (FP32, o * 33 floats of shared memory; CT_ERR_UNSUPPORTED if larger).
+ct_status t_assemble(int64_t o, int wp, const float *G, int64_t ldg, float *Tm, int64_t ldt,
+                     cudaStream_t s);
 ct_status larft_from_gram(bool fp64, int nb, const void *G, int64_t ldg, const void *tau, void *T,
                           int64_t ldt, cudaStream_t s);
 

@@ -682,8 +682,109 @@ ct_status extract_vtop(bool fp64, const void *A, int64_t lda, int64_t j0, int nb
     return CT_OK;
 }
 
+// One warp, nb <= 32: lane i owns row i of T in registers; column j is
+//   T[i, j] = -tau_j * sum_{i <= l < j} T[i, l] G[l, j]   (i < j),
+// with G's column read from shared memory.  Fully unrolled (register indices
+// are compile-time), in the factor's precision.
+template <typename T>
+__global__ void __launch_bounds__(32) larft_warp_kernel(int nb, const T *G, int64_t ldg, const T *tau,
+                                                        T *Tm, int64_t ldt) {
+    __shared__ T gs[32][33];
+    __shared__ T ts[32];
+    const int lane = threadIdx.x;
+    for (int j = 0; j < 32; ++j) gs[lane][j] = (lane < nb && j < nb) ? G[lane + (int64_t)j * ldg] : T(0);
+    ts[lane] = lane < nb ? tau[lane] : T(0);
+    __syncwarp();
+    T row[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        T y = T(0);
+#pragma unroll
+        for (int l = 0; l < j; ++l) y += (l >= lane) ? row[l] * gs[l][j] : T(0);
+        row[j] = (lane < j) ? -ts[j] * y : (lane == j ? ts[j] : T(0));
+    }
+    if (lane < nb) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < nb) Tm[lane + (int64_t)j * ldt] = row[j];
+    }
+}
+
+// One column block of the outer T (FP32):  for the panel at offset o (width
+// wp <= 32) of a block reflector with Gram matrix G = V^T V,
+//     T[0:o, o:o+wp] = -T[0:o, 0:o] * (G[0:o, o:o+wp] * T_p),  T_p = T[o:o+wp, o:o+wp],
+// the off-diagonal block of the product of the block reflectors (I - V1 T1 V1^T)
+// (I - Vp T_p Vp^T).  CTA b computes rows [32b, 32b+32): first
+// Y[l, :] = G[l, o:o+wp] T_p for l in [32b, o) into shared memory, then
+// out[r, :] = -sum_{l >= r} T[r, l] Y[l, :]  (T upper triangular).
+__global__ void __launch_bounds__(256) tassemble_kernel(int64_t o, int wp, const float *G, int64_t ldg,
+                                                        float *Tm, int64_t ldt) {
+    extern __shared__ float ys[];  // [(o - rb)][33]
+    __shared__ float tp[32][33];
+    const int64_t rb = (int64_t)blockIdx.x * 32;
+    const int t = threadIdx.x;
+    for (int e = t; e < 32 * 32; e += 256) {
+        const int q = e % 32, j = e / 32;
+        tp[q][j] = (q < wp && j < wp) ? Tm[(o + q) + (o + j) * ldt] : 0.0f;
+    }
+    __syncthreads();
+    for (int64_t l = rb + t; l < o; l += 256) {
+        float g[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) g[q] = (q < wp) ? G[l + (o + q) * ldg] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            float y = 0.0f;
+#pragma unroll
+            for (int q = 0; q <= j; ++q) y += g[q] * tp[q][j];
+            ys[(l - rb) * 33 + j] = y;
+        }
+    }
+    __syncthreads();
+    const int64_t r = rb + (t % 32);
+    const int j0 = 4 * (t / 32);
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (r < o) {
+        for (int64_t l = r; l < o; ++l) {
+            const float tv = Tm[r + l * ldt];
+            const float *yr = ys + (l - rb) * 33 + j0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += tv * yr[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j0 + u < wp) Tm[r + (o + j0 + u) * ldt] = -acc[u];
+    }
+}
+
+ct_status t_assemble(int64_t o, int wp, const float *G, int64_t ldg, float *Tm, int64_t ldt,
+                     cudaStream_t s) {
+    if (o <= 0 || wp <= 0) return CT_OK;
+    if (wp > 32) return CT_ERR_ARG;
+    const size_t smem = sizeof(float) * (size_t)o * 33;
+    if (smem > 200 * 1024) return CT_ERR_UNSUPPORTED;
+    static bool attr = false;
+    if (!attr) {
+        CT_CUDA(cudaFuncSetAttribute(tassemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    tassemble_kernel<<<(unsigned)ceil_div(o, 32), 256, smem, s>>>(o, wp, G, ldg, Tm, ldt);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
 ct_status larft_from_gram(bool fp64, int nb, const void *G, int64_t ldg, const void *tau, void *T,
                           int64_t ldt, cudaStream_t s) {
+    if (nb <= 32) {
+        if (fp64) larft_warp_kernel<double><<<1, 32, 0, s>>>(nb, (const double *)G, ldg, (const double *)tau,
+                                                             (double *)T, ldt);
+        else larft_warp_kernel<float><<<1, 32, 0, s>>>(nb, (const float *)G, ldg, (const float *)tau,
+                                                       (float *)T, ldt);
+        count_launch();
+        CT_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
     const int threads = std::min(1024, std::max(32, nb));
     const size_t smem = sizeof(double) * nb;
     if (fp64) {

@@ -133,6 +133,10 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
             CT_TRY(gram(f, j, w, VtJ, f->G.ptr, s));
             for (int64_t o = nb; o < w; o += nb) {
                 const int64_t wp = std::min<int64_t>(nb, w - o);
+                if (!f->fp64 && (size_t)o * 33 * sizeof(float) <= 200 * 1024) {
+                    CT_TRY(t_assemble(o, (int)wp, (const float *)f->G.ptr, NB, (float *)TJ, NB, s));
+                    continue;
+                }
                 const void *Tp = at(TJ, o, o, NB, es);
                 GemmArgs g1{small_kind, false, false, o, wp, wp, 1.0, at(f->G.ptr, 0, o, NB, es), NB,
                             Tp, NB, 0.0, Y, NB};
