@@ -217,6 +217,36 @@ CT_API ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t 
 CT_API ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
                            int64_t ldgb, const ct_opts *opts, void *stream, ct_solve_info *info);
 
+/* ---- Out-of-core factorisation (Sec. 2.2: the matrix does not fit the GPU) --
+ *
+ * As ct_build_system, but the dense A~ is assembled on the device a column
+ * slab at a time (at most device_budget bytes) and kept in library-owned
+ * pinned host memory; the sparse rows stay on the device.  Such a system is
+ * factored with ct_qr_factor_ooc (ct_qr_factor refuses it).  The dense
+ * values equal the in-core build's bit for bit.  Errors: as ct_build_system;
+ * CT_ERR_ARG if device_budget is below one column; CT_ERR_HOSTMEM if the host
+ * memory cannot be pinned. */
+CT_API ct_status ct_build_system_host(const ct_geometry *geom, ct_precision storage,
+                                      size_t device_budget, void *stream, ct_system *out);
+
+/* Blocked Householder QR of a host-resident system with a bounded device
+ * working set: left-looking superpanels of W columns (W a multiple of the
+ * outer block, as wide as device_budget allows after two staging buffers of
+ * one outer block of V each); each superpanel is copied in, updated by every
+ * earlier block reflector (V streamed from host memory on a second stream,
+ * overlapping the GEMMs), factored in core and copied back.  V and R end in
+ * the system's host memory (taken over, as ct_qr_factor takes the device
+ * copy); tau, T and the V tops stay on the device, plus a device copy of the
+ * n x n triangle R (n * round_up(n,32) elements, not part of the budget) for
+ * ct_solve, whose Q^T sweep then streams V from host memory.  The factor
+ * works with ct_solve, ct_solve_host, ct_solve_adjoint, ct_factor_export and
+ * ct_factor_save; ct_factor_device_ptrs returns CT_ERR_UNSUPPORTED.
+ * Errors: CT_ERR_ARG (no host matrix, budget below 2 staging buffers plus
+ * one outer block of columns), CT_ERR_OOM, CT_ERR_RANK (factor returned),
+ * CT_ERR_TIMEOUT, CT_ERR_CUDA. */
+CT_API ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t device_budget,
+                                  void *stream, ct_factor *out);
+
 /* Checkpoint of a factorisation: the paper recomputes A = QR only when A
  * changes and reuses it for every sinogram of the same geometry (Sec. 2, text
  * after Eq. 3; Sec. 3.1.2), so a factor can be written to a file and read

@@ -55,7 +55,7 @@ SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info"
            "ct_factor_device_ptrs", "ct_factor_export", "ct_solve", "ct_solve_host",
            "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm", "ct_stats_reset",
            "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc", "ct_factor_save",
-           "ct_factor_load"]
+           "ct_factor_load", "ct_build_system_host", "ct_qr_factor_ooc"]
 
 
 def lib_path() -> str:
@@ -92,6 +92,8 @@ def lib():
                           C.c_double, vp, I64, vp]
     L.ct_gemm_noalloc.argtypes = list(L.ct_gemm.argtypes)
     L.ct_factor_save.argtypes = [vp, C.c_char_p]
+    L.ct_build_system_host.argtypes = [C.POINTER(Geometry), I32, C.c_size_t, vp, C.POINTER(vp)]
+    L.ct_qr_factor_ooc.argtypes = [vp, C.POINTER(Opts), C.c_size_t, vp, C.POINTER(vp)]
     L.ct_factor_load.argtypes = [vp, C.c_char_p, vp, C.POINTER(vp)]
     L.ct_stats_reset.argtypes = [I32]
     L.ct_stats_read.argtypes = [C.POINTER(I64), vp, vp, vp, vp]
@@ -130,11 +132,17 @@ class System:
     """Device-resident system matrix A~ = [A; sqrt(lambda) I] (dense, column
     major) plus the FP64 CSR/CSC of A, built by the Siddon kernels."""
 
-    def __init__(self, geom: Geometry, storage: str = "fp32", stream=None):
+    def __init__(self, geom: Geometry, storage: str = "fp32", stream=None, host_budget: int = 0):
+        """host_budget > 0: keep the dense matrix in pinned host memory (built in
+        column slabs of at most host_budget device bytes) for factor_ooc."""
         self.geom = geom
         self.storage = storage
         h = C.c_void_p()
-        _check(lib().ct_build_system(C.byref(geom), PRECISIONS[storage], _stream(stream), C.byref(h)))
+        if host_budget > 0:
+            _check(lib().ct_build_system_host(C.byref(geom), PRECISIONS[storage], int(host_budget),
+                                              _stream(stream), C.byref(h)))
+        else:
+            _check(lib().ct_build_system(C.byref(geom), PRECISIONS[storage], _stream(stream), C.byref(h)))
         self.h = h
         vals = [C.c_int64() for _ in range(5)]
         _check(lib().ct_system_info(h, *[C.byref(v) for v in vals]))
@@ -171,6 +179,16 @@ class System:
         o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0)
         h = C.c_void_p()
         _check(lib().ct_qr_factor(self.h, C.byref(o), _stream(stream), C.byref(h)))
+        return Factor(h, self, precision)
+
+    def factor_ooc(self, precision: str | None = None, device_budget: int = 16 << 30,
+                   nb_outer: int = 0, nb_inner: int = 0, stream=None) -> "Factor":
+        """Out-of-core QR of a host-resident system (see ct_qr_factor_ooc)."""
+        if precision is None:
+            precision = "fp64" if self.storage == "fp64" else "tf32"
+        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0)
+        h = C.c_void_p()
+        _check(lib().ct_qr_factor_ooc(self.h, C.byref(o), int(device_budget), _stream(stream), C.byref(h)))
         return Factor(h, self, precision)
 
     def free(self):

@@ -174,6 +174,7 @@ namespace {
 
 void free_system_storage(ct_system s) {
     cudaFree(s->dense);
+    if (s->host_dense) cudaFreeHost(s->host_dense);
     cudaFree(s->d_cs);
     cudaFree(s->row_nnz);
     cudaFree(s->row_ptr);
@@ -198,6 +199,13 @@ ct_status dmalloc(T **p, size_t count) {
 bool is_refine(ct_precision p) { return p == CT_TF32_REFINE || p == CT_BF16_REFINE; }
 
 }  // namespace
+
+namespace ctqr {
+ct_status rdiag_check(ct_factor f, cudaStream_t s);
+// The system without (device_dense = false) or with its dense device matrix.
+ct_status build_system_impl(const ct_geometry *geom, ct_precision storage, void *stream,
+                            bool device_dense, ct_system *out);
+}  // namespace ctqr
 
 extern "C" {
 
@@ -271,6 +279,13 @@ ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *by
 
 ct_status ct_build_system(const ct_geometry *geom, ct_precision storage, void *stream,
                           ct_system *out) {
+    return build_system_impl(geom, storage, stream, true, out);
+}
+
+}  // extern "C"
+
+ct_status ctqr::build_system_impl(const ct_geometry *geom, ct_precision storage, void *stream,
+                                  bool device_dense, ct_system *out) {
     if (!geom || !out) return CT_ERR_ARG;
     *out = nullptr;
     const ct_geometry g = *geom;
@@ -332,7 +347,7 @@ ct_status ct_build_system(const ct_geometry *geom, ct_precision storage, void *s
     if ((st = dmalloc(&sys->col, nnz)) != CT_OK) return fail(st);
     if ((st = dmalloc(&sys->val, nnz)) != CT_OK) return fail(st);
     const size_t es = sys->fp64 ? 8 : 4;
-    {
+    if (device_dense) {
         cudaError_t e = cudaMalloc(&sys->dense, es * (size_t)sys->lda * sys->n);
         if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc(dense A)", __FILE__, __LINE__));
         e = cudaMemsetAsync(sys->dense, 0, es * (size_t)sys->lda * sys->n, s);
@@ -351,6 +366,8 @@ ct_status ct_build_system(const ct_geometry *geom, ct_precision storage, void *s
     *out = sys;
     return CT_OK;
 }
+
+extern "C" {
 
 ct_status ct_system_info(ct_system sys, int64_t *m_rays, int64_t *n_pixels, int64_t *rows,
                          int64_t *lda, int64_t *nnz) {
@@ -376,15 +393,16 @@ ct_status ct_system_device_ptrs(ct_system sys, void **dense, const int64_t **row
 ct_status ct_system_export(ct_system sys, int64_t *row_ptr, int32_t *col_idx, double *val,
                            void *dense, int64_t ldd) {
     if (!sys) return CT_ERR_ARG;
-    if (dense && !sys->dense) return CT_ERR_STATE;
+    const void *dsrc = sys->dense ? sys->dense : sys->host_dense;
+    if (dense && !dsrc) return CT_ERR_STATE;
     if (dense && ldd < sys->rows) return CT_ERR_ARG;
     if (row_ptr) CT_CUDA(cudaMemcpy(row_ptr, sys->row_ptr, sizeof(int64_t) * (sys->m + 1), cudaMemcpyDeviceToHost));
     if (col_idx && sys->nnz) CT_CUDA(cudaMemcpy(col_idx, sys->col, sizeof(int32_t) * sys->nnz, cudaMemcpyDeviceToHost));
     if (val && sys->nnz) CT_CUDA(cudaMemcpy(val, sys->val, sizeof(double) * sys->nnz, cudaMemcpyDeviceToHost));
     if (dense) {
         const size_t es = sys->fp64 ? 8 : 4;
-        CT_CUDA(cudaMemcpy2D(dense, es * ldd, sys->dense, es * sys->lda, es * sys->rows, sys->n,
-                             cudaMemcpyDeviceToHost));
+        CT_CUDA(cudaMemcpy2D(dense, es * ldd, dsrc, es * sys->lda, es * sys->rows, sys->n,
+                             cudaMemcpyDefault));
     }
     return CT_OK;
 }
@@ -394,7 +412,8 @@ ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau) {
     const size_t es = f->es();
     if (VR) {
         if (ldv < f->M) return CT_ERR_ARG;
-        CT_CUDA(cudaMemcpy2D(VR, es * ldv, f->VR, es * f->lda, es * f->M, f->n, cudaMemcpyDeviceToHost));
+        CT_CUDA(cudaMemcpy2D(VR, es * ldv, f->ooc ? f->VR_host : f->VR, es * f->lda, es * f->M, f->n,
+                             cudaMemcpyDefault));
     }
     if (tau) CT_CUDA(cudaMemcpy(tau, f->tau, es * f->n, cudaMemcpyDeviceToHost));
     return CT_OK;
@@ -435,6 +454,11 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
         set_error("precision does not match the system's storage");
         return CT_ERR_ARG;
     }
+    if (!sys->dense) {
+        set_error(sys->host_dense ? "the dense matrix is in host memory: use ct_qr_factor_ooc"
+                                  : "the system's dense storage was already consumed by a factor");
+        return CT_ERR_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     ct_factor f = new (std::nothrow) ct_factor_s;
     if (!f) return CT_ERR_HOSTMEM;
@@ -470,32 +494,51 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     if (cudaMalloc(&f->Vtop, es * (size_t)f->nblocks * NB * NB) != cudaSuccess) return fail(CT_ERR_OOM);
     f->VR = sys->dense;
     sys->dense = nullptr;
+    f->Rm = f->VR;
+    f->ldr = f->lda;
     ct_status st = qr_factor_run(f, s);
     if (st != CT_OK) return fail(st);
+    st = rdiag_check(f, s);
+    if (st == CT_ERR_RANK) {  // keep the factor: the caller may still inspect it
+        *out = f;
+        return CT_ERR_RANK;
+    }
+    if (st != CT_OK) return fail(st);
+    *out = f;
+    return CT_OK;
+}
+
+}  // extern "C"
+
+// min/max |R_jj| into the factor, and the rank test |R_jj| >= n u max|R_jj|.
+ct_status ctqr::rdiag_check(ct_factor f, cudaStream_t s) {
     double *dmm = nullptr;
-    if (cudaMallocAsync((void **)&dmm, 2 * sizeof(double), s) != cudaSuccess) return fail(CT_ERR_OOM);
-    st = rdiag_minmax(f->fp64, f->VR, f->lda, f->n, dmm, s);
+    if (cudaMallocAsync((void **)&dmm, 2 * sizeof(double), s) != cudaSuccess) return CT_ERR_OOM;
+    ct_status st = rdiag_minmax(f->fp64, f->Rm, f->ldr, f->n, dmm, s);
     double hmm[2] = {0, 0};
     if (st == CT_OK && cudaMemcpyAsync(hmm, dmm, sizeof(hmm), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         st = CT_ERR_CUDA;
     cudaFreeAsync(dmm, s);
     if (st == CT_OK) st = check_device_status(s);
-    if (st != CT_OK) return fail(st);
+    if (st != CT_OK) return st;
     f->rjj_min = hmm[0];
     f->rjj_max = hmm[1];
     const double u = f->fp64 ? 1.1102230246251565e-16 : 5.960464477539063e-08;
     if (!(f->rjj_min >= (double)f->n * u * f->rjj_max)) {
         set_error("rank deficient: min|R_jj| = %g, max|R_jj| = %g", f->rjj_min, f->rjj_max);
-        // keep the factor: the caller may still inspect it
-        *out = f;
         return CT_ERR_RANK;
     }
-    *out = f;
     return CT_OK;
 }
 
+extern "C" {
+
 ct_status ct_factor_device_ptrs(ct_factor f, void **VR, int64_t *lda, void **tau) {
     if (!f) return CT_ERR_ARG;
+    if (f->ooc) {
+        set_error("out-of-core factor: V and R are in host memory");
+        return CT_ERR_UNSUPPORTED;
+    }
     if (VR) *VR = f->VR;
     if (lda) *lda = f->lda;
     if (tau) *tau = f->tau;
@@ -558,6 +601,11 @@ void ct_factor_free(ct_factor f) {
     cudaFree(f->Rinv);
     cudaFree(f->RinvT);
     cudaFree(f->Rt);
+    if (f->ooc) {
+        cudaFree(f->Rm);
+        cudaFree(f->stage);
+        if (f->VR_host) cudaFreeHost(f->VR_host);
+    }
     cudaFree(f->RinvB);
     cudaFree(f->RinvTB);
     cudaFree(f->VR);

@@ -177,6 +177,8 @@ extern "C" ct_status ct_factor_load(ct_system sys, const char *path, void *strea
     } else if (cudaMalloc(&f->VR, es * (size_t)f->lda * f->n) != cudaSuccess) {
         st = CT_ERR_OOM;
     }
+    f->Rm = f->VR;
+    f->ldr = f->lda;
     if (st == CT_OK && !took_dense && f->lda > f->M &&
         cudaMemsetAsync(f->VR, 0, es * (size_t)f->lda * f->n, (cudaStream_t)stream) != cudaSuccess)
         st = CT_ERR_CUDA;

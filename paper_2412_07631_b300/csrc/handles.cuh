@@ -10,6 +10,7 @@ struct ct_system_s {
     bool fp64 = false;  // dense storage element type
     int64_t m = 0, n = 0, rows = 0, lda = 0, nnz = 0;
     void *dense = nullptr;  // column-major rows x n (NULL once consumed by a factor)
+    void *host_dense = nullptr;  // out-of-core systems: the same matrix in pinned host memory
     double *d_cs = nullptr;
     int32_t *row_nnz = nullptr;
     int64_t *row_ptr = nullptr;
@@ -50,6 +51,16 @@ struct ct_factor_s {
     void *Tall = nullptr;  // nblocks x (NB x NB), T_J of block J
     void *Vtop = nullptr;  // nblocks x (NB x NB), unit-lower top of V_J
     double rjj_min = 0, rjj_max = 0;
+    // R for the triangular solves: VR itself (ld lda) for in-core factors, a
+    // device copy of the top n rows (ld ldr) for out-of-core factors
+    void *Rm = nullptr;
+    int64_t ldr = 0;
+    // out-of-core factors: V and R in pinned host memory (VR_host, ld lda,
+    // owned); V blocks are streamed through `stage` for the Q^T sweep
+    bool ooc = false;
+    void *VR_host = nullptr;
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
     // triangular-solve aids (built on first solve): inverse diagonal blocks of R
     // and their transposes (trsm_tb x trsm_tb each), R^T for the tensor-core path
     void *Rinv = nullptr, *RinvT = nullptr, *Rt = nullptr;
@@ -84,6 +95,13 @@ ct_status run_graphed(ct_factor f, GraphSlot &g, uint64_t key, cudaStream_t call
 uint64_t graph_key(ct_factor f, int64_t k, const void *extra);
 bool graphs_allowed(ct_factor f);
 ct_status qr_factor_run(ct_factor f, cudaStream_t s);
+ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, cudaStream_t s);
+// C <- (I - V op(T) V^T) C for the block at column j (see qr.cu); vb/ldvb:
+// V below the top block from a staging buffer instead of VR (nullptr: VR).
+ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void *T, bool qt, void *C,
+                      int64_t ldc, int64_t ncols, cudaStream_t s, ctqr::GemmKind big, const void *vb,
+                      int64_t ldvb);
+ct_status stage_v_block(ct_factor f, int64_t J, void *dst, int64_t *ldd, cudaStream_t s);
 // R X = C or R^T X = C in place for the factor's R (blocked, inverse diagonal blocks).
 ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, cudaStream_t s);
 // Apply Q^T (forward block order) or Q (reverse order) to the M x k matrix C.

@@ -61,12 +61,17 @@ ct_status gram(ct_factor f, int64_t j, int w, const void *Vt, void *G, cudaStrea
     return CT_OK;
 }
 
+}  // namespace
+
 // C[j:M, 0:ncols] <- (I - V op(T) V^T) C, op(T) = T^T for Q^T, T for Q.
 // C points at row j of the target; V is the block at column j of width w.
 // `big` is the engine of the two products over the rows below the top block
-// (V_b^T C_b and C_b -= V_b W2), the bulk of the flops.
+// (V_b^T C_b and C_b -= V_b W2), the bulk of the flops.  V_b (rows j+w ..
+// row_end(j+w) of the block) is read in place in VR, or from `vb` (ld ldvb)
+// when given (a block streamed from host memory).
 ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void *T, bool qt,
-                      void *C, int64_t ldc, int64_t ncols, cudaStream_t s, GemmKind big) {
+                      void *C, int64_t ldc, int64_t ncols, cudaStream_t s, GemmKind big,
+                      const void *vb, int64_t ldvb) {
     if (ncols <= 0) return CT_OK;
     const int64_t NB = f->NB;
     const size_t es = f->es();
@@ -74,12 +79,13 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     CT_TRY(f->W2.ensure(es * (size_t)NB * ncols));
     void *W = f->W.ptr, *W2 = f->W2.ptr;
     const int64_t kb = f->row_end(j + w) - j - w;  // rows beyond: V is zero there
-    const void *Vb = at(f->VR, j + w, j, f->lda, es);
+    const void *Vb = vb ? vb : at(f->VR, j + w, j, f->lda, es);
+    const int64_t ldV = vb ? ldvb : f->lda;
     void *Cb = (char *)C + es * (size_t)w;
     // W = V^T C
     CT_TRY(gemm(mk(f, true, false, w, ncols, w, 1.0, Vt, NB, C, ldc, 0.0, W, NB), f->gemm_ws, s));
     if (kb > 0) {
-        GemmArgs g = mk(f, true, false, w, ncols, kb, 1.0, Vb, f->lda, Cb, ldc, 1.0, W, NB);
+        GemmArgs g = mk(f, true, false, w, ncols, kb, 1.0, Vb, ldV, Cb, ldc, 1.0, W, NB);
         g.kind = big;
         CT_TRY(gemm(g, f->gemm_ws, s));
     }
@@ -88,27 +94,29 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     // C -= V W2
     CT_TRY(gemm(mk(f, false, false, w, ncols, w, -1.0, Vt, NB, W2, NB, 1.0, C, ldc), f->gemm_ws, s));
     if (kb > 0) {
-        GemmArgs g = mk(f, false, false, kb, ncols, w, -1.0, Vb, f->lda, W2, NB, 1.0, Cb, ldc);
+        GemmArgs g = mk(f, false, false, kb, ncols, w, -1.0, Vb, ldV, W2, NB, 1.0, Cb, ldc);
         g.kind = big;
         CT_TRY(gemm(g, f->gemm_ws, s));
     }
     return CT_OK;
 }
 
-}  // namespace
-
-ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
+// Factor outer blocks [J0, J1) of VR; trailing updates reach column col_end.
+// (In core: all blocks, col_end = n.  Out of core: the blocks of one
+// superpanel, whose columns [c0, col_end) are resident; VR is then offset so
+// that global column indices address the superpanel buffer.)
+ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, cudaStream_t s) {
     const size_t es = f->es();
-    const int64_t NB = f->NB, nb = f->nb, n = f->n, lda = f->lda;
+    const int64_t NB = f->NB, nb = f->nb, n = col_end, lda = f->lda;
     CT_TRY(f->G.ensure(es * (size_t)NB * NB));
     // misc: Vt_p (ld NB) for inner panels | Y (ld NB) for the T assembly
     CT_TRY(f->misc.ensure(2 * es * (size_t)NB * NB));
     void *Vtp = f->misc.ptr;
     void *Y = (char *)f->misc.ptr + es * (size_t)NB * NB;
     const GemmKind small_kind = f->fp64 ? GEMM_F64 : GEMM_F32;
-    for (int64_t J = 0; J < f->nblocks; ++J) {
+    for (int64_t J = J0; J < J1; ++J) {
         const int64_t j = J * NB;
-        const int w = (int)std::min<int64_t>(NB, n - j);
+        const int w = (int)std::min<int64_t>(NB, f->n - j);
         void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
         void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
         CT_CUDA(cudaMemsetAsync(TJ, 0, es * (size_t)NB * NB, s));
@@ -123,7 +131,7 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
             const int64_t ncols_in = j + w - (p + wp);
             if (ncols_in > 0)
                 CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,
-                                   ncols_in, s, f->upd_kind));
+                                   ncols_in, s, f->upd_kind, nullptr, 0));
         }
         CT_TRY(extract_vtop(f->fp64, f->VR, lda, j, w, VtJ, NB, s));
         if (w > nb) {
@@ -148,8 +156,24 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s) {
         }
         if (j + w < n)
             CT_TRY(apply_block(f, j, w, VtJ, TJ, true, at(f->VR, j, j + w, lda, es), lda, n - j - w, s,
-                               f->upd_kind));
+                               f->upd_kind, nullptr, 0));
     }
+    return CT_OK;
+}
+
+ct_status qr_factor_run(ct_factor f, cudaStream_t s) { return qr_factor_range(f, 0, f->nblocks, f->n, s); }
+
+// Rows j+w .. row_end(j+w) of V_J (the part below its top block) from the
+// host copy into the staging buffer (ld = rows rounded up to 32).
+ct_status stage_v_block(ct_factor f, int64_t J, void *dst, int64_t *ldd, cudaStream_t s) {
+    const size_t es = f->es();
+    const int64_t j = J * f->NB;
+    const int w = (int)std::min<int64_t>(f->NB, f->n - j);
+    const int64_t kb = f->row_end(j + w) - j - w;
+    *ldd = round_up(std::max<int64_t>(kb, 1), 32);
+    if (kb <= 0) return CT_OK;
+    CT_CUDA(cudaMemcpy2DAsync(dst, es * (size_t)*ldd, (const char *)f->VR_host + es * (size_t)(j + w + j * f->lda),
+                              es * (size_t)f->lda, es * (size_t)kb, w, cudaMemcpyHostToDevice, s));
     return CT_OK;
 }
 
@@ -163,7 +187,15 @@ ct_status apply_q_blocks(ct_factor f, bool transpose, void *C, int64_t ldc, int6
         const int w = (int)std::min<int64_t>(NB, f->n - j);
         const void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
         const void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
-        CT_TRY(apply_block(f, j, w, VtJ, TJ, transpose, (char *)C + es * (size_t)j, ldc, k, s, f->kind));
+        if (f->ooc) {  // stream the block's V from host memory
+            int64_t ldv = 0;
+            CT_TRY(stage_v_block(f, J, f->stage, &ldv, s));
+            CT_TRY(apply_block(f, j, w, VtJ, TJ, transpose, (char *)C + es * (size_t)j, ldc, k, s, f->kind,
+                               f->stage, ldv));
+            continue;
+        }
+        CT_TRY(apply_block(f, j, w, VtJ, TJ, transpose, (char *)C + es * (size_t)j, ldc, k, s, f->kind,
+                           nullptr, 0));
     }
     return CT_OK;
 }

@@ -174,7 +174,7 @@ static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
                 const int64_t bb = std::min<int64_t>(b, s1 - p - b);
                 // Y = R[p:p+b, p+b:p+b+bb] inv(C)
                 GemmArgs g1{GEMM_F32, false, false, b, bb, bb, 1.0,
-                            (char *)f->VR + es * (size_t)(p + (p + b) * f->lda), f->lda,
+                            (char *)f->Rm + es * (size_t)(p + (p + b) * f->ldr), f->ldr,
                             inv_at(t, p + b - s0, p + b - s0), SB, 0.0, Y, SB};
                 CT_TRY(gemm(g1, f->trsm_ws, s));
                 // inv block (p, p+b) = -inv(A) Y
@@ -202,15 +202,15 @@ ct_status trsm_prepare(ct_factor f, cudaStream_t s) {
     CT_CUDA(cudaMalloc(&f->RinvT, es * (size_t)nbt * TB * TB));
     f->trsm_tb = TB;
     if (f->fp64)
-        CT_TRY((diag_inverse_launch<double, 64>(f->n, (const double *)f->VR, f->lda,
+        CT_TRY((diag_inverse_launch<double, 64>(f->n, (const double *)f->Rm, f->ldr,
                                                 (double *)f->Rinv, (double *)f->RinvT, s)));
     else
-        CT_TRY((diag_inverse_launch<float, 128>(f->n, (const float *)f->VR, f->lda,
+        CT_TRY((diag_inverse_launch<float, 128>(f->n, (const float *)f->Rm, f->ldr,
                                                 (float *)f->Rinv, (float *)f->RinvT, s)));
     if (f->kind == GEMM_TF32 || f->kind == GEMM_BF16) {
         f->ldrt = round_up(f->n, 32);
         CT_CUDA(cudaMalloc(&f->Rt, es * (size_t)f->ldrt * f->n));
-        CT_TRY(transpose_any(0, f->VR, f->lda, 0, f->Rt, f->ldrt, f->n, f->n, s));
+        CT_TRY(transpose_any(0, f->Rm, f->ldr, 0, f->Rt, f->ldrt, f->n, f->n, s));
         CT_TRY(build_superblock_inverses(f, s));
     }
     return CT_OK;
@@ -260,13 +260,13 @@ ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, 
                 g.lda = f->ldrt;
             } else {
                 g.ta = false;
-                g.A = (char *)f->VR + es * (size_t)(r0 + c0 * f->lda);
-                g.lda = f->lda;
+                g.A = (char *)f->Rm + es * (size_t)(r0 + c0 * f->ldr);
+                g.lda = f->ldr;
             }
         } else {
             g.ta = true;
-            g.A = (char *)f->VR + es * (size_t)(c0 + r0 * f->lda);
-            g.lda = f->lda;
+            g.A = (char *)f->Rm + es * (size_t)(c0 + r0 * f->ldr);
+            g.lda = f->ldr;
         }
         return gemm(g, f->trsm_ws, s);
     };
