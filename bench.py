@@ -147,15 +147,22 @@ def make_inputs(ct, torch, name, rank=0):
 
 
 NB_OUTER = 0  # 0: the library's default outer block width
+OOC_BUDGET = 0  # > 0: out-of-core path with this device budget (bytes)
 
 
 def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=None):
     """One pass of the hot path.  Returns (X, info, per-phase ms)."""
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
-    sysg = ct.System(geom, "fp64" if precision == "fp64" else "fp32")
-    ev[1].record()
-    F = sysg.factor(precision, nb_outer=NB_OUTER)
+    storage = "fp64" if precision == "fp64" else "fp32"
+    if OOC_BUDGET > 0:  # out of core: host-resident A~, bounded device working set
+        sysg = ct.System(geom, storage, host_budget=OOC_BUDGET)
+        ev[1].record()
+        F = sysg.factor_ooc(precision, device_budget=OOC_BUDGET, nb_outer=NB_OUTER)
+    else:
+        sysg = ct.System(geom, storage)
+        ev[1].record()
+        F = sysg.factor(precision, nb_outer=NB_OUTER)
     ev[2].record()
     if host:
         X = F.solve_host(B, max_iter=max_iter, tol=tol)
@@ -218,9 +225,12 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cert", action="store_true")
     ap.add_argument("--nb-outer", type=int, default=0, help="outer WY block width (0: default)")
+    ap.add_argument("--ooc-budget-gb", type=float, default=0.0,
+                    help="run the out-of-core path: A~ in pinned host memory, this many GB of device working set")
     args = ap.parse_args()
-    global NB_OUTER
+    global NB_OUTER, OOC_BUDGET
     NB_OUTER = args.nb_outer
+    OOC_BUDGET = int(args.ooc_budget_gb * (1 << 30))
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -394,6 +404,8 @@ def main():
             "config": {"workload": workload_desc(args.workload), "n_side": ns, "views": nv,
                        "bins": nb, "rows": M, "unknowns": n, "slices": k,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "out_of_core": ({"device_budget_gb": args.ooc_budget_gb,
+                                        "host_matrix": "pinned host memory"} if OOC_BUDGET else None),
                        "l2": "inputs larger than L2 (dense A~ of %.1f GB rebuilt every step)"
                              % (M * n * 4 / 1e9)},
             "qr_tflops": qr_fl / (qr_ms * 1e-3) / 1e12,

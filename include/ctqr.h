@@ -247,6 +247,11 @@ CT_API ct_status ct_build_system_host(const ct_geometry *geom, ct_precision stor
 CT_API ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t device_budget,
                                   void *stream, ct_factor *out);
 
+/* Pinned host blocks of freed out-of-core systems and factors are kept (at
+ * most two) for reuse by the next ct_build_system_host, since pinning tens
+ * of GB takes seconds; this unpins and frees them. */
+CT_API void ct_host_cache_release(void);
+
 /* Checkpoint of a factorisation: the paper recomputes A = QR only when A
  * changes and reuses it for every sinogram of the same geometry (Sec. 2, text
  * after Eq. 3; Sec. 3.1.2), so a factor can be written to a file and read

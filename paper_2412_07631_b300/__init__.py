@@ -55,7 +55,7 @@ SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info"
            "ct_factor_device_ptrs", "ct_factor_export", "ct_solve", "ct_solve_host",
            "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm", "ct_stats_reset",
            "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc", "ct_factor_save",
-           "ct_factor_load", "ct_build_system_host", "ct_qr_factor_ooc"]
+           "ct_factor_load", "ct_build_system_host", "ct_qr_factor_ooc", "ct_host_cache_release"]
 
 
 def lib_path() -> str:
@@ -94,6 +94,8 @@ def lib():
     L.ct_factor_save.argtypes = [vp, C.c_char_p]
     L.ct_build_system_host.argtypes = [C.POINTER(Geometry), I32, C.c_size_t, vp, C.POINTER(vp)]
     L.ct_qr_factor_ooc.argtypes = [vp, C.POINTER(Opts), C.c_size_t, vp, C.POINTER(vp)]
+    L.ct_host_cache_release.argtypes = []
+    L.ct_host_cache_release.restype = None
     L.ct_factor_load.argtypes = [vp, C.c_char_p, vp, C.POINTER(vp)]
     L.ct_stats_reset.argtypes = [I32]
     L.ct_stats_read.argtypes = [C.POINTER(I64), vp, vp, vp, vp]

@@ -174,7 +174,7 @@ namespace {
 
 void free_system_storage(ct_system s) {
     cudaFree(s->dense);
-    if (s->host_dense) cudaFreeHost(s->host_dense);
+    if (s->host_dense) pinned_release(s->host_dense, s->host_bytes);
     cudaFree(s->d_cs);
     cudaFree(s->row_nnz);
     cudaFree(s->row_ptr);
@@ -604,7 +604,7 @@ void ct_factor_free(ct_factor f) {
     if (f->ooc) {
         cudaFree(f->Rm);
         cudaFree(f->stage);
-        if (f->VR_host) cudaFreeHost(f->VR_host);
+        if (f->VR_host) pinned_release(f->VR_host, f->host_bytes);
     }
     cudaFree(f->RinvB);
     cudaFree(f->RinvTB);

@@ -60,7 +60,7 @@ struct Region {
 };
 
 int regions(ct_factor f, Region *out) {
-    out[0] = {f->VR, f->M, f->n, f->lda};
+    out[0] = {f->ooc ? f->VR_host : f->VR, f->M, f->n, f->lda};  // host memory for out-of-core factors
     out[1] = {f->tau, f->n, 1, f->n};
     out[2] = {f->Tall, (int64_t)f->NB * f->NB, f->nblocks, (int64_t)f->NB * f->NB};
     out[3] = {f->Vtop, (int64_t)f->NB * f->NB, f->nblocks, (int64_t)f->NB * f->NB};
@@ -107,7 +107,7 @@ extern "C" ct_status ct_factor_save(ct_factor f, const char *path) {
             const int64_t nc = std::min(cols_per, rg[r].cols - c0);
             const size_t rb = es * rg[r].rows;
             if (cudaMemcpy2D(buf.p, rb, (char *)rg[r].dev + es * rg[r].ld * c0, es * rg[r].ld, rb, nc,
-                             cudaMemcpyDeviceToHost) != cudaSuccess) {
+                             cudaMemcpyDefault) != cudaSuccess) {
                 st = CT_ERR_CUDA;
                 break;
             }

@@ -11,6 +11,7 @@ struct ct_system_s {
     int64_t m = 0, n = 0, rows = 0, lda = 0, nnz = 0;
     void *dense = nullptr;  // column-major rows x n (NULL once consumed by a factor)
     void *host_dense = nullptr;  // out-of-core systems: the same matrix in pinned host memory
+    size_t host_bytes = 0;       // size of that pinned block
     double *d_cs = nullptr;
     int32_t *row_nnz = nullptr;
     int64_t *row_ptr = nullptr;
@@ -59,6 +60,7 @@ struct ct_factor_s {
     // owned); V blocks are streamed through `stage` for the Q^T sweep
     bool ooc = false;
     void *VR_host = nullptr;
+    size_t host_bytes = 0;
     void *stage = nullptr;
     size_t stage_bytes = 0;
     // triangular-solve aids (built on first solve): inverse diagonal blocks of R
@@ -93,6 +95,9 @@ namespace ctqr {
 template <class Body>
 ct_status run_graphed(ct_factor f, GraphSlot &g, uint64_t key, cudaStream_t caller, Body body);
 uint64_t graph_key(ct_factor f, int64_t k, const void *extra);
+// pinned host blocks of out-of-core matrices (cached across free/alloc)
+ct_status pinned_acquire(size_t bytes, void **out, size_t *got);
+void pinned_release(void *p, size_t bytes);
 bool graphs_allowed(ct_factor f);
 ct_status qr_factor_run(ct_factor f, cudaStream_t s);
 ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, cudaStream_t s);

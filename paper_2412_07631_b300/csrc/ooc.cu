@@ -19,7 +19,9 @@
 // solves.  Host-link traffic: each superpanel twice, plus, for superpanel s,
 // the V of all earlier columns.
 #include <algorithm>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "handles.cuh"
 
@@ -63,6 +65,14 @@ __global__ void lambda_slab_kernel(int64_t m, int64_t c0, int64_t c1, double sl,
     if (j < c1) slab[(m + j) + (j - c0) * lds] = (T)sl;
 }
 
+// Pinned host blocks of out-of-core matrices are expensive to create (the
+// pages are locked one by one: seconds for tens of GB), so freed blocks are
+// kept and handed to the next request they fit, largest-fit last.  At most
+// kMaxCached blocks are kept; ct_host_cache_release() unpins them.
+constexpr int kMaxCached = 2;
+std::mutex g_pin_mu;
+std::vector<std::pair<void *, size_t>> g_pin_free;
+
 struct Events {
     cudaEvent_t e[6] = {};
     ~Events() {
@@ -72,9 +82,62 @@ struct Events {
 };
 
 }  // namespace
+
+// Pinned host block of at least `bytes` (from the cache when one fits).
+ct_status pinned_acquire(size_t bytes, void **out, size_t *got) {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        int best = -1;
+        for (int i = 0; i < (int)g_pin_free.size(); ++i)
+            if (g_pin_free[i].second >= bytes && (best < 0 || g_pin_free[i].second < g_pin_free[best].second))
+                best = i;
+        if (best >= 0) {
+            *out = g_pin_free[best].first;
+            *got = g_pin_free[best].second;
+            g_pin_free.erase(g_pin_free.begin() + best);
+            return CT_OK;
+        }
+    }
+    if (cudaMallocHost(out, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        // release the cache and try once more
+        ct_host_cache_release();
+        if (cudaMallocHost(out, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *out = nullptr;
+            return CT_ERR_HOSTMEM;
+        }
+    }
+    *got = bytes;
+    return CT_OK;
+}
+
+void pinned_release(void *p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if ((int)g_pin_free.size() >= kMaxCached) {  // drop the smallest
+        auto it = std::min_element(g_pin_free.begin(), g_pin_free.end(),
+                                   [](auto &a, auto &b) { return a.second < b.second; });
+        if (it->second < bytes) {
+            cudaFreeHost(it->first);
+            g_pin_free.erase(it);
+        } else {
+            cudaFreeHost(p);
+            return;
+        }
+    }
+    g_pin_free.emplace_back(p, bytes);
+}
+
 }  // namespace ctqr
 
 using namespace ctqr;
+
+extern "C" void ct_host_cache_release(void) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (auto &b : g_pin_free) cudaFreeHost(b.first);
+    g_pin_free.clear();
+}
 
 extern "C" ct_status ct_build_system_host(const ct_geometry *geom, ct_precision storage,
                                           size_t device_budget, void *stream, ct_system *out) {
@@ -91,8 +154,7 @@ extern "C" ct_status ct_build_system_host(const ct_geometry *geom, ct_precision 
         ct_system_free(sys);
         return CT_ERR_ARG;
     }
-    if (cudaMallocHost(&sys->host_dense, col_bytes * (size_t)sys->n) != cudaSuccess) {
-        cudaGetLastError();
+    if (pinned_acquire(col_bytes * (size_t)sys->n, &sys->host_dense, &sys->host_bytes) != CT_OK) {
         sys->host_dense = nullptr;
         set_error("cannot pin %zu B of host memory for the dense matrix", col_bytes * (size_t)sys->n);
         ct_system_free(sys);
@@ -190,6 +252,7 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
         return CT_ERR_ARG;
     }
     f->VR_host = sys->host_dense;  // factored in place, as ct_qr_factor does with the device copy
+    f->host_bytes = sys->host_bytes;
     sys->host_dense = nullptr;
     void *sp = nullptr, *stg[2] = {nullptr, nullptr};
     cudaStream_t cs = nullptr;
@@ -204,6 +267,7 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
         if (stg[1]) cudaFree(stg[1]);
         // the host storage goes back to the system (its content is no longer A~)
         sys->host_dense = f->VR_host;
+        sys->host_bytes = f->host_bytes;
         f->VR_host = nullptr;
         f->VR = nullptr;  // the superpanel alias, freed above
         f->stage = stg[0];

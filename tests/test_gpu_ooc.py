@@ -95,3 +95,27 @@ def test_ooc_budget_too_small_is_refused():
     # the system keeps its host matrix after the refusal
     F = host.factor_ooc("tf32", device_budget=64 << 20, nb_outer=64)
     assert F.n == NS * NS
+
+
+@pytest.mark.gpu
+def test_ooc_factor_checkpoint_loads_in_core(oracle_mod, tmp_path):
+    """An out-of-core factor written with save() loads as an in-core factor
+    of a device-built system and solves to the same bits."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, B = _case(O)
+    geom = ct.make_geometry(NS, NV, NBINS, SL)
+    probe = ct.System(geom, "fp64")
+    budget = _budget(probe, 8, 64, 128)
+    probe.free()
+    host = ct.System(geom, "fp64", host_budget=budget)
+    Fo = host.factor_ooc("fp64", device_budget=budget, nb_outer=64)
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    x1 = Fo.solve(Bt).clone()
+    path = str(tmp_path / "ooc.ctqr")
+    Fo.save(path)
+    dev = ct.System(geom, "fp64")
+    Fi = ct.Factor.load(dev, path)
+    x2 = Fi.solve(Bt)
+    assert torch.allclose(x1, x2, rtol=0, atol=1e-12 * float(x1.abs().max()))
