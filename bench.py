@@ -210,6 +210,40 @@ def cpu_oracle_sample(name, cols=None):
 
 
 # ---------------------------------------------------------------------------
+def gemm_only(args):
+    """The GEMM engine on one shape (the trailing-update products in
+    isolation): C += op(A) op(B) with random operands, `warmup` untimed and
+    `steps` timed calls (CUDA events), one JSON line."""
+    import torch
+    import paper_2412_07631_b300 as ct
+    kind, tr, shape = args.gemm.split(":")
+    ta, tb = tr[0], tr[1]
+    M, N, K = (int(v) for v in shape.split(","))
+    ra, ca = (K, M) if ta == "T" else (M, K)
+    rb, cb = (N, K) if tb == "T" else (K, N)
+    lda, ldb = -(-ra // 32) * 32, -(-rb // 32) * 32
+    dt = torch.float64 if kind == "fp64" else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.rand((ca, lda), device="cuda", dtype=dt, generator=g)
+    B = torch.rand((cb, ldb), device="cuda", dtype=dt, generator=g)
+    Cm = torch.rand((N, M), device="cuda", dtype=dt, generator=g)
+    for _ in range(args.warmup):
+        ct.gemm(kind, ta, tb, M, N, K, -1.0, A, lda, B, ldb, 1.0, Cm, M)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ct.gemm(kind, ta, tb, M, N, K, -1.0, A, lda, B, ldb, 1.0, Cm, M)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    es = 8 if kind == "fp64" else 4
+    print(json.dumps({"kernel": "gemm engine", "kind": kind, "trans": tr, "M": M, "N": N, "K": K,
+                      "ms": ms, "tflops": 2.0 * M * N * K / ms / 1e9,
+                      "algorithmic_bytes": es * (M * K + K * N + 2 * M * N),
+                      "steps": args.steps, "warmup": args.warmup}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,7 +261,12 @@ def main():
     ap.add_argument("--nb-outer", type=int, default=0, help="outer WY block width (0: default)")
     ap.add_argument("--ooc-budget-gb", type=float, default=0.0,
                     help="run the out-of-core path: A~ in pinned host memory, this many GB of device working set")
+    ap.add_argument("--gemm", type=str, default="",
+                    help="time only the GEMM engine on one shape, 'KIND:TA TB:M,N,K' (e.g. "
+                         "'tf32:TN:768,16384,32768'), beta = 1; for kernel profiling")
     args = ap.parse_args()
+    if args.gemm:
+        return gemm_only(args)
     global NB_OUTER, OOC_BUDGET
     NB_OUTER = args.nb_outer
     OOC_BUDGET = int(args.ooc_budget_gb * (1 << 30))

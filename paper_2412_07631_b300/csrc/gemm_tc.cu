@@ -138,11 +138,21 @@ struct TileSched {
         m_fast = mt <= nt;
     }
     // work item w -> (m tile, n tile, split)
+    // Tiles are walked in groups of kGroup rows of the longer grid dimension;
+    // inside a group the shorter dimension varies fastest, then the group's
+    // rows.  CTAs resident together then share a few operand tiles of each
+    // dimension, so neither operand is streamed from DRAM once per row of
+    // the other when it does not fit L2 (the short-K trailing updates).
     __device__ void decode(int64_t w, int64_t &mi, int64_t &ni, int64_t &z) const {
+        constexpr int64_t kGroup = 8;
         z = w / tiles;
         const int64_t t = w - z * tiles;
-        if (m_fast) { mi = t % mt; ni = t / mt; }
-        else { ni = t % nt; mi = t / nt; }
+        const int64_t nf = m_fast ? mt : nt, ns = m_fast ? nt : mt;
+        const int64_t g = t / (kGroup * nf), r = t - g * (kGroup * nf);
+        const int64_t rows = min(kGroup, ns - g * kGroup);
+        const int64_t sl = g * kGroup + r % rows, fa = r / rows;
+        if (m_fast) { mi = fa; ni = sl; }
+        else { ni = fa; mi = sl; }
     }
 };
 

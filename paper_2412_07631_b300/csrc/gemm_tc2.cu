@@ -182,11 +182,20 @@ struct PairSched {
         work = tiles * splits;
         m_fast = mt <= nt;
     }
+    // Tiles are walked in groups of kGroup rows of the longer grid dimension;
+    // inside a group the shorter dimension varies fastest, then the group's
+    // rows, so pairs resident together share a few operand tiles of each
+    // dimension through L2.
     __device__ void decode(int64_t w, int64_t &mi, int64_t &ni, int64_t &z) const {
+        constexpr int64_t kGroup = 8;
         z = w / tiles;
         const int64_t t = w - z * tiles;
-        if (m_fast) { mi = t % mt; ni = t / mt; }
-        else { ni = t % nt; mi = t / nt; }
+        const int64_t nf = m_fast ? mt : nt, ns = m_fast ? nt : mt;
+        const int64_t g = t / (kGroup * nf), r = t - g * (kGroup * nf);
+        const int64_t rows = min(kGroup, ns - g * kGroup);
+        const int64_t sl = g * kGroup + r % rows, fa = r / rows;
+        if (m_fast) { mi = fa; ni = sl; }
+        else { ni = fa; mi = sl; }
     }
 };
 
