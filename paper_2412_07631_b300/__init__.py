@@ -174,10 +174,15 @@ class System:
         _check(lib().ct_forward_project(self.h, _ptr(X), self.n, k, _ptr(P), self.m, _stream(stream)))
         return P
 
-    def factor(self, precision: str | None = None, nb_outer: int = 0, nb_inner: int = 0,
+    def factor(self, precision: str | None = None, nb_outer: int | str = 0, nb_inner: int = 0,
                stream=None) -> "Factor":
+        """nb_outer: outer block width (0: library default; "auto": the
+        autotuner's cached choice for this geometry, measured on first use)."""
         if precision is None:
             precision = "fp64" if self.storage == "fp64" else "tf32"
+        if nb_outer == "auto":
+            from . import autotune
+            nb_outer = autotune.outer_block(self.geom, precision)
         o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0)
         h = C.c_void_p()
         _check(lib().ct_qr_factor(self.h, C.byref(o), _stream(stream), C.byref(h)))

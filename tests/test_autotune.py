@@ -1,0 +1,48 @@
+"""Autotuner selection and cache logic (CPU, with a stand-in timer), and one
+real tuning run on the GPU."""
+import json
+
+import pytest
+
+
+def test_autotune_picks_fastest_and_caches(tmp_path):
+    from paper_2412_07631_b300 import autotune, make_geometry
+    g = make_geometry(24, 40, 36, 0.05)
+    calls = []
+
+    def timer(geom, prec, nb):
+        calls.append(nb)
+        return {512: 9.0, 768: 7.5, 1024: 8.0}[nb]
+
+    path = str(tmp_path / "tune.json")
+    assert autotune.outer_block(g, "tf32", path=path, timer=timer) == 768
+    assert sorted(calls) == [512, 768, 1024]
+    d = json.load(open(path))
+    (entry,) = d.values()
+    assert entry["nb_outer"] == 768 and set(entry["ms"]) == {"512", "768", "1024"}
+    # second call: from the cache, no timing
+    calls.clear()
+    assert autotune.outer_block(g, "tf32", path=path, timer=timer) == 768
+    assert calls == []
+    # another precision or geometry is a different key
+    assert autotune.outer_block(g, "bf16", path=path, timer=lambda *a: 1.0) == 512
+    assert len(json.load(open(path))) == 2
+
+
+def test_autotune_tie_goes_to_narrower():
+    from paper_2412_07631_b300 import autotune
+    assert autotune.pick({1024: 5.0, 512: 5.0, 768: 6.0}) == 512
+
+
+@pytest.mark.gpu
+def test_autotune_real_run(tmp_path):
+    from gpu_util import need_cuda
+    need_cuda()
+    import paper_2412_07631_b300 as ct
+    from paper_2412_07631_b300 import autotune
+    g = ct.make_geometry(32, 60, 46, 0.05)
+    path = str(tmp_path / "tune.json")
+    nb = autotune.outer_block(g, "tf32", candidates=(64, 128), path=path)
+    assert nb in (64, 128)
+    F = ct.System(g, "fp32").factor("tf32", nb_outer=nb)
+    assert F.n == 32 * 32
