@@ -263,7 +263,7 @@ ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     const int64_t BN = tc ? 256 : (fp64 ? 64 : 128);
     const int64_t tiles = ceil_div(g.M, BM) * ceil_div(g.N, BN);
     int64_t splits, kchunk;
-    plan_splits(tiles, g.K, tc ? 1024 : 128, tc ? 32 : 16, &splits, &kchunk);
+    plan_splits(tiles, g.K, tc ? 256 : 128, tc ? 32 : 16, &splits, &kchunk);
     const size_t esz = fp64 ? 8 : 4;
     const size_t pbytes = splits > 1 ? esz * (size_t)(g.M * g.N * splits) : 0;
     if (abytes + bbytes + pbytes > 0) CT_TRY(ws.ensure(abytes + bbytes + pbytes));
