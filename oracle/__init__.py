@@ -53,6 +53,10 @@ def lib():
         _lib.oracle_siddon_count.restype = I64
         _lib.oracle_siddon_fill.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                             C.c_double, i64p, i32p, dp]
+        _lib.oracle_fan_rays.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp]
+        _lib.oracle_siddon_count_rays.argtypes = [C.c_int, C.c_double, I64, dp, i32p]
+        _lib.oracle_siddon_count_rays.restype = I64
+        _lib.oracle_siddon_fill_rays.argtypes = [C.c_int, C.c_double, I64, dp, i64p, i32p, dp]
         _lib.oracle_dense_from_csr.argtypes = [I64, I64, i64p, i32p, dp, C.c_double, dp, I64]
         _lib.oracle_forward.argtypes = [I64, I64, i64p, i32p, dp, I64, dp, I64, dp, I64]
         _lib.oracle_householder_qr.argtypes = [I64, I64, dp, I64, dp]
@@ -77,7 +81,10 @@ class Geometry:
     """Parallel-beam geometry: n_side^2 pixels of width pixel_width centred on
     the origin, n_views angles over arc_deg (endpoint excluded), n_bins
     detector bins of width bin_width centred on the axis; optional
-    sqrt(lambda)*I rows below the ray rows."""
+    sqrt(lambda)*I rows below the ray rows.  kind="fan": the scanner of the
+    paper's Tables (Sec. 3.1, 3.2): a point source at distance source_dist
+    from the axis, n_views source positions over arc_deg, n_bins detectors
+    of an equiangular arc spanning fan_deg (bin_width unused)."""
     n_side: int
     n_views: int
     n_bins: int
@@ -85,6 +92,9 @@ class Geometry:
     bin_width: float = 1.0
     arc_deg: float = 180.0
     sqrt_lambda: float = 0.0
+    kind: str = "parallel"
+    source_dist: float = 0.0
+    fan_deg: float = 0.0
 
     @property
     def n(self) -> int:
@@ -132,9 +142,27 @@ class CSR:
         return sp.csr_matrix((self.val, self.col_idx, self.row_ptr), shape=(self.m, self.n))
 
 
+def fan_rays(g: Geometry) -> np.ndarray:
+    """(m, 3) table of (c, s, t) per fan-beam ray, i = v n_bins + d."""
+    out = np.empty(3 * g.m, np.float64)
+    lib().oracle_fan_rays(g.n_views, g.n_bins, g.arc_deg, g.fan_deg, g.source_dist, _p(out))
+    return out.reshape(g.m, 3)
+
+
 def siddon_csr(g: Geometry) -> CSR:
     """Siddon system matrix A (ray rows only) as CSR, entries in walk order."""
     L = lib()
+    if g.kind == "fan":
+        rays = np.ascontiguousarray(fan_rays(g))
+        cnt = np.empty(g.m, np.int32)
+        nnz = L.oracle_siddon_count_rays(g.n_side, g.pixel_width, g.m, _p(rays), _p(cnt, C.c_int32))
+        row_ptr = np.zeros(g.m + 1, np.int64)
+        np.cumsum(cnt, out=row_ptr[1:])
+        col = np.empty(nnz, np.int32)
+        val = np.empty(nnz, np.float64)
+        L.oracle_siddon_fill_rays(g.n_side, g.pixel_width, g.m, _p(rays), _p(row_ptr, C.c_int64),
+                                  _p(col, C.c_int32), _p(val))
+        return CSR(g.m, g.n, row_ptr, col, val)
     cnt = np.empty(g.m, np.int32)
     nnz = L.oracle_siddon_count(g.n_side, g.n_views, g.n_bins, g.pixel_width, g.bin_width,
                                 g.arc_deg, _p(cnt, C.c_int32))

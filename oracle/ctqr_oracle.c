@@ -55,6 +55,35 @@ EXPORT void oracle_view_table(int n_views, double arc_deg, double *cs)
     }
 }
 
+/* Fan-beam rays (equiangular arc detector centred on the source): source v
+ * at beta_v = v * arc / n_views (degrees, endpoint excluded), at distance
+ * sid from the rotation axis, S = sid (cos beta, sin beta); detector d at
+ * fan angle gamma_d = (d - (n_det - 1)/2) * fan / (n_det - 1) from the central
+ * ray, which points from S through the axis.  The ray's line in normal form
+ * {t (c, s) + u (-s, c)}: its direction (-cos(beta+gamma), -sin(beta+gamma))
+ * gives theta = beta + gamma + pi/2, (c, s) = (cos theta, sin theta), and
+ * t = S . (c, s) = -sid sin(gamma).  Values below 1e-15 in magnitude are
+ * snapped as in the view table.  out[3i..3i+2] = (c, s, t), i = v n_det + d. */
+EXPORT void oracle_fan_rays(int n_views, int n_det, double arc_deg, double fan_deg, double sid,
+                            double *out)
+{
+    for (int v = 0; v < n_views; ++v) {
+        const double beta = ((double)v * arc_deg / (double)n_views) * (M_PI / 180.0);
+        for (int d = 0; d < n_det; ++d) {
+            const double gamma =
+                (((double)d - 0.5 * (double)(n_det - 1)) * (fan_deg / (double)(n_det - 1))) * (M_PI / 180.0);
+            const double theta = (beta + gamma) + 0.5 * M_PI;
+            double c = cos(theta), s = sin(theta);
+            if (fabs(c) < 1e-15) { c = 0.0; s = (s > 0.0) ? 1.0 : -1.0; }
+            if (fabs(s) < 1e-15) { s = 0.0; c = (c > 0.0) ? 1.0 : -1.0; }
+            const int64_t i = (int64_t)v * n_det + d;
+            out[3 * i] = c;
+            out[3 * i + 1] = s;
+            out[3 * i + 2] = -(sid * sin(gamma));
+        }
+    }
+}
+
 /* Detector coordinate of bin d: bin centres spaced bin_width apart, centred
  * on the rotation axis. */
 static double bin_centre(int d, int n_bins, double bin_width)
@@ -180,6 +209,42 @@ EXPORT int64_t oracle_siddon_count(int n_side, int n_views, int n_bins, double w
     }
     free(cs);
     return total;
+}
+
+/* As oracle_siddon_count / oracle_siddon_fill for an explicit ray table
+ * rays[3i..3i+2] = (c, s, t) (any geometry, e.g. oracle_fan_rays). */
+EXPORT int64_t oracle_siddon_count_rays(int n_side, double w, int64_t m, const double *rays,
+                                        int32_t *row_nnz)
+{
+    int64_t total = 0;
+#pragma omp parallel reduction(+ : total)
+    {
+        int32_t *pix = (int32_t *)malloc(sizeof(int32_t) * (2 * (size_t)n_side + 2));
+        double *len = (double *)malloc(sizeof(double) * (2 * (size_t)n_side + 2));
+        double *work = (double *)malloc(sizeof(double) * (2 * (size_t)n_side + 4));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < m; ++i) {
+            int ns = oracle_siddon_ray(n_side, w, rays[3 * i], rays[3 * i + 1], rays[3 * i + 2], pix, len, work);
+            row_nnz[i] = ns;
+            total += ns;
+        }
+        free(pix); free(len); free(work);
+    }
+    return total;
+}
+
+EXPORT void oracle_siddon_fill_rays(int n_side, double w, int64_t m, const double *rays,
+                                    const int64_t *row_ptr, int32_t *col_idx, double *val)
+{
+#pragma omp parallel
+    {
+        double *work = (double *)malloc(sizeof(double) * (2 * (size_t)n_side + 4));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < m; ++i)
+            oracle_siddon_ray(n_side, w, rays[3 * i], rays[3 * i + 1], rays[3 * i + 2], col_idx + row_ptr[i],
+                              val + row_ptr[i], work);
+        free(work);
+    }
 }
 
 /* CSR of the ray rows of A (m rows, n_side^2 columns), segments in walk order.

@@ -123,3 +123,64 @@ def test_dense_has_lambda_rows(oracle_mod):
     A = O.dense_system(g)
     assert A.shape == (g.m + g.n, g.n)
     np.testing.assert_array_equal(A[g.m:], 0.05 * np.eye(g.n))
+
+
+# ---- fan-beam geometry (the paper's scanner, Sec. 3.1 / 3.2 tables) ----------
+
+FAN = [(16, 24, 21, 30.0, 40.0), (24, 36, 33, 25.0, 60.0)]  # n_side, views, dets, fan, source
+
+
+@pytest.mark.parametrize("n_side,n_views,n_det,fan,sid", FAN)
+def test_fan_rays_pass_through_their_source(oracle_mod, n_side, n_views, n_det, fan, sid):
+    """Every ray of view v contains the source point S_v = sid (cos b, sin b),
+    the central detector's ray contains the rotation axis, and the rays of a
+    view span the fan angle."""
+    O = oracle_mod
+    g = O.Geometry(n_side, n_views, n_det, arc_deg=360.0, kind="fan", source_dist=sid, fan_deg=fan)
+    r = O.fan_rays(g).reshape(n_views, n_det, 3)
+    for v in range(n_views):
+        b = math.radians(v * 360.0 / n_views)
+        S = (sid * math.cos(b), sid * math.sin(b))
+        dist = S[0] * r[v, :, 0] + S[1] * r[v, :, 1] - r[v, :, 2]
+        assert np.abs(dist).max() <= 1e-12 * sid
+        assert r[v, (n_det - 1) // 2, 2] == 0.0  # odd detector count: central ray
+        # directions (-s, c) of the extreme rays make the fan angle
+        d0 = np.array([-r[v, 0, 1], r[v, 0, 0]])
+        d1 = np.array([-r[v, -1, 1], r[v, -1, 0]])
+        ang = math.degrees(math.acos(max(-1.0, min(1.0, float(d0 @ d1)))))
+        assert abs(ang - fan) <= 1e-9
+        # and the central ray points from the source through the axis
+        dc = np.array([-r[v, (n_det - 1) // 2, 1], r[v, (n_det - 1) // 2, 0]])
+        assert dc @ np.array([-math.cos(b), -math.sin(b)]) > 1 - 1e-12
+
+
+@pytest.mark.parametrize("n_side,n_views,n_det,fan,sid", FAN)
+def test_fan_row_sums_equal_chord_length(oracle_mod, n_side, n_views, n_det, fan, sid):
+    O = oracle_mod
+    g = O.Geometry(n_side, n_views, n_det, arc_deg=360.0, kind="fan", source_dist=sid, fan_deg=fan)
+    csr = O.siddon_csr(g)
+    rays = O.fan_rays(g)
+    h = n_side / 2.0
+    for i in range(g.m):
+        got = float(np.sum(csr.val[csr.row_ptr[i]:csr.row_ptr[i + 1]]))
+        want = clip_length(rays[i, 0], rays[i, 1], rays[i, 2], -h, h, -h, h)
+        assert abs(got - want) <= 1e-13 * max(1.0, want), (i, got, want)
+
+
+def test_fan_beam_tends_to_parallel_beam(oracle_mod):
+    """A far source with a narrow fan (detector spacing 1 at the axis) gives
+    nearly parallel rays: view v, detector d of the fan matches the parallel
+    view a quarter turn later, detector n-1-d (orientation and sign pin).  An
+    even detector count puts the rays through pixel centres, away from the
+    grid lines where a tilt of 1e-6 would move a whole segment across."""
+    O = oracle_mod
+    n_side, n_views, n_det = 16, 24, 22
+    sid = 1e7
+    fan = math.degrees((n_det - 1) * 1.0 / sid)
+    gf = O.Geometry(n_side, n_views, n_det, arc_deg=360.0, kind="fan", source_dist=sid, fan_deg=fan)
+    gp = O.Geometry(n_side, n_views, n_det, arc_deg=360.0)
+    Af = O.dense_system(gf).reshape(n_views, n_det, -1)
+    Ap = O.dense_system(gp).reshape(n_views, n_det, -1)
+    q = n_views // 4
+    for v in range(n_views):
+        np.testing.assert_allclose(Af[v], Ap[(v + q) % n_views][::-1], rtol=0, atol=1e-4)
