@@ -82,10 +82,23 @@ typedef struct {
     int32_t n_views;
     int32_t n_bins;
     double pixel_width;  /* > 0, usually 1 */
-    double bin_width;    /* > 0, usually 1 */
-    double arc_deg;      /* usually 180 */
+    double bin_width;    /* > 0, usually 1 (parallel beam only) */
+    double arc_deg;      /* usually 180 (parallel) or 360 (fan) */
     double sqrt_lambda;  /* >= 0; 0 = no regularisation rows */
+    int32_t kind;        /* CT_GEOM_PARALLEL (0, the default) or CT_GEOM_FAN */
+    double source_dist;  /* fan: source to rotation axis, > the image half-diagonal */
+    double fan_deg;      /* fan: angle spanned by the n_bins detectors, in (0, 180) */
 } ct_geometry;
+
+/* ct_geometry.kind.  Parallel beam: view v at theta_v = v * arc / n_views,
+ * bin d at signed distance (d - (n_bins-1)/2) * bin_width from the axis.
+ * Fan beam (the scanner of the paper's Sec. 3.1 / 3.2 tables): source v at
+ * beta_v = v * arc / n_views and distance source_dist from the axis,
+ * detector d of an equiangular arc at fan angle
+ * gamma_d = (d - (n_bins-1)/2) * fan_deg / (n_bins-1) from the central ray
+ * (which points from the source through the axis).  Ray i = v n_bins + d. */
+#define CT_GEOM_PARALLEL 0
+#define CT_GEOM_FAN 1
 
 typedef struct {
     ct_precision precision;

@@ -291,8 +291,16 @@ ct_status ctqr::build_system_impl(const ct_geometry *geom, ct_precision storage,
     const ct_geometry g = *geom;
     if (g.n_side < 1 || g.n_views < 1 || g.n_bins < 1 || !(g.pixel_width > 0) ||
         !(g.bin_width > 0) || !(g.arc_deg > 0) || !(g.sqrt_lambda >= 0) ||
-        !std::isfinite(g.sqrt_lambda) || g.n_side > 46340) {
+        !std::isfinite(g.sqrt_lambda) || g.n_side > 46340 ||
+        (g.kind != CT_GEOM_PARALLEL && g.kind != CT_GEOM_FAN)) {
         set_error("invalid geometry");
+        return CT_ERR_ARG;
+    }
+    if (g.kind == CT_GEOM_FAN &&
+        (g.n_bins < 2 || !(g.fan_deg > 0 && g.fan_deg < 180) ||
+         !(g.source_dist > 0.7071067811865476 * g.n_side * g.pixel_width) || !std::isfinite(g.source_dist))) {
+        set_error("invalid fan-beam geometry: needs n_bins >= 2, 0 < fan_deg < 180 and the source "
+                  "outside the image (source_dist > half-diagonal)");
         return CT_ERR_ARG;
     }
     if ((int64_t)g.n_views * g.n_bins > INT32_MAX) {
@@ -320,15 +328,41 @@ ct_status ctqr::build_system_impl(const ct_geometry *geom, ct_precision storage,
         delete sys;
         return st;
     };
-    // View table: theta_v = v * arc / n_views degrees; exact axis values.
-    std::vector<double> cs(2 * (size_t)g.n_views);
-    for (int v = 0; v < g.n_views; ++v) {
-        double theta = ((double)v * g.arc_deg / (double)g.n_views) * (M_PI / 180.0);
-        double c = std::cos(theta), sn = std::sin(theta);
+    // Ray geometry on the host in FP64 (libm cos/sin), exact axis values.
+    // Parallel: per-view (cos, sin), theta_v = v * arc / n_views degrees.
+    // Fan: per-ray (c, s, t) of the line from source v through detector d:
+    // theta = beta_v + gamma_d + 90 degrees, t = -source_dist * sin(gamma_d).
+    auto snap = [](double &c, double &sn) {
         if (std::fabs(c) < 1e-15) { c = 0.0; sn = (sn > 0.0) ? 1.0 : -1.0; }
         if (std::fabs(sn) < 1e-15) { sn = 0.0; c = (c > 0.0) ? 1.0 : -1.0; }
-        cs[2 * v] = c;
-        cs[2 * v + 1] = sn;
+    };
+    std::vector<double> cs;
+    if (g.kind == CT_GEOM_FAN) {
+        cs.resize(3 * (size_t)sys->m);
+        for (int v = 0; v < g.n_views; ++v) {
+            const double beta = ((double)v * g.arc_deg / (double)g.n_views) * (M_PI / 180.0);
+            for (int d = 0; d < g.n_bins; ++d) {
+                const double gamma =
+                    (((double)d - 0.5 * (double)(g.n_bins - 1)) * (g.fan_deg / (double)(g.n_bins - 1))) *
+                    (M_PI / 180.0);
+                const double theta = (beta + gamma) + 0.5 * M_PI;
+                double c = std::cos(theta), sn = std::sin(theta);
+                snap(c, sn);
+                const size_t r = (size_t)v * g.n_bins + d;
+                cs[3 * r] = c;
+                cs[3 * r + 1] = sn;
+                cs[3 * r + 2] = -(g.source_dist * std::sin(gamma));
+            }
+        }
+    } else {
+        cs.resize(2 * (size_t)g.n_views);
+        for (int v = 0; v < g.n_views; ++v) {
+            double theta = ((double)v * g.arc_deg / (double)g.n_views) * (M_PI / 180.0);
+            double c = std::cos(theta), sn = std::sin(theta);
+            snap(c, sn);
+            cs[2 * v] = c;
+            cs[2 * v + 1] = sn;
+        }
     }
     ct_status st;
     if ((st = dmalloc(&sys->d_cs, cs.size())) != CT_OK) return fail(st);
@@ -337,7 +371,7 @@ ct_status ctqr::build_system_impl(const ct_geometry *geom, ct_precision storage,
     if ((st = dmalloc(&sys->row_nnz, sys->m)) != CT_OK) return fail(st);
     if ((st = dmalloc(&sys->row_ptr, sys->m + 1)) != CT_OK) return fail(st);
     SiddonArgs a{g.n_side, g.n_views, g.n_bins, g.pixel_width, g.bin_width, g.sqrt_lambda,
-                 sys->d_cs, sys->row_nnz, sys->row_ptr, nullptr, nullptr, &sys->tmp};
+                 sys->d_cs, g.kind, sys->row_nnz, sys->row_ptr, nullptr, nullptr, &sys->tmp};
     if ((st = siddon_build(a, s)) != CT_OK) return fail(st);
     int64_t nnz = 0;
     if (cudaMemcpyAsync(&nnz, sys->row_ptr + sys->m, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

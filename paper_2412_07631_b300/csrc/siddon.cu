@@ -23,6 +23,7 @@ namespace {
 struct Geo {
     int n_side, n_views, n_bins;
     double w, bw;
+    int kind;  // CT_GEOM_PARALLEL: cs = per-view (cos, sin); CT_GEOM_FAN: cs = per-ray (c, s, t)
 };
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
@@ -127,6 +128,12 @@ __device__ int siddon_walk(const Geo &g, double c, double sn, double t, Emit emi
 
 __device__ __forceinline__ void ray_params(const Geo &g, const double *cs, int i, double &c,
                                            double &sn, double &t) {
+    if (g.kind == CT_GEOM_FAN) {  // host-computed table of the ray lines
+        c = cs[3 * (int64_t)i];
+        sn = cs[3 * (int64_t)i + 1];
+        t = cs[3 * (int64_t)i + 2];
+        return;
+    }
     int v = i / g.n_bins, d = i - v * g.n_bins;
     c = cs[2 * v];
     sn = cs[2 * v + 1];
@@ -306,7 +313,7 @@ ct_status exclusive_scan(const int32_t *in, int64_t n, int64_t *out_np1, Scratch
 }
 
 ct_status siddon_build(const SiddonArgs &a, cudaStream_t s) {
-    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width};
+    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width, a.kind};
     const int m = a.n_views * a.n_bins;
     const int threads = 128;
     const unsigned blocks = (unsigned)ceil_div(m, threads);
@@ -320,7 +327,7 @@ ct_status siddon_build(const SiddonArgs &a, cudaStream_t s) {
 
 ct_status siddon_fill(const SiddonArgs &a, void *dense, bool dense_fp64, int64_t lda,
                       cudaStream_t s) {
-    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width};
+    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width, a.kind};
     const int m = a.n_views * a.n_bins;
     const int threads = 128;
     const unsigned blocks = (unsigned)ceil_div(m, threads);
