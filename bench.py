@@ -45,13 +45,39 @@ WORKLOADS = {
     "c3": (256, 360, 364, 0.05, 512, 5e3, 10),
     "c2": (128, 180, 182, 0.05, 64, 1e4, 10),
     "c1": (32, 60, 46, 0.0, 1, None, 8),
+    # fan beam, the paper's scanner scaled to 256^2: 360 source positions over
+    # 360 degrees, 512 detectors over a 30-degree fan, source at 720 pixels
+    # (the fan covers the image's half-diagonal of 181 pixels)
+    "fan256": (256, 360, 512, 0.05, 512, 5e3, 10),
 }
+FAN = {"fan256": (720.0, 30.0)}  # name: (source_dist, fan_deg)
+
+
+def geometry_of(ct, name):
+    ns, nv, nb, sl = WORKLOADS[name][:4]
+    if name in FAN:
+        sid, fan = FAN[name]
+        return ct.make_geometry(ns, nv, nb, sl, kind="fan", source_dist=sid, fan_deg=fan)
+    return ct.make_geometry(ns, nv, nb, sl)
+
+
+def oracle_geometry_of(O, name):
+    ns, nv, nb, sl = WORKLOADS[name][:4]
+    if name in FAN:
+        sid, fan = FAN[name]
+        return O.Geometry(ns, nv, nb, arc_deg=360.0, sqrt_lambda=sl, kind="fan", source_dist=sid, fan_deg=fan)
+    return O.Geometry(ns, nv, nb, sqrt_lambda=sl)
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
 
 
 def workload_desc(name):
     ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
     noise = f"Poisson I0={i0:g}" if i0 else "noiseless"
+    if name in FAN:
+        sid, fan = FAN[name]
+        return (f"{ns}x{ns} fan-beam Siddon, {nv} sources x {nb} detectors over {fan:g} deg, source at "
+                f"{sid:g} px" + (f" + sqrt(lambda)={sl} I rows" if sl > 0 else "")
+                + f", {k} sinograms of {ne}-ellipse phantoms, {noise}")
     return (f"{ns}x{ns} parallel-beam Siddon, {nv} views x {nb} bins"
             + (f" + sqrt(lambda)={sl} I rows" if sl > 0 else "")
             + f", {k} sinograms of {ne}-ellipse phantoms, {noise}")
@@ -138,7 +164,7 @@ def make_inputs(ct, torch, name, rank=0):
     ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
     first = synth.BASE_SEED + rank * k
     X = synth.phantom_batch(ns, k, ne, first)
-    sysg = ct.System(ct.make_geometry(ns, nv, nb, sl), "fp32")
+    sysg = ct.System(geometry_of(ct, name), "fp32")
     P = sysg.forward(torch.from_numpy(np.ascontiguousarray(X.T)).cuda()).cpu().numpy().T
     sysg.free()
     del sysg
@@ -186,7 +212,7 @@ def cpu_oracle_sample(name, cols=None):
     (TFLOP/s, seconds, description, cores)."""
     import oracle as O
     ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
-    g = O.Geometry(ns, nv, nb, sqrt_lambda=sl)
+    g = oracle_geometry_of(O, name)
     n = g.n
     w = cols or min(n, 512)
     csr = O.siddon_csr(g)
@@ -310,7 +336,7 @@ def main():
         dist.init_process_group("nccl")
     peaks, peak_src = load_peaks()
 
-    geom = ct.make_geometry(ns, nv, nb, sl)
+    geom = geometry_of(ct, args.workload)
     Xtrue, Bh = make_inputs(ct, torch, args.workload, rank)
     io_dt = torch.float32 if args.precision == "fp32" else torch.float64
     B = torch.from_numpy(Bh).to(io_dt).cuda()
@@ -397,7 +423,7 @@ def main():
     acc = {}
     if rank == 0 and not args.no_cert and sl > 0:
         import oracle as O
-        g = O.Geometry(ns, nv, nb, sqrt_lambda=sl)
+        g = oracle_geometry_of(O, args.workload)
         csr = O.siddon_csr(g)
         pick = np.linspace(0, k - 1, min(k, 4)).astype(int)
         cert = O.certificate(g, csr, np.asfortranarray(Bh[pick].T), np.asfortranarray(Xn[:, pick]))
