@@ -162,7 +162,8 @@ def make_inputs(ct, torch, name, rank=0):
     product), Poisson noise from the seeded generator.  Untimed."""
     from paper_2412_07631_b300 import synth
     ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
-    first = synth.BASE_SEED + rank * k
+    from paper_2412_07631_b300 import replicas
+    _, first = replicas.rank_slices(rank, int(os.environ.get("WORLD_SIZE", "1")), k, synth.BASE_SEED)
     X = synth.phantom_batch(ns, k, ne, first)
     sysg = ct.System(geometry_of(ct, name), "fp32")
     P = sysg.forward(torch.from_numpy(np.ascontiguousarray(X.T)).cuda()).cpu().numpy().T
@@ -367,10 +368,8 @@ def main():
     clk = clocks.stop()
     launches = ct.stats_read()["launches"]
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    from paper_2412_07631_b300 import replicas
+    ms = replicas.max_over_ranks(ms, dist, device="cuda")
     step_fl = (qr_fl + solve_fl) * world
     value = step_fl / (ms * 1e-3) / 1e12
     qr_ms = float(np.median([p["qr"] for p in phases]))
