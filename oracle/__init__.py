@@ -53,6 +53,10 @@ def lib():
         _lib.oracle_siddon_count.restype = I64
         _lib.oracle_siddon_fill.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                             C.c_double, i64p, i32p, dp]
+        _lib.oracle_joseph_ray.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, i32p, dp]
+        _lib.oracle_joseph_count_rays.argtypes = [C.c_int, C.c_double, I64, dp, i32p]
+        _lib.oracle_joseph_count_rays.restype = I64
+        _lib.oracle_joseph_fill_rays.argtypes = [C.c_int, C.c_double, I64, dp, i64p, i32p, dp]
         _lib.oracle_fan_rays.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp]
         _lib.oracle_siddon_count_rays.argtypes = [C.c_int, C.c_double, I64, dp, i32p]
         _lib.oracle_siddon_count_rays.restype = I64
@@ -95,6 +99,7 @@ class Geometry:
     kind: str = "parallel"
     source_dist: float = 0.0
     fan_deg: float = 0.0
+    projector: str = "siddon"  # or "joseph"
 
     @property
     def n(self) -> int:
@@ -149,9 +154,45 @@ def fan_rays(g: Geometry) -> np.ndarray:
     return out.reshape(g.m, 3)
 
 
+def ray_table(g: Geometry) -> np.ndarray:
+    """(m, 3) table of (c, s, t) per ray of either geometry."""
+    if g.kind == "fan":
+        return fan_rays(g)
+    cs = view_table(g)
+    d = np.arange(g.n_bins, dtype=np.float64)
+    t = (d - 0.5 * (g.n_bins - 1)) * g.bin_width  # the same two roundings as the kernels
+    out = np.empty((g.n_views, g.n_bins, 3))
+    out[:, :, 0] = cs[:, None, 0]
+    out[:, :, 1] = cs[:, None, 1]
+    out[:, :, 2] = t[None, :]
+    return out.reshape(g.m, 3)
+
+
+def joseph_ray(g: Geometry, c: float, s: float, t: float):
+    """Entries (pixel index, weight) of one ray under Joseph's projector."""
+    cap = 2 * g.n_side + 2
+    pix = np.empty(cap, np.int32)
+    val = np.empty(cap, np.float64)
+    k = lib().oracle_joseph_ray(g.n_side, g.pixel_width, c, s, t, _p(pix, C.c_int32), _p(val))
+    return pix[:k].copy(), val[:k].copy()
+
+
 def siddon_csr(g: Geometry) -> CSR:
-    """Siddon system matrix A (ray rows only) as CSR, entries in walk order."""
+    """The system matrix A (ray rows only) as CSR, entries in walk order:
+    Siddon's exact lengths, or Joseph's interpolation weights when
+    g.projector == "joseph"."""
     L = lib()
+    if g.projector == "joseph":
+        rays = np.ascontiguousarray(ray_table(g))
+        cnt = np.empty(g.m, np.int32)
+        nnz = L.oracle_joseph_count_rays(g.n_side, g.pixel_width, g.m, _p(rays), _p(cnt, C.c_int32))
+        row_ptr = np.zeros(g.m + 1, np.int64)
+        np.cumsum(cnt, out=row_ptr[1:])
+        col = np.empty(nnz, np.int32)
+        val = np.empty(nnz, np.float64)
+        L.oracle_joseph_fill_rays(g.n_side, g.pixel_width, g.m, _p(rays), _p(row_ptr, C.c_int64),
+                                  _p(col, C.c_int32), _p(val))
+        return CSR(g.m, g.n, row_ptr, col, val)
     if g.kind == "fan":
         rays = np.ascontiguousarray(fan_rays(g))
         cnt = np.empty(g.m, np.int32)

@@ -211,6 +211,81 @@ EXPORT int64_t oracle_siddon_count(int n_side, int n_views, int n_bins, double w
     return total;
 }
 
+/* Joseph's projector for one ray (the paper's matrices come from Joseph's
+ * method, Sec. 3.1).  The ray {t (c, s) + u (-s, c)} is sampled once per
+ * pixel row when |c| >= |s| (the ray runs closer to the y axis), else once per
+ * pixel column, on the row's (column's) centre line.  Its position across
+ * that line is interpolated linearly between the two nearest pixel centres,
+ * and both weights are scaled by the ray length per row (column), w/|c|
+ * (w/|s|).  Pixels outside the grid take no weight and zero weights are not
+ * stored; entries come in sampling order, the lower pixel index of a pair
+ * first.  pix/val must hold 2*n_side entries.  Returns the count. */
+EXPORT int oracle_joseph_ray(int n_side, double w, double c, double s, double t, int32_t *pix,
+                             double *val)
+{
+    const double h = 0.5 * (double)n_side * w;
+    int n = 0;
+    const int rows = fabs(c) >= fabs(s);
+    const double L = w / (rows ? fabs(c) : fabs(s));
+    for (int k = 0; k < n_side; ++k) {
+        /* centre line of row (column) k, the ray's crossing point on it, and
+         * its fractional pixel coordinate along the line */
+        const double q = ((double)k + 0.5) * w - h;
+        double p;
+        if (rows) {
+            const double a = (q - t * s) / c; /* x = t c - u s at y = q */
+            p = t * c - s * a;
+        } else {
+            const double a = (t * c - q) / s; /* y = t s + u c at x = q */
+            p = t * s + c * a;
+        }
+        const double fp = (p + h) / w - 0.5;
+        const double fl = floor(fp);
+        if (!(fl >= -1.0 && fl <= (double)n_side - 1.0)) continue;
+        const double f = fp - fl;
+        const int j = (int)fl;
+        if (j >= 0) {
+            pix[n] = rows ? k * n_side + j : j * n_side + k;
+            val[n] = (1.0 - f) * L;
+            ++n;
+        }
+        if (j + 1 < n_side && f > 0.0) {
+            pix[n] = rows ? k * n_side + (j + 1) : (j + 1) * n_side + k;
+            val[n] = f * L;
+            ++n;
+        }
+    }
+    return n;
+}
+
+EXPORT int64_t oracle_joseph_count_rays(int n_side, double w, int64_t m, const double *rays,
+                                        int32_t *row_nnz)
+{
+    int64_t total = 0;
+#pragma omp parallel reduction(+ : total)
+    {
+        int32_t *pix = (int32_t *)malloc(sizeof(int32_t) * (2 * (size_t)n_side + 2));
+        double *val = (double *)malloc(sizeof(double) * (2 * (size_t)n_side + 2));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < m; ++i) {
+            int ns = oracle_joseph_ray(n_side, w, rays[3 * i], rays[3 * i + 1], rays[3 * i + 2], pix, val);
+            row_nnz[i] = ns;
+            total += ns;
+        }
+        free(pix); free(val);
+    }
+    return total;
+}
+
+EXPORT void oracle_joseph_fill_rays(int n_side, double w, int64_t m, const double *rays,
+                                    const int64_t *row_ptr, int32_t *col_idx, double *val)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i)
+        oracle_joseph_ray(n_side, w, rays[3 * i], rays[3 * i + 1], rays[3 * i + 2], col_idx + row_ptr[i],
+                          val + row_ptr[i]);
+}
+
 /* As oracle_siddon_count / oracle_siddon_fill for an explicit ray table
  * rays[3i..3i+2] = (c, s, t) (any geometry, e.g. oracle_fan_rays). */
 EXPORT int64_t oracle_siddon_count_rays(int n_side, double w, int64_t m, const double *rays,

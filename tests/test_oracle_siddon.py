@@ -184,3 +184,79 @@ def test_fan_beam_tends_to_parallel_beam(oracle_mod):
     q = n_views // 4
     for v in range(n_views):
         np.testing.assert_allclose(Af[v], Ap[(v + q) % n_views][::-1], rtol=0, atol=1e-4)
+
+
+# ---- Joseph's projector (the paper's matrices, Sec. 3.1) ----------------------
+
+def test_joseph_hand_cases(oracle_mod):
+    """Hand-derived entries on a 4x4 grid (pixels 0..15, row-major from the
+    bottom-left, unit pixels): a horizontal ray along the centre of row 2 has
+    weight 1 in each of its pixels; a vertical ray at x = 0.25 (fractional
+    column position 1.75) splits 1/4 : 3/4 between columns 1 and 2 of every
+    row; the 45-degree ray through the origin meets row centres at pixel
+    centres, weight sqrt(2) each."""
+    O = oracle_mod
+    g = O.Geometry(4, 1, 1, projector="joseph")
+    pix, val = O.joseph_ray(g, 0.0, 1.0, 0.5)
+    assert list(pix) == [8, 9, 10, 11] and np.all(val == 1.0)
+    pix, val = O.joseph_ray(g, 1.0, 0.0, 0.25)
+    assert list(pix) == [1, 2, 5, 6, 9, 10, 13, 14]
+    np.testing.assert_array_equal(val, [0.25, 0.75] * 4)
+    r = math.sqrt(0.5)
+    pix, val = O.joseph_ray(g, r, r, 0.0)
+    big = val > 1e-12
+    assert list(pix[big]) == [3, 6, 9, 12]
+    np.testing.assert_allclose(val[big], math.sqrt(2.0), rtol=1e-15)
+
+
+def test_joseph_integrates_linear_images_exactly(oracle_mod):
+    """Linear interpolation reproduces a linear image exactly, and the row
+    sampling is the midpoint rule along the ray, exact for linear functions:
+    for rays whose sampled positions keep both neighbours inside the grid,
+    sum_j a_ij f(centre_j) = the integral of f along the ray across the grid's
+    sampled strip.  With f = 1 this is the row-sum (strip length) invariant."""
+    O = oracle_mod
+    n = 24
+    g = O.Geometry(n, 1, 1, projector="joseph")
+    h = n / 2.0
+    ys, xs = np.divmod(np.arange(n * n), n)
+    cx, cy = xs - h + 0.5, ys - h + 0.5
+    rng = np.random.default_rng(3)
+    al, be, ga = 0.3, -0.7, 1.9
+    f = al + be * cx + ga * cy
+    checked = 0
+    for _ in range(300):
+        th = rng.uniform(0, math.pi)
+        c, s = math.cos(th), math.sin(th)
+        t = rng.uniform(-4.0, 4.0)
+        pix, val = O.joseph_ray(g, c, s, t)
+        rows = abs(c) >= abs(s)
+        # sampled positions across the stepping lines must stay within [centre 0, centre n-1]
+        q = (np.arange(n) + 0.5) - h
+        p = (t * c - s * (q - t * s) / c) if rows else (t * s + c * (t * c - q) / s)
+        if not np.all((p >= -h + 0.5) & (p <= h - 0.5)):
+            continue
+        checked += 1
+        L = 1.0 / (abs(c) if rows else abs(s))
+        # integral of f along the ray over the strip: parametrise by the stepping coordinate
+        pts_x = p if rows else q
+        pts_y = q if rows else p
+        want = L * np.sum(al + be * pts_x + ga * pts_y)  # midpoint rule, exact for linear f
+        got = float(np.dot(val, f[pix]))
+        assert abs(got - want) <= 1e-11 * max(1.0, abs(want))
+        assert abs(val.sum() - n * L) <= 1e-12 * n * L
+    assert checked > 50
+
+
+def test_joseph_same_line_same_row(oracle_mod):
+    O = oracle_mod
+    g = O.Geometry(16, 1, 1, projector="joseph")
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        th = rng.uniform(0, math.pi)
+        c, s, t = math.cos(th), math.sin(th), rng.uniform(-9, 9)
+        a = dict(zip(*O.joseph_ray(g, c, s, t)))
+        b = dict(zip(*O.joseph_ray(g, -c, -s, -t)))
+        assert set(a) == set(b)
+        for k in a:
+            assert abs(a[k] - b[k]) <= 1e-12
