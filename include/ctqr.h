@@ -88,7 +88,18 @@ typedef struct {
     int32_t kind;        /* CT_GEOM_PARALLEL (0, the default) or CT_GEOM_FAN */
     double source_dist;  /* fan: source to rotation axis, > the image half-diagonal */
     double fan_deg;      /* fan: angle spanned by the n_bins detectors, in (0, 180) */
+    int32_t projector;   /* CT_PROJ_SIDDON (0, the default) or CT_PROJ_JOSEPH */
 } ct_geometry;
+
+/* ct_geometry.projector.  Siddon: a_ij = exact length of ray i in pixel j.
+ * Joseph (the method behind the paper's matrices, Sec. 3.1): the ray is
+ * sampled once per pixel row when |cos theta| >= |sin theta| (else once per
+ * pixel column) on the row's (column's) centre line; its position there is
+ * interpolated linearly between the two nearest pixel centres, weights
+ * scaled by the ray length per row (column); pixels outside the grid and
+ * zero weights are dropped. */
+#define CT_PROJ_SIDDON 0
+#define CT_PROJ_JOSEPH 1
 
 /* ct_geometry.kind.  Parallel beam: view v at theta_v = v * arc / n_views,
  * bin d at signed distance (d - (n_bins-1)/2) * bin_width from the axis.

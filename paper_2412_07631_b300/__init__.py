@@ -25,7 +25,7 @@ class Geometry(C.Structure):
     _fields_ = [("n_side", C.c_int32), ("n_views", C.c_int32), ("n_bins", C.c_int32),
                 ("pixel_width", C.c_double), ("bin_width", C.c_double),
                 ("arc_deg", C.c_double), ("sqrt_lambda", C.c_double), ("kind", C.c_int32),
-                ("source_dist", C.c_double), ("fan_deg", C.c_double)]
+                ("source_dist", C.c_double), ("fan_deg", C.c_double), ("projector", C.c_int32)]
 
 
 class Opts(C.Structure):
@@ -127,17 +127,20 @@ def _ptr(t):
 
 
 GEOMETRY_KINDS = {"parallel": 0, "fan": 1}
+PROJECTORS = {"siddon": 0, "joseph": 1}
 
 
 def make_geometry(n_side, n_views, n_bins, sqrt_lambda=0.0, pixel_width=1.0, bin_width=1.0,
-                  arc_deg=None, kind="parallel", source_dist=0.0, fan_deg=0.0) -> Geometry:
+                  arc_deg=None, kind="parallel", source_dist=0.0, fan_deg=0.0,
+                  projector="siddon") -> Geometry:
     """Parallel beam (arc 180 by default) or kind="fan": a point source at
     source_dist from the axis and an equiangular arc of n_bins detectors
-    spanning fan_deg (arc 360 by default)."""
+    spanning fan_deg (arc 360 by default).  projector: "siddon" (exact
+    lengths) or "joseph" (interpolated samples)."""
     if arc_deg is None:
         arc_deg = 360.0 if kind == "fan" else 180.0
     return Geometry(n_side, n_views, n_bins, pixel_width, bin_width, arc_deg, sqrt_lambda,
-                    GEOMETRY_KINDS[kind], source_dist, fan_deg)
+                    GEOMETRY_KINDS[kind], source_dist, fan_deg, PROJECTORS[projector])
 
 
 class System:

@@ -292,7 +292,8 @@ ct_status ctqr::build_system_impl(const ct_geometry *geom, ct_precision storage,
     if (g.n_side < 1 || g.n_views < 1 || g.n_bins < 1 || !(g.pixel_width > 0) ||
         !(g.bin_width > 0) || !(g.arc_deg > 0) || !(g.sqrt_lambda >= 0) ||
         !std::isfinite(g.sqrt_lambda) || g.n_side > 46340 ||
-        (g.kind != CT_GEOM_PARALLEL && g.kind != CT_GEOM_FAN)) {
+        (g.kind != CT_GEOM_PARALLEL && g.kind != CT_GEOM_FAN) ||
+        (g.projector != CT_PROJ_SIDDON && g.projector != CT_PROJ_JOSEPH)) {
         set_error("invalid geometry");
         return CT_ERR_ARG;
     }
@@ -371,7 +372,7 @@ ct_status ctqr::build_system_impl(const ct_geometry *geom, ct_precision storage,
     if ((st = dmalloc(&sys->row_nnz, sys->m)) != CT_OK) return fail(st);
     if ((st = dmalloc(&sys->row_ptr, sys->m + 1)) != CT_OK) return fail(st);
     SiddonArgs a{g.n_side, g.n_views, g.n_bins, g.pixel_width, g.bin_width, g.sqrt_lambda,
-                 sys->d_cs, g.kind, sys->row_nnz, sys->row_ptr, nullptr, nullptr, &sys->tmp};
+                 sys->d_cs, g.kind, g.projector, sys->row_nnz, sys->row_ptr, nullptr, nullptr, &sys->tmp};
     if ((st = siddon_build(a, s)) != CT_OK) return fail(st);
     int64_t nnz = 0;
     if (cudaMemcpyAsync(&nnz, sys->row_ptr + sys->m, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

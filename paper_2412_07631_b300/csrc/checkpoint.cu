@@ -16,7 +16,7 @@ namespace ctqr {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'T', 'Q', 'R', 'F', 'A', 'C', '1'};
-constexpr uint32_t kVersion = 2;  // 2: geometry with kind / source_dist / fan_deg
+constexpr uint32_t kVersion = 3;  // 2: fan-beam geometry fields; 3: projector
 constexpr size_t kChunk = (size_t)64 << 20;
 
 struct FileHeader {
@@ -51,7 +51,7 @@ bool same_geom(const ct_geometry &a, const ct_geometry &b) {
     return a.n_side == b.n_side && a.n_views == b.n_views && a.n_bins == b.n_bins &&
            a.pixel_width == b.pixel_width && a.bin_width == b.bin_width && a.arc_deg == b.arc_deg &&
            a.sqrt_lambda == b.sqrt_lambda && a.kind == b.kind && a.source_dist == b.source_dist &&
-           a.fan_deg == b.fan_deg;
+           a.fan_deg == b.fan_deg && a.projector == b.projector;
 }
 
 // Device regions of a factor in file order: (pointer, rows, cols, ld).

@@ -11,6 +11,7 @@ struct SiddonArgs {
     double pixel_width, bin_width, sqrt_lambda;
     const double *d_cs;  // parallel: [2*n_views] (cos, sin) per view; fan: [3*m] (c, s, t) per ray
     int kind;            // CT_GEOM_PARALLEL / CT_GEOM_FAN
+    int projector;       // CT_PROJ_SIDDON / CT_PROJ_JOSEPH
     int32_t *d_row_nnz;  // [m]
     int64_t *d_row_ptr;  // [m+1]
     int32_t *d_col;      // [nnz]

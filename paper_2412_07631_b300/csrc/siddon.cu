@@ -24,6 +24,7 @@ struct Geo {
     int n_side, n_views, n_bins;
     double w, bw;
     int kind;  // CT_GEOM_PARALLEL: cs = per-view (cos, sin); CT_GEOM_FAN: cs = per-ray (c, s, t)
+    int projector;  // CT_PROJ_SIDDON / CT_PROJ_JOSEPH
 };
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
@@ -126,6 +127,50 @@ __device__ int siddon_walk(const Geo &g, double c, double sn, double t, Emit emi
     return nseg;
 }
 
+// Joseph's projector for ray (c, s, t): sampled once per pixel row when
+// |c| >= |s| (else per column) on its centre line, the crossing point
+// interpolated linearly between the two nearest pixel centres, weights
+// scaled by the ray length per row (column).  Pixels outside the grid and
+// zero weights are dropped; a pair's lower pixel index comes first.  The
+// operations are the oracle's, one IEEE rounding each.
+template <class Emit>
+__device__ int joseph_walk(const Geo &g, double c, double s, double t, Emit emit) {
+    const double h = dmul(dmul(0.5, (double)g.n_side), g.w);
+    const bool rows = fabs(c) >= fabs(s);
+    const double L = ddiv(g.w, rows ? fabs(c) : fabs(s));
+    int n = 0;
+    for (int k = 0; k < g.n_side; ++k) {
+        const double q = dsub(dmul(dadd((double)k, 0.5), g.w), h);
+        double p;
+        if (rows) {
+            const double a = ddiv(dsub(q, dmul(t, s)), c);  // x = t c - u s at y = q
+            p = dsub(dmul(t, c), dmul(s, a));
+        } else {
+            const double a = ddiv(dsub(dmul(t, c), q), s);  // y = t s + u c at x = q
+            p = dadd(dmul(t, s), dmul(c, a));
+        }
+        const double fp = dsub(ddiv(dadd(p, h), g.w), 0.5);
+        const double fl = floor(fp);
+        if (!(fl >= -1.0 && fl <= (double)g.n_side - 1.0)) continue;
+        const double f = dsub(fp, fl);
+        const int j = (int)fl;
+        if (j >= 0) {
+            emit(n, rows ? k * g.n_side + j : j * g.n_side + k, dmul(dsub(1.0, f), L));
+            ++n;
+        }
+        if (j + 1 < g.n_side && f > 0.0) {
+            emit(n, rows ? k * g.n_side + (j + 1) : (j + 1) * g.n_side + k, dmul(f, L));
+            ++n;
+        }
+    }
+    return n;
+}
+
+template <class Emit>
+__device__ __forceinline__ int project_walk(const Geo &g, double c, double sn, double t, Emit emit) {
+    return g.projector == CT_PROJ_JOSEPH ? joseph_walk(g, c, sn, t, emit) : siddon_walk(g, c, sn, t, emit);
+}
+
 __device__ __forceinline__ void ray_params(const Geo &g, const double *cs, int i, double &c,
                                            double &sn, double &t) {
     if (g.kind == CT_GEOM_FAN) {  // host-computed table of the ray lines
@@ -145,7 +190,7 @@ __global__ void siddon_count_kernel(Geo g, const double *cs, int32_t *row_nnz) {
     if (i >= g.n_views * g.n_bins) return;
     double c, sn, t;
     ray_params(g, cs, i, c, sn, t);
-    row_nnz[i] = siddon_walk(g, c, sn, t, [](int, int, double) {});
+    row_nnz[i] = project_walk(g, c, sn, t, [](int, int, double) {});
 }
 
 // Writes the CSR row of ray i and adds its lengths into the dense column-major
@@ -160,7 +205,7 @@ __global__ void siddon_fill_kernel(Geo g, const double *cs, const int64_t *row_p
     const int64_t base = row_ptr[i];
     int run_pix = -1;
     double run_len = 0.0;
-    siddon_walk(g, c, sn, t, [&](int q, int pix, double L) {
+    project_walk(g, c, sn, t, [&](int q, int pix, double L) {
         col_idx[base + q] = pix;
         val[base + q] = L;
         if (dense) {
@@ -313,7 +358,7 @@ ct_status exclusive_scan(const int32_t *in, int64_t n, int64_t *out_np1, Scratch
 }
 
 ct_status siddon_build(const SiddonArgs &a, cudaStream_t s) {
-    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width, a.kind};
+    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width, a.kind, a.projector};
     const int m = a.n_views * a.n_bins;
     const int threads = 128;
     const unsigned blocks = (unsigned)ceil_div(m, threads);
@@ -327,7 +372,7 @@ ct_status siddon_build(const SiddonArgs &a, cudaStream_t s) {
 
 ct_status siddon_fill(const SiddonArgs &a, void *dense, bool dense_fp64, int64_t lda,
                       cudaStream_t s) {
-    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width, a.kind};
+    Geo g{a.n_side, a.n_views, a.n_bins, a.pixel_width, a.bin_width, a.kind, a.projector};
     const int m = a.n_views * a.n_bins;
     const int threads = 128;
     const unsigned blocks = (unsigned)ceil_div(m, threads);

@@ -216,3 +216,27 @@ def test_fan_beam_solve_matches_oracle(oracle_mod, precision, tol):
     err = rel_err_cols(Xg, Xo)
     print(precision, "fan-beam max rel err", err.max(), F.last_info)
     assert err.max() <= tol
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("tf32", 1e-6)])
+def test_joseph_solve_matches_oracle(oracle_mod, precision, tol):
+    """The whole path on a Joseph-projector system (24x24, 40 views x 36
+    bins, sqrt(lambda) = 0.05)."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    ns, nv, nb, sl = 24, 40, 36, 0.05
+    g = O.Geometry(ns, nv, nb, sqrt_lambda=sl, projector="joseph")
+    csr = O.siddon_csr(g)
+    X = synth.phantom_batch(ns, 3, 8, 1234)
+    B = synth.poisson_sinogram(O.forward(csr, X), ns, 1e4, seed=1234)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    storage = "fp64" if precision == "fp64" else "fp32"
+    sysg = ct.System(ct.make_geometry(ns, nv, nb, sl, projector="joseph"), storage)
+    F = sysg.factor(precision)
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    Xg = F.solve(Bt, max_iter=20, tol=1e-10, allow_noconv=True).cpu().numpy().T
+    err = rel_err_cols(Xg, Xo)
+    print(precision, "joseph max rel err", err.max(), F.last_info)
+    assert err.max() <= tol
