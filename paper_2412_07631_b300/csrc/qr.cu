@@ -105,54 +105,87 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
 // (In core: all blocks, col_end = n.  Out of core: the blocks of one
 // superpanel, whose columns [c0, col_end) are resident; VR is then offset so
 // that global column indices address the superpanel buffer.)
+// T of a block reflector of width wblk from its panels' T_p (already on the
+// diagonal of T, ld NB) and its Gram matrix G = V^T V (ld NB): for the panel
+// at offset o,  T[0:o, o:o+wp] = -T[0:o, 0:o] * G[0:o, o:o+wp] * T_p,  the
+// off-diagonal block of the product of two block reflectors.
+static ct_status assemble_t(ct_factor f, int64_t wblk, const void *G, void *T, void *Y, cudaStream_t s) {
+    const size_t es = f->es();
+    const int64_t NB = f->NB, nb = f->nb;
+    const GemmKind small_kind = f->fp64 ? GEMM_F64 : GEMM_F32;
+    for (int64_t o = nb; o < wblk; o += nb) {
+        const int64_t wp = std::min<int64_t>(nb, wblk - o);
+        if (!f->fp64 && (size_t)o * 33 * sizeof(float) <= 200 * 1024) {
+            CT_TRY(t_assemble(o, (int)wp, (const float *)G, NB, (float *)T, NB, s));
+            continue;
+        }
+        const void *Tp = at(T, o, o, NB, es);
+        GemmArgs g1{small_kind, false, false, o, wp, wp, 1.0, at(const_cast<void *>(G), 0, o, NB, es), NB,
+                    Tp, NB, 0.0, Y, NB};
+        CT_TRY(gemm(g1, f->gemm_ws, s));
+        GemmArgs g2{small_kind, false, false, o, wp, o, -1.0, T, NB, Y, NB, 0.0, at(T, 0, o, NB, es), NB};
+        CT_TRY(gemm(g2, f->gemm_ws, s));
+    }
+    return CT_OK;
+}
+
+// Factor outer blocks [J0, J1) of VR; trailing updates reach column col_end.
+// (In core: all blocks, col_end = n.  Out of core: the blocks of one
+// superpanel, whose columns [c0, col_end) are resident; VR is then offset so
+// that global column indices address the superpanel buffer.)
+//
+// Three levels for the tensor-core paths: panels of nb = 32 update only the
+// rest of their mid block of MB = 256 columns; a finished mid block updates
+// the rest of its outer block with one rank-256 product (its T from its own
+// Gram matrix); a finished outer block updates the trailing matrix.  The
+// rank-32 updates then sweep at most 224 columns instead of the whole block.
 ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, cudaStream_t s) {
     const size_t es = f->es();
     const int64_t NB = f->NB, nb = f->nb, n = col_end, lda = f->lda;
+    const int64_t MB = (!f->fp64 && NB >= 512) ? 256 : NB;
     CT_TRY(f->G.ensure(es * (size_t)NB * NB));
-    // misc: Vt_p (ld NB) for inner panels | Y (ld NB) for the T assembly
-    CT_TRY(f->misc.ensure(2 * es * (size_t)NB * NB));
+    // misc (each NB x NB, ld NB): Vt_p of a panel | Y for the T assembly | Vt_q, G_q of a mid block
+    CT_TRY(f->misc.ensure(4 * es * (size_t)NB * NB));
     void *Vtp = f->misc.ptr;
     void *Y = (char *)f->misc.ptr + es * (size_t)NB * NB;
-    const GemmKind small_kind = f->fp64 ? GEMM_F64 : GEMM_F32;
+    void *Vtq = (char *)f->misc.ptr + 2 * es * (size_t)NB * NB;
+    void *Gq = (char *)f->misc.ptr + 3 * es * (size_t)NB * NB;
     for (int64_t J = J0; J < J1; ++J) {
         const int64_t j = J * NB;
         const int w = (int)std::min<int64_t>(NB, f->n - j);
         void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
         void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
         CT_CUDA(cudaMemsetAsync(TJ, 0, es * (size_t)NB * NB, s));
-        for (int64_t p = j; p < j + w; p += nb) {
-            const int wp = (int)std::min<int64_t>(nb, j + w - p);
-            CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s));
-            // T_p of this panel goes straight into its diagonal block of T_J.
-            void *Tp = at(TJ, p - j, p - j, NB, es);
-            CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
-            CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
-            CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
-            const int64_t ncols_in = j + w - (p + wp);
-            if (ncols_in > 0)
-                CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,
-                                   ncols_in, s, f->upd_kind, nullptr, 0));
+        for (int64_t q = j; q < j + w; q += MB) {
+            const int wq = (int)std::min<int64_t>(MB, j + w - q);
+            for (int64_t p = q; p < q + wq; p += nb) {
+                const int wp = (int)std::min<int64_t>(nb, q + wq - p);
+                CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s));
+                // T_p of this panel goes straight into its diagonal block of T_J.
+                void *Tp = at(TJ, p - j, p - j, NB, es);
+                CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
+                CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
+                CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
+                const int64_t ncols_in = q + wq - (p + wp);
+                if (ncols_in > 0)
+                    CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,
+                                       ncols_in, s, f->upd_kind, nullptr, 0));
+            }
+            const int64_t ncols_mid = j + w - (q + wq);
+            if (wq < w && ncols_mid > 0) {
+                // the mid block's reflector on the rest of the outer block
+                void *Tq = at(TJ, q - j, q - j, NB, es);
+                CT_TRY(extract_vtop(f->fp64, f->VR, lda, q, wq, Vtq, NB, s));
+                CT_TRY(gram(f, q, wq, Vtq, Gq, s));
+                CT_TRY(assemble_t(f, wq, Gq, Tq, Y, s));
+                CT_TRY(apply_block(f, q, wq, Vtq, Tq, true, at(f->VR, q, q + wq, lda, es), lda, ncols_mid,
+                                   s, f->upd_kind, nullptr, 0));
+            }
         }
         CT_TRY(extract_vtop(f->fp64, f->VR, lda, j, w, VtJ, NB, s));
         if (w > nb) {
-            // T_J from the panels' T_p:  for the next panel at offset o,
-            //   T_J[0:o, o:o+wp] = -T_J[0:o, 0:o] * (V_J[:, 0:o]^T V_p) * T_p,
-            // the off-diagonal block of the product of two block reflectors.
             CT_TRY(gram(f, j, w, VtJ, f->G.ptr, s));
-            for (int64_t o = nb; o < w; o += nb) {
-                const int64_t wp = std::min<int64_t>(nb, w - o);
-                if (!f->fp64 && (size_t)o * 33 * sizeof(float) <= 200 * 1024) {
-                    CT_TRY(t_assemble(o, (int)wp, (const float *)f->G.ptr, NB, (float *)TJ, NB, s));
-                    continue;
-                }
-                const void *Tp = at(TJ, o, o, NB, es);
-                GemmArgs g1{small_kind, false, false, o, wp, wp, 1.0, at(f->G.ptr, 0, o, NB, es), NB,
-                            Tp, NB, 0.0, Y, NB};
-                CT_TRY(gemm(g1, f->gemm_ws, s));
-                GemmArgs g2{small_kind, false, false, o, wp, o, -1.0, TJ, NB, Y, NB, 0.0,
-                            at(TJ, 0, o, NB, es), NB};
-                CT_TRY(gemm(g2, f->gemm_ws, s));
-            }
+            CT_TRY(assemble_t(f, w, f->G.ptr, TJ, Y, s));
         }
         if (j + w < n)
             CT_TRY(apply_block(f, j, w, VtJ, TJ, true, at(f->VR, j, j + w, lda, es), lda, n - j - w, s,
