@@ -15,7 +15,7 @@ import json
 import os
 import time
 
-DEFAULT_CANDIDATES = (512, 768, 1024)
+DEFAULT_CANDIDATES = (768, 1024, 1280)
 
 
 def cache_path() -> str:
