@@ -175,6 +175,8 @@ def make_inputs(ct, torch, name, rank=0):
 
 NB_OUTER = 0  # 0: the library's default outer block width
 OOC_BUDGET = 0  # > 0: out-of-core path with this device budget (bytes)
+DISK_PATH = ""  # out of core with A~ in this file (disk tier) instead of pinned host memory
+HOST_CACHE = 0  # pinned block cache of the disk tier (bytes)
 
 
 def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=None):
@@ -182,7 +184,12 @@ def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=No
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
     storage = "fp64" if precision == "fp64" else "fp32"
-    if OOC_BUDGET > 0:  # out of core: host-resident A~, bounded device working set
+    if OOC_BUDGET > 0 and DISK_PATH:  # out of core, disk tier: A~ in a file + block cache
+        sysg = ct.System(geom, storage, disk_path=DISK_PATH, host_cache=HOST_CACHE,
+                         block_cols=NB_OUTER)
+        ev[1].record()
+        F = sysg.factor_ooc(precision, device_budget=OOC_BUDGET)
+    elif OOC_BUDGET > 0:  # out of core: host-resident A~, bounded device working set
         sysg = ct.System(geom, storage, host_budget=OOC_BUDGET)
         ev[1].record()
         F = sysg.factor_ooc(precision, device_budget=OOC_BUDGET, nb_outer=NB_OUTER)
@@ -288,15 +295,25 @@ def main():
     ap.add_argument("--nb-outer", type=int, default=0, help="outer WY block width (0: default)")
     ap.add_argument("--ooc-budget-gb", type=float, default=0.0,
                     help="run the out-of-core path: A~ in pinned host memory, this many GB of device working set")
+    ap.add_argument("--disk", type=str, default="",
+                    help="with --ooc-budget-gb: keep A~ in a file in this directory (disk tier)")
+    ap.add_argument("--host-cache-gb", type=float, default=8.0,
+                    help="pinned block cache of the disk tier")
     ap.add_argument("--gemm", type=str, default="",
                     help="time only the GEMM engine on one shape, 'KIND:TA TB:M,N,K' (e.g. "
                          "'tf32:TN:768,16384,32768'), beta = 1; for kernel profiling")
     args = ap.parse_args()
     if args.gemm:
         return gemm_only(args)
-    global NB_OUTER, OOC_BUDGET
+    global NB_OUTER, OOC_BUDGET, DISK_PATH, HOST_CACHE
     NB_OUTER = args.nb_outer
     OOC_BUDGET = int(args.ooc_budget_gb * (1 << 30))
+    HOST_CACHE = int(args.host_cache_gb * (1 << 30))
+    if args.disk:
+        if not OOC_BUDGET:
+            ap.error("--disk needs --ooc-budget-gb")
+        os.makedirs(args.disk, exist_ok=True)
+        DISK_PATH = os.path.join(args.disk, "ctqr_rank%s.ctqrd" % os.environ.get("RANK", "0"))
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -357,6 +374,7 @@ def main():
     barrier()
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ct.disk_stats(reset=True)
     e0.record()
     torch.cuda.nvtx.range_push("timed_step")  # lets ncu select the timed launches
     phases, infos = [], []
@@ -369,6 +387,13 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = ct.stats_read()["launches"]
+    disk_io = None
+    if DISK_PATH:
+        io = ct.disk_stats()
+        disk_io = {k: v / args.steps for k, v in io.items()}
+        disk_io["read_gbs"] = io["bytes_read"] / io["read_s"] / 1e9 if io["read_s"] else None
+        disk_io["write_gbs"] = io["bytes_written"] / io["write_s"] / 1e9 if io["write_s"] else None
+        disk_io["note"] = "per timed step; read_s and write_s sum the busy time of the I/O threads"
     ms = e0.elapsed_time(e1) / args.steps
     from paper_2412_07631_b300 import replicas
     ms = replicas.max_over_ranks(ms, dist, device="cuda")
@@ -471,7 +496,10 @@ def main():
                        "bins": nb, "rows": M, "unknowns": n, "slices": k,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "out_of_core": ({"device_budget_gb": args.ooc_budget_gb,
-                                        "host_matrix": "pinned host memory"} if OOC_BUDGET else None),
+                                        "host_matrix": (("file on local disk + %.0f GB pinned block cache"
+                                                         % args.host_cache_gb) if DISK_PATH
+                                                        else "pinned host memory")}
+                                       if OOC_BUDGET else None),
                        "l2": "inputs larger than L2 (dense A~ of %.1f GB rebuilt every step)"
                              % (M * n * 4 / 1e9)},
             "qr_tflops": qr_fl / (qr_ms * 1e-3) / 1e12,
@@ -488,6 +516,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "fp64_vs_mixed": cmp,
+            "disk_io": disk_io,
         }
         print(json.dumps(line))
     if dist:

@@ -61,7 +61,9 @@ typedef enum {
     CT_ERR_NONFINITE = 7,   /* NaN/Inf met in the input or in a reflector */
     CT_ERR_HOSTMEM = 8,     /* host memory (pinned/registered) could not be obtained */
     CT_ERR_STATE = 9,       /* handle in the wrong state (e.g. system already consumed) */
-    CT_ERR_UNSUPPORTED = 10 /* option not available in this build */
+    CT_ERR_UNSUPPORTED = 10, /* option not available in this build */
+    CT_ERR_IO = 11,         /* a file read, write or sync failed (disk tier) */
+    CT_ERR_INTERRUPTED = 12 /* stopped early on request (ct_opts.stop_after); resumable */
 } ct_status;
 
 /* Arithmetic of the factorisation and the solve.
@@ -120,6 +122,8 @@ typedef struct {
     int32_t nb_outer;        /* outer WY block width (0: automatic) */
     int32_t nb_inner;        /* panel width (0: automatic) */
     int32_t flags;           /* CT_OPT_* bits */
+    int32_t stop_after;      /* disk-tier factorisation: return CT_ERR_INTERRUPTED after this
+                                many superpanels (0: run to the end); the file stays resumable */
 } ct_opts;
 
 /* ct_opts.flags: by default the repeated parts of a solve (the Q^T sweep plus
@@ -265,11 +269,69 @@ CT_API ct_status ct_build_system_host(const ct_geometry *geom, ct_precision stor
  * ct_solve, whose Q^T sweep then streams V from host memory.  The factor
  * works with ct_solve, ct_solve_host, ct_solve_adjoint, ct_factor_export and
  * ct_factor_save; ct_factor_device_ptrs returns CT_ERR_UNSUPPORTED.
+ * Disk-backed systems (ct_build_system_disk) go through the same steps with
+ * the file in place of host memory (see the disk tier below); their factor
+ * is its own checkpoint, so ct_factor_save returns CT_ERR_UNSUPPORTED.
  * Errors: CT_ERR_ARG (no host matrix, budget below 2 staging buffers plus
- * one outer block of columns), CT_ERR_OOM, CT_ERR_RANK (factor returned),
+ * one outer block of columns, disk file partly factored with another
+ * precision or panel width), CT_ERR_OOM, CT_ERR_RANK (factor returned),
+ * CT_ERR_INTERRUPTED (stop_after reached; no factor), CT_ERR_IO,
  * CT_ERR_TIMEOUT, CT_ERR_CUDA. */
 CT_API ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t device_budget,
                                   void *stream, ct_factor *out);
+
+/* ---- Disk tier (Sec. 2.2: the matrices live in secondary storage, part of
+ * the main memory caches their blocks, and disk transfers overlap the GPU's
+ * work) ----------------------------------------------------------------------
+ *
+ * A disk-backed system keeps A~ in one file of column blocks of block_cols
+ * columns (rows [0, row_end) of each block only: the rows below are zero in
+ * the structured lambda block), with a pinned host cache of
+ * host_cache_bytes (at least three blocks) and background I/O threads.
+ * ct_qr_factor_ooc factors it left-looking like a host-resident system, with
+ * the outer block equal to block_cols; blocks move file -> cache -> device
+ * and back, the next blocks are read ahead while the device works, and V
+ * and R replace A~ in the file as superpanels finish.  The file records its
+ * progress after every superpanel: a factorisation that stops (stop_after,
+ * or a process that dies) resumes from the last finished superpanel when
+ * ct_qr_factor_ooc is called again on the same or a reopened system (the
+ * columns of the superpanel that was being written are rebuilt from the
+ * sparse rows first), and a fully factored file yields its factor without
+ * recomputation.  The factor takes over the file (ct_factor_free closes it;
+ * the file stays on disk, the caller deletes it).  Its solves stream V from
+ * the file through the cache; they run without CUDA graphs.
+ *
+ * Build the system and write A~ to `path` (created or truncated); the sparse
+ * rows stay on the device.  block_cols: 0 = 1024 (FP32 storage) or 32 (FP64),
+ * otherwise a positive multiple of 32.  The stored values equal the in-core
+ * build's bit for bit.  Synchronous (returns when A~ is on disk).
+ * Errors: as ct_build_system; CT_ERR_ARG (bad path or block_cols),
+ * CT_ERR_HOSTMEM (cache cannot be pinned), CT_ERR_IO. */
+CT_API ct_status ct_build_system_disk(const ct_geometry *geom, ct_precision storage,
+                                      const char *path, int32_t block_cols,
+                                      size_t host_cache_bytes, void *stream, ct_system *out);
+
+/* Reopen a file written by ct_build_system_disk (any state: assembled,
+ * partly or fully factored): header checked (magic, version, checksum), the
+ * sparse rows rebuilt on the device from the stored geometry.
+ * Errors: CT_ERR_ARG (missing or foreign file, checksum mismatch),
+ * CT_ERR_HOSTMEM, CT_ERR_OOM, CT_ERR_CUDA. */
+CT_API ct_status ct_system_open_disk(const char *path, size_t host_cache_bytes, void *stream,
+                                     ct_system *out);
+
+/* State of a disk-backed system's file: *state 0 = A~ assembled, 1 =
+ * factorisation in progress, 2 = factored; *done_cols = columns whose
+ * factors are final on disk.  CT_ERR_STATE if the system has no file (or a
+ * factor has taken it over). */
+CT_API ct_status ct_disk_progress(ct_system sys, int32_t *state, int64_t *done_cols);
+
+/* Process-wide disk-tier counters since the last reset: bytes read and
+ * written, cache hits (block resident), prefetched (read already in flight),
+ * misses (read on demand), and the summed seconds of the I/O threads' reads
+ * and writes.  reset != 0 zeroes them after reading.  Any pointer may be NULL. */
+CT_API ct_status ct_disk_stats(int32_t reset, int64_t *bytes_read, int64_t *bytes_written,
+                               int64_t *hits, int64_t *prefetched, int64_t *misses,
+                               double *read_s, double *write_s);
 
 /* Pinned host blocks of freed out-of-core systems and factors are kept (at
  * most two) for reuse by the next ct_build_system_host, since pinning tens

@@ -31,7 +31,7 @@ class Geometry(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("refine_max_iter", C.c_int32),
                 ("refine_tol", C.c_double), ("nb_outer", C.c_int32), ("nb_inner", C.c_int32),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("stop_after", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -56,7 +56,8 @@ SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info"
            "ct_factor_device_ptrs", "ct_factor_export", "ct_solve", "ct_solve_host",
            "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm", "ct_stats_reset",
            "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc", "ct_factor_save",
-           "ct_factor_load", "ct_build_system_host", "ct_qr_factor_ooc", "ct_host_cache_release"]
+           "ct_factor_load", "ct_build_system_host", "ct_qr_factor_ooc", "ct_host_cache_release",
+           "ct_build_system_disk", "ct_system_open_disk", "ct_disk_progress", "ct_disk_stats"]
 
 
 def lib_path() -> str:
@@ -143,17 +144,30 @@ def make_geometry(n_side, n_views, n_bins, sqrt_lambda=0.0, pixel_width=1.0, bin
                     GEOMETRY_KINDS[kind], source_dist, fan_deg, PROJECTORS[projector])
 
 
+INTERRUPTED = 12  # ct_status CT_ERR_INTERRUPTED
+
+
 class System:
     """Device-resident system matrix A~ = [A; sqrt(lambda) I] (dense, column
     major) plus the FP64 CSR/CSC of A, built by the Siddon kernels."""
 
-    def __init__(self, geom: Geometry, storage: str = "fp32", stream=None, host_budget: int = 0):
+    def __init__(self, geom: Geometry, storage: str = "fp32", stream=None, host_budget: int = 0,
+                 disk_path: str | None = None, host_cache: int = 1 << 30, block_cols: int = 0,
+                 _handle=None):
         """host_budget > 0: keep the dense matrix in pinned host memory (built in
-        column slabs of at most host_budget device bytes) for factor_ooc."""
+        column slabs of at most host_budget device bytes) for factor_ooc.
+        disk_path: keep it in that file instead (column blocks of block_cols
+        columns, host_cache bytes of pinned block cache) for factor_ooc."""
         self.geom = geom
         self.storage = storage
         h = C.c_void_p()
-        if host_budget > 0:
+        if _handle is not None:
+            h = _handle
+        elif disk_path is not None:
+            _check(lib().ct_build_system_disk(C.byref(geom), PRECISIONS[storage], disk_path.encode(),
+                                              int(block_cols), C.c_size_t(int(host_cache)),
+                                              _stream(stream), C.byref(h)))
+        elif host_budget > 0:
             _check(lib().ct_build_system_host(C.byref(geom), PRECISIONS[storage], int(host_budget),
                                               _stream(stream), C.byref(h)))
         else:
@@ -162,6 +176,27 @@ class System:
         vals = [C.c_int64() for _ in range(5)]
         _check(lib().ct_system_info(h, *[C.byref(v) for v in vals]))
         self.m, self.n, self.rows, self.lda, self.nnz = (v.value for v in vals)
+
+    @classmethod
+    def open_disk(cls, path: str, host_cache: int = 1 << 30, stream=None) -> "System":
+        """Reopen a disk-backed system's file (assembled, partly or fully factored)."""
+        import struct
+        h = C.c_void_p()
+        _check(lib().ct_system_open_disk(path.encode(), C.c_size_t(int(host_cache)), _stream(stream),
+                                         C.byref(h)))
+        # file header: magic[8], version u32, element size u32, then the geometry
+        with open(path, "rb") as fh:
+            head = fh.read(16 + C.sizeof(Geometry))
+        es = struct.unpack_from("<I", head, 12)[0]
+        geom = Geometry.from_buffer_copy(head, 16)
+        return cls(geom, "fp64" if es == 8 else "fp32", _handle=h)
+
+    def disk_progress(self) -> tuple[int, int]:
+        """(state, done_cols) of a disk-backed system's file: state 0 assembled,
+        1 factorisation in progress, 2 factored."""
+        st, done = C.c_int32(), C.c_int64()
+        _check(lib().ct_disk_progress(self.h, C.byref(st), C.byref(done)))
+        return st.value, done.value
 
     def export_csr(self):
         import numpy as np
@@ -202,13 +237,20 @@ class System:
         return Factor(h, self, precision)
 
     def factor_ooc(self, precision: str | None = None, device_budget: int = 16 << 30,
-                   nb_outer: int = 0, nb_inner: int = 0, stream=None) -> "Factor":
-        """Out-of-core QR of a host-resident system (see ct_qr_factor_ooc)."""
+                   nb_outer: int = 0, nb_inner: int = 0, stream=None,
+                   stop_after: int = 0) -> "Factor | None":
+        """Out-of-core QR of a host- or disk-resident system (see
+        ct_qr_factor_ooc).  stop_after > 0 (disk): stop after that many
+        superpanels and return None; calling again resumes."""
         if precision is None:
             precision = "fp64" if self.storage == "fp64" else "tf32"
-        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0)
+        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0, int(stop_after))
         h = C.c_void_p()
-        _check(lib().ct_qr_factor_ooc(self.h, C.byref(o), int(device_budget), _stream(stream), C.byref(h)))
+        st = lib().ct_qr_factor_ooc(self.h, C.byref(o), C.c_size_t(int(device_budget)), _stream(stream),
+                                    C.byref(h))
+        if st == INTERRUPTED:
+            return None
+        _check(st)
         return Factor(h, self, precision)
 
     def free(self):
@@ -364,6 +406,17 @@ STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "sidd
                 "spmm_fp32"]
 
 
+def disk_stats(reset: bool = False) -> dict:
+    """Disk-tier I/O counters (bytes, cache hits/prefetched/misses, I/O seconds)."""
+    v = [C.c_int64() for _ in range(5)]
+    t = [C.c_double() for _ in range(2)]
+    _check(lib().ct_disk_stats(1 if reset else 0, *[C.byref(x) for x in v], *[C.byref(x) for x in t]))
+    keys = ["bytes_read", "bytes_written", "hits", "prefetched", "misses"]
+    out = {k: x.value for k, x in zip(keys, v)}
+    out["read_s"], out["write_s"] = t[0].value, t[1].value
+    return out
+
+
 def stats_reset(timing: bool = False):
     """Zero the library's launch counter (and per-class event timing if asked)."""
     _check(lib().ct_stats_reset(1 if timing else 0))
@@ -389,5 +442,5 @@ def stats_read() -> dict:
     return out
 
 
-__all__ = ["CTSolve", "stats_reset", "stats_read", "stats_dump", "STAT_CLASSES", "Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
+__all__ = ["CTSolve", "disk_stats", "stats_reset", "stats_read", "stats_dump", "STAT_CLASSES", "Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
            "lib_path", "make_geometry", "PRECISIONS", "SYMBOLS"]

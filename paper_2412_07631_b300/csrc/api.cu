@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "diskstore.cuh"
 #include "handles.cuh"
 
 namespace ctqr {
@@ -94,7 +95,9 @@ bool timing_enabled() { return g_timing.load(std::memory_order_relaxed); }
 
 // Graphs are used unless the caller turned them off or per-launch timing is on
 // (timed launches must run one by one to be measured).
-bool graphs_allowed(ct_factor f) { return f->graphs_enabled && !timing_enabled(); }
+// Disk-backed factors read blocks on the host during the Q sweep, so they
+// always run eagerly.
+bool graphs_allowed(ct_factor f) { return f->graphs_enabled && !timing_enabled() && !f->store; }
 
 uint64_t graph_key(ct_factor f, int64_t k, const void *extra) {
     uint64_t h = 1469598103934665603ull;
@@ -175,6 +178,7 @@ namespace {
 void free_system_storage(ct_system s) {
     cudaFree(s->dense);
     if (s->host_dense) pinned_release(s->host_dense, s->host_bytes);
+    delete s->store;
     cudaFree(s->d_cs);
     cudaFree(s->row_nnz);
     cudaFree(s->row_ptr);
@@ -222,6 +226,8 @@ const char *ct_status_str(ct_status s) {
         case CT_ERR_HOSTMEM: return "CT_ERR_HOSTMEM";
         case CT_ERR_STATE: return "CT_ERR_STATE";
         case CT_ERR_UNSUPPORTED: return "CT_ERR_UNSUPPORTED";
+        case CT_ERR_IO: return "CT_ERR_IO";
+        case CT_ERR_INTERRUPTED: return "CT_ERR_INTERRUPTED";
     }
     return "CT_ERR_UNKNOWN";
 }
@@ -429,15 +435,21 @@ ct_status ct_system_export(ct_system sys, int64_t *row_ptr, int32_t *col_idx, do
                            void *dense, int64_t ldd) {
     if (!sys) return CT_ERR_ARG;
     const void *dsrc = sys->dense ? sys->dense : sys->host_dense;
-    if (dense && !dsrc) return CT_ERR_STATE;
+    if (dense && !dsrc && sys->store) {  // disk: only while the file still holds A~
+        if (sys->store->header().state != DISK_ASSEMBLED) return CT_ERR_STATE;
+    } else if (dense && !dsrc) {
+        return CT_ERR_STATE;
+    }
     if (dense && ldd < sys->rows) return CT_ERR_ARG;
     if (row_ptr) CT_CUDA(cudaMemcpy(row_ptr, sys->row_ptr, sizeof(int64_t) * (sys->m + 1), cudaMemcpyDeviceToHost));
     if (col_idx && sys->nnz) CT_CUDA(cudaMemcpy(col_idx, sys->col, sizeof(int32_t) * sys->nnz, cudaMemcpyDeviceToHost));
     if (val && sys->nnz) CT_CUDA(cudaMemcpy(val, sys->val, sizeof(double) * sys->nnz, cudaMemcpyDeviceToHost));
-    if (dense) {
+    if (dense && dsrc) {
         const size_t es = sys->fp64 ? 8 : 4;
         CT_CUDA(cudaMemcpy2D(dense, es * ldd, dsrc, es * sys->lda, es * sys->rows, sys->n,
                              cudaMemcpyDefault));
+    } else if (dense) {
+        CT_TRY(disk_export(sys->store, sys->rows, dense, ldd));
     }
     return CT_OK;
 }
@@ -447,8 +459,12 @@ ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau) {
     const size_t es = f->es();
     if (VR) {
         if (ldv < f->M) return CT_ERR_ARG;
-        CT_CUDA(cudaMemcpy2D(VR, es * ldv, f->ooc ? f->VR_host : f->VR, es * f->lda, es * f->M, f->n,
-                             cudaMemcpyDefault));
+        if (f->store) {
+            CT_TRY(disk_export(f->store, f->M, VR, ldv));
+        } else {
+            CT_CUDA(cudaMemcpy2D(VR, es * ldv, f->ooc ? f->VR_host : f->VR, es * f->lda, es * f->M, f->n,
+                                 cudaMemcpyDefault));
+        }
     }
     if (tau) CT_CUDA(cudaMemcpy(tau, f->tau, es * f->n, cudaMemcpyDeviceToHost));
     return CT_OK;
@@ -491,6 +507,7 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     }
     if (!sys->dense) {
         set_error(sys->host_dense ? "the dense matrix is in host memory: use ct_qr_factor_ooc"
+                  : sys->store    ? "the dense matrix is on disk: use ct_qr_factor_ooc"
                                   : "the system's dense storage was already consumed by a factor");
         return CT_ERR_ARG;
     }
@@ -640,6 +657,7 @@ void ct_factor_free(ct_factor f) {
         cudaFree(f->Rm);
         cudaFree(f->stage);
         if (f->VR_host) pinned_release(f->VR_host, f->host_bytes);
+        delete f->store;
     }
     cudaFree(f->RinvB);
     cudaFree(f->RinvTB);

@@ -75,6 +75,11 @@ using namespace ctqr;
 
 extern "C" ct_status ct_factor_save(ct_factor f, const char *path) {
     if (!f || !path || !f->sys) return CT_ERR_ARG;
+    if (f->store) {
+        set_error("a disk-resident factor is its own checkpoint: reopen its file with "
+                  "ct_system_open_disk and call ct_qr_factor_ooc");
+        return CT_ERR_UNSUPPORTED;
+    }
     FILE *fp = fopen(path, "wb");
     if (!fp) {
         set_error("cannot open %s for writing", path);

@@ -5,6 +5,10 @@
 
 #include "kernels.cuh"
 
+namespace ctqr {
+class DiskStore;
+}
+
 struct ct_system_s {
     ct_geometry geom{};
     bool fp64 = false;  // dense storage element type
@@ -12,6 +16,7 @@ struct ct_system_s {
     void *dense = nullptr;  // column-major rows x n (NULL once consumed by a factor)
     void *host_dense = nullptr;  // out-of-core systems: the same matrix in pinned host memory
     size_t host_bytes = 0;       // size of that pinned block
+    ctqr::DiskStore *store = nullptr;  // disk-backed systems: the file of A~ (owned)
     double *d_cs = nullptr;
     int32_t *row_nnz = nullptr;
     int64_t *row_ptr = nullptr;
@@ -61,6 +66,7 @@ struct ct_factor_s {
     bool ooc = false;
     void *VR_host = nullptr;
     size_t host_bytes = 0;
+    ctqr::DiskStore *store = nullptr;  // disk-backed factors: V and R in the file (owned)
     void *stage = nullptr;
     size_t stage_bytes = 0;
     // triangular-solve aids (built on first solve): inverse diagonal blocks of R

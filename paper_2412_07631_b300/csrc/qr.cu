@@ -17,6 +17,7 @@
 // zeros, and on average a fifth of the rows drop out at 256x256.
 #include <algorithm>
 
+#include "diskstore.cuh"
 #include "handles.cuh"
 
 namespace ctqr {
@@ -205,6 +206,17 @@ ct_status stage_v_block(ct_factor f, int64_t J, void *dst, int64_t *ldd, cudaStr
     const int64_t kb = f->row_end(j + w) - j - w;
     *ldd = round_up(std::max<int64_t>(kb, 1), 32);
     if (kb <= 0) return CT_OK;
+    if (f->store) {  // disk tier: block J from the cache (read on demand if missing)
+        DiskStore *d = f->store;
+        int slot = -1;
+        CT_TRY(d->acquire(J, s, &slot));
+        const int64_t rb = d->block_rows(J);  // = row_end(j + w)
+        const cudaError_t e = cudaMemcpy2DAsync(dst, es * (size_t)*ldd, (const char *)d->slot_ptr(slot) + es * (size_t)(j + w),
+                                                es * (size_t)rb, es * (size_t)kb, w, cudaMemcpyHostToDevice, s);
+        CT_TRY(d->release(slot, s));
+        CT_CUDA(e);
+        return CT_OK;
+    }
     CT_CUDA(cudaMemcpy2DAsync(dst, es * (size_t)*ldd, (const char *)f->VR_host + es * (size_t)(j + w + j * f->lda),
                               es * (size_t)f->lda, es * (size_t)kb, w, cudaMemcpyHostToDevice, s));
     return CT_OK;
@@ -220,7 +232,12 @@ ct_status apply_q_blocks(ct_factor f, bool transpose, void *C, int64_t ldc, int6
         const int w = (int)std::min<int64_t>(NB, f->n - j);
         const void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;
         const void *TJ = (char *)f->Tall + es * (size_t)J * NB * NB;
-        if (f->ooc) {  // stream the block's V from host memory
+        if (f->ooc) {  // stream the block's V from host memory or the file
+            if (f->store) {  // read the next blocks ahead while this one is applied
+                const int ahead = std::max(1, f->store->nslots() / 2 - 1);
+                for (int64_t q = 1; q <= ahead && t + q < f->nblocks; ++q)
+                    f->store->prefetch(transpose ? t + q : f->nblocks - 1 - t - q);
+            }
             int64_t ldv = 0;
             CT_TRY(stage_v_block(f, J, f->stage, &ldv, s));
             CT_TRY(apply_block(f, j, w, VtJ, TJ, transpose, (char *)C + es * (size_t)j, ldc, k, s, f->kind,

@@ -45,3 +45,28 @@ def test_bad_arguments_are_rejected_without_touching_the_device():
     assert L.ct_build_system(ctypes.byref(g), 0, None, ctypes.byref(h)) == 1
     assert L.ct_solve(None, None, 0, 1, None, 0, None, None, None) == 1
     assert L.ct_gemm(7, b"N", b"N", 1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1, None) == 1
+
+
+def test_disk_tier_refuses_bad_files_and_blocks_without_a_gpu(tmp_path):
+    """The disk tier checks its file header and block width before any
+    device work: a missing file, a foreign file, a header whose checksum does
+    not match and a block width that is not a multiple of 32 are refused."""
+    import paper_2412_07631_b300 as ct
+    L = ct.lib()
+    h = ctypes.c_void_p()
+    assert L.ct_system_open_disk(str(tmp_path / "none").encode(), 0, None, ctypes.byref(h)) == 1
+    foreign = tmp_path / "foreign.bin"
+    foreign.write_bytes(bytes(range(256)) * 32)
+    assert L.ct_system_open_disk(str(foreign).encode(), 0, None, ctypes.byref(h)) == 1
+    # right magic and version, wrong checksum
+    bad = tmp_path / "bad.ctqrd"
+    bad.write_bytes(b"CTQRDSK1" + (1).to_bytes(4, "little") + (4).to_bytes(4, "little") + bytes(4080))
+    assert L.ct_system_open_disk(str(bad).encode(), 0, None, ctypes.byref(h)) == 1
+    assert b"checksum" in L.ct_last_error()
+    assert not h.value
+    g = ct.make_geometry(16, 30, 24, 0.05)
+    assert L.ct_build_system_disk(ctypes.byref(g), 1, str(tmp_path / "x").encode(), 33, 0, None,
+                                  ctypes.byref(h)) == 1
+    assert L.ct_build_system_disk(ctypes.byref(g), 1, None, 64, 0, None, ctypes.byref(h)) == 1
+    assert L.ct_status_str(11) == b"CT_ERR_IO"
+    assert L.ct_status_str(12) == b"CT_ERR_INTERRUPTED"
