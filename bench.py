@@ -285,7 +285,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32",
+                    choices=["tf32", "bf16", "tf32x3", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--max-iter", type=int, default=40)
     ap.add_argument("--tol", type=float, default=5e-7)
     ap.add_argument("--no-e2e", action="store_true")
@@ -409,7 +410,7 @@ def main():
     prof = ct.stats_read()
     ct.stats_reset(False)
     tc = prof["tc_gemm"]
-    if args.precision == "bf16":
+    if args.precision in ("bf16", "bf16x3"):
         # BF16 trailing updates and TF32 solve GEMMs share the class: the BF16
         # peak bounds both, so the fraction is a lower bound
         tc_peak = peaks["bf16_tflops_sustained"]
@@ -490,6 +491,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"tf32": "tf32 (FP32 storage) + f64 refinement",
                       "bf16": "bf16 trailing updates (FP32 storage, tf32 solve) + f64 refinement",
+                      "tf32x3": "tf32x3 split trailing updates (FP32 storage, tf32 solve) + f64 refinement",
+                      "bf16x3": "bf16x3 split trailing updates (FP32 storage, tf32 solve) + f64 refinement",
                       "fp32": "f32", "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload), "n_side": ns, "views": nv,

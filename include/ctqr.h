@@ -73,8 +73,23 @@ typedef enum {
  *  CT_TF32_REFINE FP32 storage, trailing updates and Q^T applications on the
  *                 tensor cores with TF32 operands and FP32 accumulation, then
  *                 FP64 iterative refinement (residual and update in FP64).
- *  CT_BF16_REFINE as CT_TF32_REFINE with BF16 operands. */
-typedef enum { CT_FP64 = 0, CT_FP32 = 1, CT_TF32_REFINE = 2, CT_BF16_REFINE = 3 } ct_precision;
+ *  CT_BF16_REFINE as CT_TF32_REFINE with BF16 operands.
+ *  CT_TF32X3_REFINE, CT_BF16X3_REFINE  split-precision trailing updates:
+ *                 each FP32 operand x is split into x_hi (the nearest TF32 or
+ *                 BF16 value) and x_lo (x - x_hi, rounded the same way), and
+ *                 A B is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi on the
+ *                 tensor cores (three times the flops of one product; close to
+ *                 FP32 accuracy for TF32x3, about 16 bits for BF16x3), which
+ *                 widens the range of conditioning the FP64 refinement
+ *                 converges on.  Everything else as CT_TF32_REFINE. */
+typedef enum {
+    CT_FP64 = 0,
+    CT_FP32 = 1,
+    CT_TF32_REFINE = 2,
+    CT_BF16_REFINE = 3,
+    CT_TF32X3_REFINE = 4,
+    CT_BF16X3_REFINE = 5
+} ct_precision;
 
 /* Parallel-beam scan geometry.  Pixels of width pixel_width tile the square
  * centred on the rotation axis; views at v*arc_deg/n_views degrees
@@ -385,8 +400,10 @@ CT_API ct_status ct_stats_dump(const char *path);
 
 /* GEMM engine behind the WY updates: C = alpha * op(A) * op(B) + beta * C,
  * column-major, op = 'N' or 'T'.  kind: 0 = FP64 (DFMA), 1 = FP32 (FFMA),
- * 2 = TF32 tensor cores (tcgen05, FP32 accumulate), 3 = BF16 tensor cores.
- * A, B, C are device pointers of double (kind 0) or float (kinds 1-3).
+ * 2 = TF32 tensor cores (tcgen05, FP32 accumulate), 3 = BF16 tensor cores,
+ * 4 = TF32x3 and 5 = BF16x3 split-precision products on the tensor cores
+ * (see ct_precision).  A, B, C are device pointers of double (kind 0) or
+ * float (kinds 1-5).
  * Errors: CT_ERR_ARG, CT_ERR_TIMEOUT, CT_ERR_CUDA. */
 CT_API ct_status ct_gemm(int32_t kind, char transa, char transb, int64_t M, int64_t N, int64_t K,
                   double alpha, const void *A, int64_t lda, const void *B, int64_t ldb,

@@ -17,8 +17,8 @@ import os
 
 from . import build as _build
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
-GEMM_KINDS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4, "bf16x3": 5}
+GEMM_KINDS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4, "bf16x3": 5}
 
 
 class Geometry(C.Structure):

@@ -200,7 +200,7 @@ ct_status dmalloc(T **p, size_t count) {
     return CT_OK;
 }
 
-bool is_refine(ct_precision p) { return p == CT_TF32_REFINE || p == CT_BF16_REFINE; }
+bool is_refine(ct_precision p) { return is_refine_prec(p); }
 
 }  // namespace
 
@@ -314,7 +314,7 @@ ct_status ctqr::build_system_impl(const ct_geometry *geom, ct_precision storage,
         set_error("too many rays");
         return CT_ERR_ARG;
     }
-    if (storage < CT_FP64 || storage > CT_BF16_REFINE) return CT_ERR_ARG;
+    if (storage < CT_FP64 || storage > CT_BF16X3_REFINE) return CT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     ct_system sys = new (std::nothrow) ct_system_s;
     if (!sys) return CT_ERR_HOSTMEM;
@@ -500,7 +500,7 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     ct_opts o{};
     o.precision = sys->fp64 ? CT_FP64 : CT_TF32_REFINE;
     if (opts) o = *opts;
-    if (o.precision < CT_FP64 || o.precision > CT_BF16_REFINE) return CT_ERR_ARG;
+    if (o.precision < CT_FP64 || o.precision > CT_BF16X3_REFINE) return CT_ERR_ARG;
     if ((o.precision == CT_FP64) != sys->fp64) {
         set_error("precision does not match the system's storage");
         return CT_ERR_ARG;
@@ -517,8 +517,8 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     f->sys = sys;
     f->prec = o.precision;
     f->fp64 = o.precision == CT_FP64;
-    f->kind = o.precision == CT_FP64 ? GEMM_F64 : (o.precision == CT_FP32 ? GEMM_F32 : GEMM_TF32);
-    f->upd_kind = o.precision == CT_BF16_REFINE ? GEMM_BF16 : f->kind;
+    f->kind = solve_kind(o.precision);
+    f->upd_kind = update_kind(o.precision);
     f->M = sys->rows;
     f->n = sys->n;
     f->m = sys->m;
@@ -671,7 +671,7 @@ void ct_factor_free(ct_factor f) {
 ct_status ct_gemm(int32_t kind, char transa, char transb, int64_t M, int64_t N, int64_t K,
                   double alpha, const void *A, int64_t lda, const void *B, int64_t ldb, double beta,
                   void *C, int64_t ldc, void *stream) {
-    if (kind < 0 || kind > 3) return CT_ERR_ARG;
+    if (kind < 0 || kind > 5) return CT_ERR_ARG;
     const bool ta = transa == 'T' || transa == 't';
     const bool tb = transb == 'T' || transb == 't';
     if ((!ta && transa != 'N' && transa != 'n') || (!tb && transb != 'N' && transb != 'n'))

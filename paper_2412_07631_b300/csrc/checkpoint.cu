@@ -147,7 +147,7 @@ extern "C" ct_status ct_factor_load(ct_system sys, const char *path, void *strea
     }
     const bool fp64 = hd.precision == CT_FP64;
     if (!same_geom(hd.geom, sys->geom) || fp64 != sys->fp64 || hd.M != sys->rows || hd.n != sys->n ||
-        hd.m != sys->m || hd.precision < CT_FP64 || hd.precision > CT_BF16_REFINE) {
+        hd.m != sys->m || hd.precision < CT_FP64 || hd.precision > CT_BF16X3_REFINE) {
         fclose(fp);
         set_error("checkpoint %s does not match this system's geometry/precision", path);
         return CT_ERR_ARG;
@@ -160,8 +160,8 @@ extern "C" ct_status ct_factor_load(ct_system sys, const char *path, void *strea
     f->sys = sys;
     f->prec = (ct_precision)hd.precision;
     f->fp64 = fp64;
-    f->kind = fp64 ? GEMM_F64 : (f->prec == CT_FP32 ? GEMM_F32 : GEMM_TF32);
-    f->upd_kind = f->prec == CT_BF16_REFINE ? GEMM_BF16 : f->kind;
+    f->kind = solve_kind(f->prec);
+    f->upd_kind = update_kind(f->prec);
     f->M = hd.M;
     f->n = hd.n;
     f->m = hd.m;

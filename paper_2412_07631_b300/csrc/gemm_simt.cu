@@ -173,37 +173,50 @@ static void plan_splits(int64_t tiles, int64_t K, int64_t min_chunk, int64_t ali
     *kchunk_out = kchunk;
 }
 
-// BF16 tensor-core product: both operands are rounded (to nearest even) into
-// K-major BF16 copies in `ws`, then multiplied with FP32 accumulation.  A
-// product whose B copy would exceed kBf16ChunkBytes is done in column slabs
-// of C, reusing the A copy.
-static ct_status gemm_bf16(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
-    constexpr size_t kBf16ChunkBytes = (size_t)4 << 30;
-    const int64_t ldt = round_up(g.K, 64);
-    const size_t abytes = (size_t)round_up(2 * ldt * g.M, 256);
+// Tensor-core products through K-major operand copies in `ws`:
+//   BF16: both operands rounded (to nearest even) to BF16;
+//   BF16X3 / TF32X3: both operands split into hi + lo of the narrow type and
+//     laid out as [hi, hi, lo] and [hi, lo, hi] along a K three times as
+//     deep, so one product sums A_hi B_hi + A_hi B_lo + A_lo B_hi;
+// then multiplied with FP32 accumulation.  A product whose B copy would
+// exceed kChunkBytes is done in column slabs of C, reusing the A copy.
+static ct_status gemm_copied(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
+    constexpr size_t kChunkBytes = (size_t)4 << 30;
+    const bool split = g.kind == GEMM_BF16X3 || g.kind == GEMM_TF32X3;
+    const bool b16 = g.kind == GEMM_BF16 || g.kind == GEMM_BF16X3;
+    const int64_t es = b16 ? 2 : 4;
+    const int64_t Kc = split ? 3 * g.K : g.K;  // depth of the product of the copies
+    const int64_t ldt = round_up(Kc, 64);
+    const size_t abytes = (size_t)round_up(es * ldt * g.M, 256);
     int64_t nslab = g.N;
-    if ((size_t)(2 * ldt) * (size_t)g.N > kBf16ChunkBytes)
-        nslab = std::max<int64_t>(256, (int64_t)(kBf16ChunkBytes / (size_t)(2 * ldt)) / 256 * 256);
-    const size_t bbytes = (size_t)round_up(2 * ldt * nslab, 256);
+    if ((size_t)(es * ldt) * (size_t)g.N > kChunkBytes)
+        nslab = std::max<int64_t>(256, (int64_t)(kChunkBytes / (size_t)(es * ldt)) / 256 * 256);
+    const size_t bbytes = (size_t)round_up(es * ldt * nslab, 256);
     const int64_t tiles = ceil_div(g.M, 128) * ceil_div(nslab, 256);
     int64_t splits, kchunk;
-    plan_splits(tiles, g.K, 2048, 64, &splits, &kchunk);
+    plan_splits(tiles, Kc, 2048, 64, &splits, &kchunk);
     // the last, narrower slab may split K further: size the partials for both
     const int64_t nlast = g.N - (g.N - 1) / nslab * nslab;
     int64_t sp_last, kc_last;
-    plan_splits(ceil_div(g.M, 128) * ceil_div(nlast, 256), g.K, 2048, 64, &sp_last, &kc_last);
+    plan_splits(ceil_div(g.M, 128) * ceil_div(nlast, 256), Kc, 2048, 64, &sp_last, &kc_last);
     const size_t pbytes = std::max(splits > 1 ? 4 * (size_t)(g.M * nslab * splits) : (size_t)0,
                                    sp_last > 1 ? 4 * (size_t)(g.M * nlast * sp_last) : (size_t)0);
     CT_TRY(ws.ensure(abytes + bbytes + pbytes));
     void *Ab = ws.ptr, *Bb = (char *)ws.ptr + abytes, *part = (char *)ws.ptr + abytes + bbytes;
-    if (g.ta) CT_TRY(copy_convert_2d(0, g.A, g.lda, 2, Ab, ldt, g.K, g.M, s));
+    const int split_kind = b16 ? 2 : 3;
+    if (split) CT_TRY(split3_copy((const float *)g.A, g.lda, g.ta, split_kind, false, Ab, ldt, g.K, g.M, s));
+    else if (g.ta) CT_TRY(copy_convert_2d(0, g.A, g.lda, 2, Ab, ldt, g.K, g.M, s));
     else CT_TRY(transpose_any(0, g.A, g.lda, 2, Ab, ldt, g.M, g.K, s));
     for (int64_t n0 = 0; n0 < g.N; n0 += nslab) {
         const int64_t nn = std::min(nslab, g.N - n0);
-        const size_t es = 4;
-        if (!g.tb) CT_TRY(copy_convert_2d(0, (const char *)g.B + es * (size_t)(n0 * g.ldb), g.ldb, 2, Bb, ldt, g.K, nn, s));
-        else CT_TRY(transpose_any(0, (const char *)g.B + es * (size_t)n0, g.ldb, 2, Bb, ldt, nn, g.K, s));
+        const size_t fs = 4;  // FP32 operands and C
+        const float *Bs = (const float *)((const char *)g.B + fs * (size_t)(g.tb ? n0 : n0 * g.ldb));
+        if (split) CT_TRY(split3_copy(Bs, g.ldb, !g.tb, split_kind, true, Bb, ldt, g.K, nn, s));
+        else if (!g.tb) CT_TRY(copy_convert_2d(0, Bs, g.ldb, 2, Bb, ldt, g.K, nn, s));
+        else CT_TRY(transpose_any(0, Bs, g.ldb, 2, Bb, ldt, nn, g.K, s));
         GemmArgs b = g;
+        b.kind = b16 ? GEMM_BF16 : GEMM_TF32;
+        b.K = Kc;
         b.ta = true;
         b.tb = false;
         b.A = Ab;
@@ -211,14 +224,14 @@ static ct_status gemm_bf16(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
         b.B = Bb;
         b.ldb = ldt;
         b.N = nn;
-        b.C = (char *)g.C + es * (size_t)(n0 * g.ldc);
+        b.C = (char *)g.C + fs * (size_t)(n0 * g.ldc);
         int64_t sp = splits, kc = kchunk;
         if (nn != nslab) {
             sp = sp_last;
             kc = kc_last;
         }
         if (sp <= 1) {
-            CT_TRY(gemm_tc_launch(b, 1, g.K, 0, s));
+            CT_TRY(gemm_tc_launch(b, 1, Kc, 0, s));
             continue;
         }
         GemmArgs p = b;
@@ -235,10 +248,11 @@ static ct_status gemm_bf16(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
 ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     if (g0.M < 0 || g0.N < 0 || g0.K < 0) return CT_ERR_ARG;
     if (g0.M == 0 || g0.N == 0) return CT_OK;
-    if (g0.kind == GEMM_BF16 && g0.K > 0) return gemm_bf16(g0, ws, s);
+    const bool copied = g0.kind == GEMM_BF16 || g0.kind == GEMM_BF16X3 || g0.kind == GEMM_TF32X3;
+    if (copied && g0.K > 0) return gemm_copied(g0, ws, s);
     GemmArgs g = g0;
     const bool fp64 = g.kind == GEMM_F64;
-    if (g.kind == GEMM_BF16) g.kind = GEMM_F32;  // only reached with K == 0
+    if (copied) g.kind = GEMM_F32;  // only reached with K == 0
     bool tc = g.kind == GEMM_TF32;
     if (tc && (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15) || (g.lda & 3) || (g.ldb & 3))) {
         // A TMA tile must start on a 16-byte boundary; ragged sub-blocks that

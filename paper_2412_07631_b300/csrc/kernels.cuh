@@ -28,7 +28,33 @@ ct_status build_csc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
                     double *csc_val, Scratch &tmp, Scratch &tmp2, cudaStream_t s);
 
 // ---- GEMM engines (gemm_simt.cu, gemm_tc.cu) ---------------------------------------
-enum GemmKind : int { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TF32 = 2, GEMM_BF16 = 3 };
+enum GemmKind : int { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TF32 = 2, GEMM_BF16 = 3, GEMM_TF32X3 = 4, GEMM_BF16X3 = 5 };
+// Precision helpers shared by the factor constructors.
+inline bool is_refine_prec(ct_precision p) { return p >= CT_TF32_REFINE && p <= CT_BF16X3_REFINE; }
+// GEMMs of the solve (Q^T sweeps, triangular solves) and of the Gram and T
+// blocks: TF32 for the single-pass refining precisions, TF32x3 for both
+// split ones (close to FP32, so the preconditioner of the inner FP32 solves
+// is as good as the split factor).
+inline GemmKind solve_kind(ct_precision p) {
+    switch (p) {
+        case CT_FP64: return GEMM_F64;
+        case CT_FP32: return GEMM_F32;
+        case CT_TF32X3_REFINE:
+        case CT_BF16X3_REFINE: return GEMM_TF32X3;
+        default: return GEMM_TF32;
+    }
+}
+inline bool tensor_kind(GemmKind k) { return k == GEMM_TF32 || k == GEMM_BF16 || k == GEMM_TF32X3 || k == GEMM_BF16X3; }
+inline GemmKind update_kind(ct_precision p) {
+    switch (p) {
+        case CT_FP64: return GEMM_F64;
+        case CT_FP32: return GEMM_F32;
+        case CT_BF16_REFINE: return GEMM_BF16;
+        case CT_TF32X3_REFINE: return GEMM_TF32X3;
+        case CT_BF16X3_REFINE: return GEMM_BF16X3;
+        default: return GEMM_TF32;
+    }
+}
 
 struct GemmArgs {
     GemmKind kind;
@@ -92,6 +118,15 @@ ct_status trsm_upper(GemmKind kind, bool trans, int64_t n, int64_t k, const void
                      void *C, int64_t ldc, Scratch &ws, cudaStream_t s);
 
 // ---- elementwise / layout helpers (util.cu) -----------------------------------------------
+// K-major operand copy for split-precision products.  Each FP32 value x of
+// op(src) (K x MN; src_kmajor: element (k, j) at src[k + j*lds], else at
+// src[j + k*lds]) becomes hi = nearest value of the narrow type and
+// lo = (x - hi) rounded the same way; the copy holds, along K' = 3K, the
+// runs [hi, hi, lo] (second_operand = false) or [hi, lo, hi] (true), so one
+// product of the two copies over K' sums hi*hi + hi*lo + lo*hi.  dst_kind 2:
+// BF16; 3: TF32 values stored as FP32.  dst: element (k', j) at dst[k' + j*ldt].
+ct_status split3_copy(const float *src, int64_t lds, bool src_kmajor, int dst_kind, bool second_operand,
+                      void *dst, int64_t ldt, int64_t K, int64_t MN, cudaStream_t s);
 ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
                           int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s);
 // 0 = float, 1 = double for src/dst kinds above.

@@ -455,7 +455,7 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
     ct_opts o{};
     o.precision = CT_TF32_REFINE;
     if (opts) o = *opts;
-    if (o.precision < CT_FP64 || o.precision > CT_BF16_REFINE || o.stop_after < 0) return CT_ERR_ARG;
+    if (o.precision < CT_FP64 || o.precision > CT_BF16X3_REFINE || o.stop_after < 0) return CT_ERR_ARG;
     if ((o.precision == CT_FP64) != sys->fp64) {
         set_error("factor precision does not match the system's storage");
         return CT_ERR_ARG;
@@ -484,8 +484,8 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
     f->sys = sys;
     f->prec = o.precision;
     f->fp64 = o.precision == CT_FP64;
-    f->kind = f->fp64 ? GEMM_F64 : (o.precision == CT_FP32 ? GEMM_F32 : GEMM_TF32);
-    f->upd_kind = o.precision == CT_BF16_REFINE ? GEMM_BF16 : f->kind;
+    f->kind = solve_kind(o.precision);
+    f->upd_kind = update_kind(o.precision);
     f->M = sys->rows;
     f->n = sys->n;
     f->m = sys->m;

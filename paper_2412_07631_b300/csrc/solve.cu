@@ -42,7 +42,7 @@ ct_status solve_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X,
         info->rjj_min_abs = f->rjj_min;
         info->rjj_max_abs = f->rjj_max;
     }
-    if (f->prec == CT_TF32_REFINE || f->prec == CT_BF16_REFINE)
+    if (is_refine_prec(f->prec))
         return refine_run(f, B, ldb, k, X, ldx, o, s, info);
     return check_device_status(s);
 }
@@ -52,8 +52,7 @@ ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t 
 
 ct_status adjoint_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB, int64_t ldgb,
                       const ct_opts *o, cudaStream_t s, ct_solve_info *info) {
-    if ((f->prec == CT_TF32_REFINE || f->prec == CT_BF16_REFINE) &&
-        !(o && o->refine_max_iter < 0))
+    if (is_refine_prec(f->prec) && !(o && o->refine_max_iter < 0))
         return adjoint_refine_run(f, gX, ldgx, k, gB, ldgb, o, s, info);
     const int64_t M = f->M, m = f->m, n = f->n, ldbt = f->lda;
     CT_TRY(f->Bt.ensure(f->es() * (size_t)ldbt * k));

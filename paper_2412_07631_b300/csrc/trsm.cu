@@ -207,7 +207,7 @@ ct_status trsm_prepare(ct_factor f, cudaStream_t s) {
     else
         CT_TRY((diag_inverse_launch<float, 128>(f->n, (const float *)f->Rm, f->ldr,
                                                 (float *)f->Rinv, (float *)f->RinvT, s)));
-    if (f->kind == GEMM_TF32 || f->kind == GEMM_BF16) {
+    if (tensor_kind(f->kind)) {
         f->ldrt = round_up(f->n, 32);
         CT_CUDA(cudaMalloc(&f->Rt, es * (size_t)f->ldrt * f->n));
         CT_TRY(transpose_any(0, f->Rm, f->ldr, 0, f->Rt, f->ldrt, f->n, f->n, s));
@@ -236,7 +236,7 @@ ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, 
     const int64_t nsb = ceil_div(n, SB);
     CT_TRY(f->misc2.ensure(es * (size_t)TB * k));
     void *tmp = f->misc2.ptr;
-    const bool tc = f->kind == GEMM_TF32 || f->kind == GEMM_BF16;
+    const bool tc = tensor_kind(f->kind);
     auto Cp = [&](int64_t i) { return (char *)C + es * i; };
     // C[r0:r0+rows] -= R[r0:r0+rows, c0:c0+cols] X   with X = C[c0:c0+cols]   (back)
     // C[r0:r0+rows] -= R[c0:c0+cols, r0:r0+rows]^T X with X = C[c0:c0+cols]   (forward)

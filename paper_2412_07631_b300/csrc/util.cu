@@ -101,7 +101,82 @@ __global__ void transpose_kernel(const S *src, int64_t lds, D *dst, int64_t ldd,
     }
 }
 
+// Round to the nearest TF32 value (10 explicit mantissa bits), ties away
+// from zero, kept in FP32 format with the 13 low bits cleared.  Finite
+// inputs only (the factorisation stops on non-finite values elsewhere).
+__device__ __forceinline__ float round_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+template <typename D> struct Split;
+template <> struct Split<__nv_bfloat16> {
+    static __device__ __forceinline__ void run(float x, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+        *hi = __float2bfloat16_rn(x);
+        *lo = __float2bfloat16_rn(x - __bfloat162float(*hi));
+    }
+};
+template <> struct Split<float> {  // TF32 values in FP32 words
+    static __device__ __forceinline__ void run(float x, float *hi, float *lo) {
+        *hi = round_tf32(x);
+        *lo = round_tf32(x - *hi);
+    }
+};
+
+// One 32 x 32 tile of op(src) (k0.., j0..) through shared memory, so both
+// the read (either layout) and the three K-runs of the write are coalesced.
+template <typename D, bool KMAJOR>
+__global__ void split3_kernel(const float *src, int64_t lds, D *dst, int64_t ldt, int64_t K, int64_t MN,
+                              bool second) {
+    __shared__ float tile[32][33];  // [j][k]
+    const int64_t k0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        if (KMAJOR) {
+            const int64_t k = k0 + threadIdx.x, j = j0 + r;
+            if (k < K && j < MN) tile[r][threadIdx.x] = src[k + j * lds];
+        } else {
+            const int64_t j = j0 + threadIdx.x, k = k0 + r;
+            if (k < K && j < MN) tile[threadIdx.x][r] = src[j + k * lds];
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t k = k0 + threadIdx.x, j = j0 + r;
+        if (k < K && j < MN) {
+            D hi, lo;
+            Split<D>::run(tile[r][threadIdx.x], &hi, &lo);
+            D *d = dst + j * ldt;
+            d[k] = hi;
+            d[K + k] = second ? lo : hi;
+            d[2 * K + k] = second ? hi : lo;
+        }
+    }
+}
+
 }  // namespace
+
+ct_status split3_copy(const float *src, int64_t lds, bool src_kmajor, int dst_kind, bool second_operand,
+                      void *dst, int64_t ldt, int64_t K, int64_t MN, cudaStream_t s) {
+    if (K == 0 || MN == 0) return CT_OK;
+    if ((dst_kind != 2 && dst_kind != 3) || ldt < 3 * K) return CT_ERR_ARG;
+    const dim3 block(32, 8);
+    for (int64_t c0 = 0; c0 < MN; c0 += 32 * 65535LL) {  // grid.y limit
+        const int64_t cc = std::min<int64_t>(MN - c0, 32 * 65535LL);
+        const float *sp = src + (src_kmajor ? c0 * lds : c0);
+        const dim3 grid((unsigned)ceil_div(K, 32), (unsigned)ceil_div(cc, 32));
+        if (dst_kind == 2) {
+            __nv_bfloat16 *dp = (__nv_bfloat16 *)dst + c0 * ldt;
+            if (src_kmajor) split3_kernel<__nv_bfloat16, true><<<grid, block, 0, s>>>(sp, lds, dp, ldt, K, cc, second_operand);
+            else split3_kernel<__nv_bfloat16, false><<<grid, block, 0, s>>>(sp, lds, dp, ldt, K, cc, second_operand);
+        } else {
+            float *dp = (float *)dst + c0 * ldt;
+            if (src_kmajor) split3_kernel<float, true><<<grid, block, 0, s>>>(sp, lds, dp, ldt, K, cc, second_operand);
+            else split3_kernel<float, false><<<grid, block, 0, s>>>(sp, lds, dp, ldt, K, cc, second_operand);
+        }
+        count_launch();
+    }
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
 
 ct_status transpose_any(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
                         int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {

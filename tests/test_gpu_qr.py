@@ -120,12 +120,12 @@ def test_adjoint_matches_oracle_gradient(oracle_mod):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("precision", ["tf32", "bf16", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("ns,nv,nb,sl,noisy", [(32, 60, 46, 0.0, False), (24, 40, 36, 0.05, True),
                                                (19, 31, 29, 0.05, True)])
 def test_refined_reaches_1e6(oracle_mod, precision, ns, nv, nb, sl, noisy):
-    """TF32 or BF16 tensor-core factors + FP64 refinement: relative image
-    error <= 1e-6 against the FP64 oracle solution."""
+    """TF32, BF16 or split-precision tensor-core factors + FP64 refinement:
+    relative image error <= 1e-6 against the FP64 oracle solution."""
     torch = need_cuda()
     import paper_2412_07631_b300 as ct
     O = oracle_mod
@@ -133,11 +133,38 @@ def test_refined_reaches_1e6(oracle_mod, precision, ns, nv, nb, sl, noisy):
     Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
     sysg = ct.System(ct.make_geometry(ns, nv, nb, sl), "fp32")
     # small blocks so the BF16 trailing-update GEMMs run at these sizes
-    F = sysg.factor(precision, nb_outer=64 if precision == "bf16" else 0)
+    F = sysg.factor(precision, nb_outer=64 if precision != "tf32" else 0)
     Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
     Xg = F.solve(Bt, max_iter=30, tol=1e-9).cpu().numpy().T
     print("refine info", F.last_info)
     assert rel_err_cols(Xg, Xo).max() <= 1e-6
+
+
+@pytest.mark.gpu
+def test_split_precision_widens_refinement(oracle_mod):
+    """An ill-conditioned system (32x32 image from 30 views, no
+    regularisation: condition number about 3e4, so TF32 or BF16 factors are
+    poor preconditioners): the split-precision factors refine to the oracle
+    solution in a few FP64 steps with a handful of inner steps, where the
+    single-pass TF32 factor needs many times more inner steps."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, 32, 30, 46, 0.0, 3, False)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    info = {}
+    for precision in ("tf32", "tf32x3", "bf16x3"):
+        sysg = ct.System(ct.make_geometry(32, 30, 46, 0.0), "fp32")
+        F = sysg.factor(precision, nb_outer=64)
+        Xg = F.solve(Bt, max_iter=10, tol=1e-12, allow_noconv=True).cpu().numpy().T
+        info[precision] = F.last_info
+        print(precision, rel_err_cols(Xg, Xo).max(), F.last_info)
+        if precision != "tf32":
+            assert rel_err_cols(Xg, Xo).max() <= 1e-10
+            assert F.last_info["iterations"] <= 6
+    for precision in ("tf32x3", "bf16x3"):
+        assert 5 * info[precision]["inner_iterations"] <= info["tf32"]["inner_iterations"]
 
 
 @pytest.mark.gpu
