@@ -147,6 +147,14 @@ typedef struct {
  * runs them as individual launches instead.  (Per-launch timing from
  * ct_stats_reset(1) also disables graphs.) */
 #define CT_OPT_NO_GRAPHS 1
+/* ct_opts.flags for ct_qr_factor / ct_qr_factor_ooc: FP32-storage panels of
+ * 32 columns are by default factored from two Gram matrices (CholeskyQR
+ * twice, then the Householder reflectors reconstructed from the orthonormal
+ * factor: the same reflectors in exact arithmetic, two grid-wide exchanges
+ * per panel instead of 32), falling back to the column-by-column sweep for
+ * a panel whose columns are nearly dependent in FP32; this bit always uses
+ * the column-by-column sweep. */
+#define CT_OPT_COLUMN_PANEL 2
 
 typedef struct {
     int32_t iterations;       /* refinement steps taken: FP64 residual + correction

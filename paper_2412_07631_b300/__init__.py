@@ -223,28 +223,31 @@ class System:
         return P
 
     def factor(self, precision: str | None = None, nb_outer: int | str = 0, nb_inner: int = 0,
-               stream=None) -> "Factor":
+               stream=None, column_panel: bool = False) -> "Factor":
         """nb_outer: outer block width (0: library default; "auto": the
-        autotuner's cached choice for this geometry, measured on first use)."""
+        autotuner's cached choice for this geometry, measured on first use).
+        column_panel: factor every panel column by column (CT_OPT_COLUMN_PANEL)
+        instead of from its Gram matrices."""
         if precision is None:
             precision = "fp64" if self.storage == "fp64" else "tf32"
         if nb_outer == "auto":
             from . import autotune
             nb_outer = autotune.outer_block(self.geom, precision)
-        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0)
+        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 2 if column_panel else 0)
         h = C.c_void_p()
         _check(lib().ct_qr_factor(self.h, C.byref(o), _stream(stream), C.byref(h)))
         return Factor(h, self, precision)
 
     def factor_ooc(self, precision: str | None = None, device_budget: int = 16 << 30,
                    nb_outer: int = 0, nb_inner: int = 0, stream=None,
-                   stop_after: int = 0) -> "Factor | None":
+                   stop_after: int = 0, column_panel: bool = False) -> "Factor | None":
         """Out-of-core QR of a host- or disk-resident system (see
         ct_qr_factor_ooc).  stop_after > 0 (disk): stop after that many
         superpanels and return None; calling again resumes."""
         if precision is None:
             precision = "fp64" if self.storage == "fp64" else "tf32"
-        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 0, int(stop_after))
+        o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 2 if column_panel else 0,
+                 int(stop_after))
         h = C.c_void_p()
         st = lib().ct_qr_factor_ooc(self.h, C.byref(o), C.c_size_t(int(device_budget)), _stream(stream),
                                     C.byref(h))

@@ -519,6 +519,7 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     f->fp64 = o.precision == CT_FP64;
     f->kind = solve_kind(o.precision);
     f->upd_kind = update_kind(o.precision);
+    f->gram_panel = !(o.flags & CT_OPT_COLUMN_PANEL);
     f->M = sys->rows;
     f->n = sys->n;
     f->m = sys->m;

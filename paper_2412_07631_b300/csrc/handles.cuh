@@ -85,6 +85,7 @@ struct ct_factor_s {
     double *pinned = nullptr;  // host readback of per-slice scalars (pinned)
     size_t pinned_count = 0;
     bool graphs_enabled = true;
+    bool gram_panel = true;  // FP32 panels from Gram matrices (else column by column)
     // work buffers
     ctqr::Scratch gemm_ws, W, W2, G, panel_ws, Bt, trsm_ws, refine_ws, host_pinned, misc, misc2;
     size_t es() const { return fp64 ? 8 : 4; }

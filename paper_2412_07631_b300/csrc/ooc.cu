@@ -486,6 +486,7 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
     f->fp64 = o.precision == CT_FP64;
     f->kind = solve_kind(o.precision);
     f->upd_kind = update_kind(o.precision);
+    f->gram_panel = !(o.flags & CT_OPT_COLUMN_PANEL);
     f->M = sys->rows;
     f->n = sys->n;
     f->m = sys->m;

@@ -314,7 +314,10 @@ __device__ __forceinline__ uint64_t tag(unsigned epoch, float v) {
 template <int RPT>
 __global__ void __launch_bounds__(RP_THREADS, 1)
     panel_qr_regs_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec,
-                         uint64_t *tot, unsigned *counter, DevStatus *st, int64_t rows_per) {
+                         uint64_t *tot, unsigned *counter, DevStatus *st, int64_t rows_per,
+                         const int *only_if) {
+    // after the Gram-based kernel: run only if it declined this panel
+    if (only_if != nullptr && *only_if == 0) return;
     __shared__ float red[RP_WARPS][32];
     __shared__ float red_ss[RP_WARPS];
     __shared__ float rowsm[32];
@@ -534,8 +537,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
 }
 
 template <int RPT>
-ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, Scratch &ws,
-                            int G, int64_t rows_per, cudaStream_t s) {
+ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, char *wsp,
+                            int G, int64_t rows_per, const int *only_if, cudaStream_t s) {
     const int64_t rows = M - j0;
     auto fn = panel_qr_regs_kernel<RPT>;
     int per_sm = 0;
@@ -544,17 +547,15 @@ ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float 
         set_error("panel: cooperative grid %d does not fit (%d per SM)", G, per_sm);
         return CT_ERR_CUDA;
     }
-    // workspace: totals [2][RP_TOT] words | counters [2] | records [2][G][RP_REC] floats
+    // workspace (regs_ws_bytes): totals [2][RP_TOT] words | counters [2] | records [2][G][RP_REC] floats
     const size_t tot_bytes = sizeof(uint64_t) * 2 * RP_TOT;
     const size_t cnt_bytes = 256;
-    const size_t need = tot_bytes + cnt_bytes + sizeof(float) * 2 * (size_t)G * RP_REC;
-    CT_TRY(ws.ensure(need));
-    uint64_t *tot = (uint64_t *)ws.ptr;
-    unsigned *counter = (unsigned *)((char *)ws.ptr + tot_bytes);
-    float *rec = (float *)((char *)ws.ptr + tot_bytes + cnt_bytes);
-    CT_CUDA(cudaMemsetAsync(ws.ptr, 0, tot_bytes + cnt_bytes, s));
+    uint64_t *tot = (uint64_t *)wsp;
+    unsigned *counter = (unsigned *)(wsp + tot_bytes);
+    float *rec = (float *)(wsp + tot_bytes + cnt_bytes);
+    CT_CUDA(cudaMemsetAsync(wsp, 0, tot_bytes + cnt_bytes, s));
     DevStatus *st = device_status();
-    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &counter, &st, &rows_per};
+    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &counter, &st, &rows_per, (void *)&only_if};
     ProfScope prof(PROF_PANEL, s, 2.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32, G,
                    2 + RPT);
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(RP_THREADS), args, 0, s));
@@ -642,8 +643,12 @@ ct_status panel_launch(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau,
 
 }  // namespace
 
+size_t regs_ws_bytes(int G) {
+    return sizeof(uint64_t) * 2 * RP_TOT + 256 + sizeof(float) * 2 * (size_t)G * RP_REC;
+}
+
 ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int nb, void *tau,
-                   Scratch &ws, cudaStream_t s) {
+                   Scratch &ws, cudaStream_t s, bool use_gram) {
     if (nb <= 0 || nb > 32 || M - j0 < 1) return CT_ERR_ARG;
     if (fp64) {
         if (nb <= 16) return panel_launch<double, 16>((double *)A, lda, M, j0, nb, (double *)tau, ws, s);
@@ -658,10 +663,24 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
         G = (int)ceil_div(rows, rows_per);
         const int64_t rpt = ceil_div(rows_per, RP_THREADS);
         if (rows >= 32 && rpt <= 4 && G <= RP_WARPS * RP_MAX_PER_WARP) {
-            if (rpt <= 1) return panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
-            if (rpt <= 2) return panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
-            if (rpt <= 3) return panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
-            return panel_regs_launch<4>((float *)A, lda, M, j0, (float *)tau, ws, G, rows_per, s);
+            // workspace: fallback flag | column-by-column kernel | Gram kernel
+            const size_t rb = round_up((int64_t)regs_ws_bytes(G), 256);
+            CT_TRY(ws.ensure(256 + rb + panel_gram_ws_bytes(G)));
+            int *fallback = (int *)ws.ptr;
+            char *wr = (char *)ws.ptr + 256;
+            const int *only_if = nullptr;
+            if (use_gram) {
+                CT_CUDA(cudaMemsetAsync(fallback, 0, sizeof(int), s));
+                ProfScope prof(PROF_PANEL, s, 4.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32,
+                               G, 10 + (int)rpt);
+                CT_TRY(panel_gram((float *)A, lda, M, j0, (float *)tau, wr + rb, G, rows_per, (int)rpt,
+                                  fallback, s));
+                only_if = fallback;
+            }
+            if (rpt <= 1) return panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
+            if (rpt <= 2) return panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
+            if (rpt <= 3) return panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
+            return panel_regs_launch<4>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
         }
     }
     return panel_launch<float, 32>((float *)A, lda, M, j0, nb, (float *)tau, ws, s);

@@ -1,0 +1,400 @@
+// panel_gram.cu -- panel factorisation from Gram matrices (FP32 storage,
+// 32-column panels, rows in registers).
+//
+// The reflectors of a panel A (rows j0 .. M-1, 32 columns) are the ones the
+// column-by-column Householder sweep (Sec. 2, Eq. 2; Sec. 2.1 'dgeqrf')
+// produces, obtained with two grid-wide exchanges instead of one per column:
+//   1. CholeskyQR twice: G1 = A^T A, R1 = chol(G1), Q = A R1^-1;
+//      G2 = Q^T Q, R2 = chol(G2), Q <- Q R2^-1, R = R2 R1 (A = Q R, Q with
+//      orthonormal columns to working precision after the second pass).
+//   2. Householder reconstruction: the thin Q of the Householder form is
+//      Q D for a diagonal D of signs, with Q D = [I - V1 T V1^T; -V2 T V1^T].
+//      So I - Q1 D = V1 U is an LU factorisation (V1 unit lower, U = T V1^T
+//      upper), whose signs d_j are chosen during the elimination so every
+//      pivot is 1 + |w_jj| >= 1; then tau_j = U_jj, V2 = -Q2 D U^-1 and the
+//      triangle is D R.  (In exact arithmetic these are exactly the
+//      reflectors, tau and R of the Householder sweep with the sign rule
+//      beta = -sign(alpha) ||x||, up to that sign choice.)
+// Each exchange: every CTA writes its partial Gram matrix (upper triangle,
+// FP32 sums over its rows), the grid meets, CTA b sums its share of the 528
+// entries over all CTAs in a fixed order (FP64), the grid meets again and
+// every CTA reads the totals.  Every CTA then repeats the same small
+// 32 x 32 steps (in FP32) on identical inputs, so
+// all hold identical factors.  A Cholesky pivot that is not safely positive
+// (the panel's columns nearly dependent in FP32) or a second Gram matrix
+// far from the identity makes every CTA leave the panel untouched and raise
+// the fallback flag; the column-by-column kernel then factors it.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ctqr {
+namespace {
+
+constexpr int GQ_THREADS = 256;
+constexpr int GQ_WARPS = GQ_THREADS / 32;
+constexpr int GQ_TRI = 528;  // upper triangle of a 32 x 32 matrix
+constexpr int GQ_LD = 36;    // row stride of the shared copy of the rows (16-byte rows, 4-way stores)
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (i, j), i <= j, of the column-packed upper triangle
+__device__ __forceinline__ void tri_ij(int e, int &i, int &j) {
+    j = 0;
+    while ((j + 1) * (j + 2) / 2 <= e) ++j;
+    i = e - j * (j + 1) / 2;
+}
+
+// All CTAs meet (bounded wait).  Returns false on timeout or another CTA's
+// error; the caller then leaves.
+__device__ bool grid_meet(unsigned *ctr, unsigned G, DevStatus *st, int site, int *ok_s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        const uint64_t t0 = globaltimer_ns();
+        int ok = 1;
+        unsigned spins = 0;
+        while (*((volatile unsigned *)ctr) < G) {
+            __nanosleep(40);
+            if ((++spins & 63u) == 0) {
+                if (*((volatile int *)&st->code) != 0) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                    raise_status(st, DEV_TIMEOUT, site, 0);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *ok_s = ok;
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
+
+struct GramShared {
+    float g[32][33];             // Gram totals (symmetric), then scratch
+    float W[32][33];             // Q1 and its eliminations
+    float Rm[3][32][33];         // R1, R2, U (the three right-hand triangles of the row solves)
+    float rinv[3][32];
+    float LR[32][33];            // first 32 rows of the result: V1 below the diagonal, D R on and above
+    float dsign[32], rw[32], dg[32];
+    int ok, bad;
+};
+
+// One Gram exchange.  The CTA's rows sit in rows_sm (row-major, GQ_LD floats
+// a row).  The 36 4 x 4 blocks on and above the diagonal of their Gram
+// matrix are split over 7 groups of rows: thread t < 252 forms block
+// t % 36 over row group t / 36 in FP32; after a barrier the partials go
+// through rows_sm (no longer needed) and are summed over the groups in a
+// fixed order into the CTA's record (upper triangle).  The grid's totals
+// (summed in FP64 in a fixed order) end in s.g (full symmetric).
+__device__ bool gram_exchange(float *rows_sm, int64_t nloc, GramShared &s, float *rec, double *tot,
+                              unsigned *bar, unsigned G, DevStatus *st, int site) {
+    constexpr int NGRP = 7, NBLK = 36;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int blk = threadIdx.x % NBLK, grp = threadIdx.x / NBLK;
+    // block blk -> (bj, bk), bj <= bk, in row-major order of the upper triangle of 8 x 8
+    int bj = 0, rem = blk;
+    while (rem >= 8 - bj) {
+        rem -= 8 - bj;
+        ++bj;
+    }
+    const int bk = bj + rem;
+    float p[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) p[q] = 0.0f;
+    if (grp < NGRP) {
+        const int64_t chunk = (nloc + NGRP - 1) / NGRP;
+        const int64_t ra = grp * chunk, rb = min(nloc, ra + chunk);
+#pragma unroll 2
+        for (int64_t r = ra; r < rb; ++r) {
+            const float4 x = *reinterpret_cast<const float4 *>(rows_sm + r * GQ_LD + 4 * bj);
+            const float4 y = *reinterpret_cast<const float4 *>(rows_sm + r * GQ_LD + 4 * bk);
+            const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) p[u * 4 + v] = fmaf(xv[u], yv[v], p[u * 4 + v]);
+        }
+    }
+    __syncthreads();  // every thread is done reading the rows
+    if (grp < NGRP) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) rows_sm[(grp * NBLK + blk) * 16 + q] = p[q];
+    }
+    __syncthreads();
+    float *mine = rec + (size_t)blockIdx.x * GQ_TRI;
+    for (int e = threadIdx.x; e < GQ_TRI; e += GQ_THREADS) {
+        int i, j;
+        tri_ij(e, i, j);  // i <= j
+        const int ib = i / 4, jbb = j / 4;
+        // the block (ib, jbb) of the upper triangle, entry (i % 4, j % 4)
+        const int b = ib * 8 - ib * (ib - 1) / 2 + (jbb - ib);
+        const int q = (i % 4) * 4 + (j % 4);
+        float v = 0.0f;
+#pragma unroll
+        for (int g2 = 0; g2 < NGRP; ++g2) v += rows_sm[(g2 * NBLK + b) * 16 + q];
+        mine[e] = v;
+    }
+    if (!grid_meet(bar, G, st, site, &s.ok)) return false;
+    // CTA b sums entries [b*E, (b+1)*E) over all CTAs, warp by warp, lanes
+    // striding the records, in a fixed order
+    const int E = (GQ_TRI + (int)G - 1) / (int)G;
+    const int e0 = (int)blockIdx.x * E, e1 = min(GQ_TRI, e0 + E);
+    for (int e = e0 + warp; e < e1; e += GQ_WARPS) {
+        double v = 0.0;
+        for (unsigned b = lane; b < G; b += 32) v += (double)__ldcg(rec + (size_t)b * GQ_TRI + e);
+        v = warp_sum_d(v);
+        if (lane == 0) tot[e] = v;
+    }
+    if (!grid_meet(bar + 1, G, st, site + 1, &s.ok)) return false;
+    for (int e = threadIdx.x; e < GQ_TRI; e += GQ_THREADS) {
+        int i, j;
+        tri_ij(e, i, j);
+        const float v = (float)__ldcg(tot + e);
+        s.g[i][j] = v;
+        s.g[j][i] = v;
+    }
+    __syncthreads();
+    return true;
+}
+
+// The small 32 x 32 steps (a few per panel) use the whole CTA on shared
+// memory, one barrier-separated pass per pivot: short loops whose few
+// instructions stay in the instruction cache, and eight warps to hide the
+// latency of each step.
+
+// R <- chol(s.g) (upper, R^T R = G) into Rout, 1 / diag(R) into rinv;
+// s.g is overwritten.  Returns false (the same in every thread) if a pivot
+// is not above min_rel times its original diagonal entry or, with
+// near_identity, if s.g is not within 0.25 of I entrywise.
+__device__ bool chol_cta(GramShared &s, float (*Rout)[33], float *rinv, float min_rel, bool near_identity) {
+    const int t = threadIdx.x;
+    int flag = 0;
+    if (near_identity)
+        for (int e = t; e < 1024; e += GQ_THREADS) {
+            const int i = e >> 5, j = e & 31;
+            if (fabsf(s.g[i][j] - (i == j ? 1.0f : 0.0f)) > 0.25f) flag = 1;
+        }
+    if (t < 32) s.dg[t] = s.g[t][t];
+    bool bad = __syncthreads_or(flag) != 0;
+    for (int i = 0; i < 32; ++i) {
+        const float gii = s.g[i][i];
+        const bool ok = gii > min_rel * s.dg[i];
+        bad = bad || !ok;
+        const float rii = ok ? sqrtf(gii) : 1.0f;
+        if (t < 32) s.rw[t] = (t > i) ? s.g[i][t] / rii : (t == i ? rii : 0.0f);
+        __syncthreads();
+        for (int e = t; e < 1024; e += GQ_THREADS) {
+            const int k = e >> 5, c = e & 31;
+            if (k > i && c >= k) s.g[k][c] = fmaf(-s.rw[k], s.rw[c], s.g[k][c]);
+        }
+        if (t < 32) Rout[i][t] = s.rw[t];
+        __syncthreads();
+    }
+    if (t < 32) rinv[t] = 1.0f / Rout[t][t];
+    __syncthreads();
+    return !bad;
+}
+
+// Householder reconstruction (see the top of the file), whole CTA:
+// R = R2 R1; Q1 = A1 R^-1; LU of I - Q1 D with the signs d_j chosen on the
+// way; U (with 1 / diag U), V1 and D R into s; tau = diag(U).
+__device__ void reconstruct_cta(GramShared &s, const float *topbuf, float *tau, bool write_tau) {
+    const int t = threadIdx.x;
+    // R = R2 R1 (upper) into s.g; Q1 rows into s.W
+    for (int e = t; e < 1024; e += GQ_THREADS) {
+        const int i = e >> 5, k = e & 31;
+        float v = 0.0f;
+        for (int l = i; l <= k; ++l) v = fmaf(s.Rm[1][i][l], s.Rm[0][l][k], v);
+        s.g[i][k] = v;  // zero below the diagonal (empty sum)
+        s.W[i][k] = __ldcg(topbuf + e);
+    }
+    __syncthreads();
+    // W <- W R^-1, column by column
+    for (int j = 0; j < 32; ++j) {
+        if (t < 32) s.W[t][j] = s.W[t][j] / s.g[j][j];
+        __syncthreads();
+        for (int e = t; e < 1024; e += GQ_THREADS) {
+            const int r = e >> 5, k = e & 31;
+            if (k > j) s.W[r][k] = fmaf(-s.W[r][j], s.g[j][k], s.W[r][k]);
+        }
+        __syncthreads();
+    }
+    // LU of I - W D: step j picks d_j = -sign(w_jj), pivot 1 + |w_jj|,
+    // multipliers l_rj = -d_j w_rj / (1 + |w_jj|), then eliminates
+    for (int j = 0; j < 32; ++j) {
+        const float wjj = s.W[j][j];
+        const float dj = (wjj >= 0.0f) ? -1.0f : 1.0f;
+        const float ujj = 1.0f + fabsf(wjj);
+        if (t < 32) {
+            const float l = (t > j) ? (-dj * s.W[t][j]) / ujj : 0.0f;
+            s.rw[t] = l;
+            if (t > j) s.LR[t][j] = l;
+            if (t == j) s.dsign[j] = dj;
+        }
+        __syncthreads();
+        for (int e = t; e < 1024; e += GQ_THREADS) {
+            const int r = e >> 5, k = e & 31;
+            if (r > j && k > j) s.W[r][k] = fmaf(-s.rw[r], s.W[j][k], s.W[r][k]);
+        }
+        __syncthreads();
+    }
+    // U (row j as it stood at step j: w_jk, signs folded in), D R
+    float (*U)[33] = s.Rm[2];
+    for (int e = t; e < 1024; e += GQ_THREADS) {
+        const int j = e >> 5, k = e & 31;
+        U[j][k] = (k > j) ? -s.dsign[k] * s.W[j][k] : (k == j ? 1.0f + fabsf(s.W[j][j]) : 0.0f);
+        if (k >= j) s.LR[j][k] = s.dsign[j] * s.g[j][k];
+    }
+    __syncthreads();
+    if (t < 32) {
+        s.rinv[2][t] = 1.0f / U[t][t];
+        if (write_tau) tau[t] = U[t][t];
+    }
+    __syncthreads();
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(GQ_THREADS, 1)
+    panel_gram_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec, double *tot,
+                      float *topbuf, unsigned *bar, int *fallback, DevStatus *st, int64_t rows_per) {
+    __shared__ GramShared s;
+    extern __shared__ float rows_sm[];  // [RPT * GQ_THREADS][GQ_LD], row-major
+    const unsigned G = gridDim.x;
+    const int64_t r0 = j0 + (int64_t)blockIdx.x * rows_per;
+    const int64_t r1 = min(M, r0 + rows_per);
+    const int64_t nloc = max((int64_t)0, r1 - r0);
+
+    float a[RPT][32];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int64_t lr = threadIdx.x + (int64_t)i * GQ_THREADS;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a[i][k] = (lr < nloc) ? A[(r0 + lr) + (j0 + k) * lda] : 0.0f;
+    }
+    // the first 32 rows of the panel (CTA 0, rows 0..31 of its first slice)
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) topbuf[threadIdx.x * 32 + k] = a[0][k];
+    }
+
+    // phase 0: G1 = A^T A, R1 = chol(G1), rows <- rows R1^-1
+    // phase 1: G2 = Q^T Q, R2 = chol(G2), rows <- rows R2^-1
+    // phase 2: reconstruction (D, U, V1, D R), rows <- -rows D U^-1
+#pragma unroll 1
+    for (int phase = 0; phase < 3; ++phase) {
+        if (phase < 2) {
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                float4 *dst = reinterpret_cast<float4 *>(rows_sm + (threadIdx.x + i * GQ_THREADS) * GQ_LD);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) dst[k] = make_float4(a[i][4 * k], a[i][4 * k + 1], a[i][4 * k + 2], a[i][4 * k + 3]);
+            }
+            __syncthreads();
+            if (!gram_exchange(rows_sm, nloc, s, rec + (size_t)phase * G * GQ_TRI, tot + phase * GQ_TRI,
+                               bar + 2 * phase, G, st, 40 + 2 * phase))
+                return;
+            // after one pass Q^T Q must already be near the identity
+            const bool good = chol_cta(s, s.Rm[phase], s.rinv[phase], phase == 0 ? 2e-5f : 0.25f, phase == 1);
+            if (!good) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) *fallback = 1;
+                return;
+            }
+        } else {
+            reconstruct_cta(s, topbuf, tau + j0, blockIdx.x == 0);
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                for (int k = 0; k < 32; ++k) a[i][k] = -a[i][k] * s.dsign[k];
+        }
+        // rows <- rows Rm[phase]^-1: x_k = (x_k - sum_{j<k} x_j R_jk) / R_kk, j ascending
+        const float (*R)[33] = s.Rm[phase];
+        const float *ri = s.rinv[phase];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            float sm[RPT];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) sm[i] = a[i][k];
+#pragma unroll
+            for (int j = 0; j < k; ++j) {
+                const float r = R[j][k];
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) sm[i] = fmaf(-a[i][j], r, sm[i]);
+            }
+            const float rk = ri[k];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) a[i][k] = sm[i] * rk;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int64_t lr = threadIdx.x + (int64_t)i * GQ_THREADS;
+        const int64_t gr = r0 + lr;
+        if (lr >= nloc) continue;
+        if (gr < j0 + 32) {  // the first 32 rows: V1 below the diagonal, D R on and above
+            const int r = (int)(gr - j0);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) A[gr + (j0 + k) * lda] = s.LR[r][k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) A[gr + (j0 + k) * lda] = a[i][k];
+        }
+    }
+}
+
+template <int RPT>
+ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
+                      int64_t rows_per, int *fallback, cudaStream_t s) {
+    auto fn = panel_gram_kernel<RPT>;
+    const size_t dyn = sizeof(float) * GQ_LD * RPT * GQ_THREADS;
+    static bool attr = false;
+    if (!attr) {
+        CT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        attr = true;
+    }
+    int per_sm = 0;
+    CT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GQ_THREADS, dyn));
+    if (per_sm * num_sms() < G) {
+        set_error("gram panel: cooperative grid %d does not fit (%d per SM)", G, per_sm);
+        return CT_ERR_CUDA;
+    }
+    // ws: barriers [4] + pad | totals [2][528] FP64 | top block [1024] | records [2][G][528]
+    unsigned *bar = (unsigned *)ws;
+    double *tot = (double *)((char *)ws + 256);
+    float *top = (float *)((char *)tot + sizeof(double) * 2 * GQ_TRI);
+    float *rec = top + 1024;
+    CT_CUDA(cudaMemsetAsync(bar, 0, 256, s));
+    DevStatus *st = device_status();
+    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &top, &bar, &fallback, &st, &rows_per};
+    CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(GQ_THREADS), args, dyn, s));
+    count_launch();
+    return CT_OK;
+}
+
+}  // namespace
+
+size_t panel_gram_ws_bytes(int G) {
+    return 256 + sizeof(double) * 2 * GQ_TRI + sizeof(float) * (1024 + 2 * (size_t)G * GQ_TRI);
+}
+
+ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
+                     int64_t rows_per, int rpt, int *fallback, cudaStream_t s) {
+    switch (rpt) {
+        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
+        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
+        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
+        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
+        default: return CT_ERR_ARG;
+    }
+}
+
+}  // namespace ctqr

@@ -161,7 +161,8 @@ ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, 
             const int wq = (int)std::min<int64_t>(MB, j + w - q);
             for (int64_t p = q; p < q + wq; p += nb) {
                 const int wp = (int)std::min<int64_t>(nb, q + wq - p);
-                CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s));
+                CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s,
+                                f->gram_panel));
                 // T_p of this panel goes straight into its diagonal block of T_J.
                 void *Tp = at(TJ, p - j, p - j, NB, es);
                 CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));

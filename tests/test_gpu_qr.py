@@ -267,3 +267,37 @@ def test_joseph_solve_matches_oracle(oracle_mod, precision, tol):
     err = rel_err_cols(Xg, Xo)
     print(precision, "joseph max rel err", err.max(), F.last_info)
     assert err.max() <= tol
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("tf32", 1e-6), ("bf16", 1e-6)])
+@pytest.mark.parametrize("ns,nv,nb,sl,noisy", [(24, 40, 36, 0.05, True), (32, 60, 46, 0.0, False),
+                                               (40, 70, 58, 0.05, True)])
+def test_gram_panel_matches_column_panel(oracle_mod, precision, tol, ns, nv, nb, sl, noisy):
+    """FP32 panels factored from their Gram matrices (CholeskyQR twice, then
+    the Householder reflectors reconstructed) solve to the oracle's accuracy,
+    like the column-by-column sweep; the factors agree with the sweep's to
+    FP32 rounding (R up to the sign of each row), so the reconstruction gives
+    the same reflectors."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, ns, nv, nb, sl, 3, noisy)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(dt).cuda()
+    out = {}
+    for column in (False, True):
+        sysg = ct.System(ct.make_geometry(ns, nv, nb, sl), "fp32")
+        F = sysg.factor(precision, nb_outer=64, column_panel=column)
+        VR, tau = F.export()
+        Xg = F.solve(Bt, max_iter=20, tol=1e-9, allow_noconv=True).double().cpu().numpy().T
+        assert rel_err_cols(Xg, Xo).max() <= tol
+        out[column] = (VR, tau)
+    (VRg, taug), (VRc, tauc) = out[False], out[True]
+    n = ns * ns
+    Rg, Rc = np.triu(VRg[:n]), np.triu(VRc[:n])
+    sg = np.sign(np.diag(Rg)) * np.sign(np.diag(Rc))
+    scale = np.abs(Rc).max()
+    assert np.abs(sg[:, None] * Rg - Rc).max() <= 2e-3 * scale
+    assert not np.array_equal(VRg, VRc)  # a different kernel ran
