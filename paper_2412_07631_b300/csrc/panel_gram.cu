@@ -167,98 +167,123 @@ __device__ bool gram_exchange(float *rows_sm, int64_t nloc, GramShared &s, float
     return true;
 }
 
-// The small 32 x 32 steps (a few per panel) use the whole CTA on shared
-// memory, one barrier-separated pass per pivot: short loops whose few
-// instructions stay in the instruction cache, and eight warps to hide the
-// latency of each step.
+// The small 32 x 32 steps (a few per panel) run on warp 0 with one row or
+// column per lane in registers: each of the 32 sequential steps is one
+// broadcast (shuffles) and 32 independent FMAs per lane, the pivot picked
+// from the registers by a 5-level select tree.  Reciprocal square roots and
+// reciprocals use the fast hardware approximations (a few ulp; the second
+// Cholesky pass and the FP64 refinement absorb such errors).
 
-// R <- chol(s.g) (upper, R^T R = G) into Rout, 1 / diag(R) into rinv;
-// s.g is overwritten.  Returns false (the same in every thread) if a pivot
-// is not above min_rel times its original diagonal entry or, with
-// near_identity, if s.g is not within 0.25 of I entrywise.
-__device__ bool chol_cta(GramShared &s, float (*Rout)[33], float *rinv, float min_rel, bool near_identity) {
-    const int t = threadIdx.x;
-    int flag = 0;
-    if (near_identity)
-        for (int e = t; e < 1024; e += GQ_THREADS) {
-            const int i = e >> 5, j = e & 31;
-            if (fabsf(s.g[i][j] - (i == j ? 1.0f : 0.0f)) > 0.25f) flag = 1;
-        }
-    if (t < 32) s.dg[t] = s.g[t][t];
-    bool bad = __syncthreads_or(flag) != 0;
-    for (int i = 0; i < 32; ++i) {
-        const float gii = s.g[i][i];
-        const bool ok = gii > min_rel * s.dg[i];
-        bad = bad || !ok;
-        const float rii = ok ? sqrtf(gii) : 1.0f;
-        if (t < 32) s.rw[t] = (t > i) ? s.g[i][t] / rii : (t == i ? rii : 0.0f);
-        __syncthreads();
-        for (int e = t; e < 1024; e += GQ_THREADS) {
-            const int k = e >> 5, c = e & 31;
-            if (k > i && c >= k) s.g[k][c] = fmaf(-s.rw[k], s.rw[c], s.g[k][c]);
-        }
-        if (t < 32) Rout[i][t] = s.rw[t];
-        __syncthreads();
-    }
-    if (t < 32) rinv[t] = 1.0f / Rout[t][t];
-    __syncthreads();
-    return !bad;
+// v[i] for a run-time i (select tree of depth 5).
+__device__ __forceinline__ float pick(const float (&v)[32], int i) {
+    float a16[16], a8[8], a4[4];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) a16[q] = (i & 16) ? v[q + 16] : v[q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a8[q] = (i & 8) ? a16[q + 8] : a16[q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a4[q] = (i & 4) ? a8[q + 4] : a8[q];
+    const float b0 = (i & 2) ? a4[2] : a4[0], b1 = (i & 2) ? a4[3] : a4[1];
+    return (i & 1) ? b1 : b0;
 }
 
-// Householder reconstruction (see the top of the file), whole CTA:
-// R = R2 R1; Q1 = A1 R^-1; LU of I - Q1 D with the signs d_j chosen on the
-// way; U (with 1 / diag U), V1 and D R into s; tau = diag(U).
-__device__ void reconstruct_cta(GramShared &s, const float *topbuf, float *tau, bool write_tau) {
-    const int t = threadIdx.x;
-    // R = R2 R1 (upper) into s.g; Q1 rows into s.W
-    for (int e = t; e < 1024; e += GQ_THREADS) {
+// R <- chol(s.g) (upper, R^T R = G) into Rout, 1 / diag(R) into rinv, one
+// warp, lane c holding column c.  Returns false (same in every lane) if a
+// pivot is not above min_rel times its original diagonal entry or, with
+// near_identity, if s.g is not within 0.25 of I entrywise.
+__device__ __noinline__ bool chol_warp(GramShared &s, float (*Rout)[33], float *rinv, float min_rel,
+                                       bool near_identity) {
+    const int lane = threadIdx.x % 32;
+    float g[32];
+    bool good = true;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        g[r] = s.g[r][lane];
+        if (near_identity) good = good && fabsf(g[r] - (r == lane ? 1.0f : 0.0f)) <= 0.25f;
+    }
+    const float d0 = s.g[lane][lane];
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i) {
+        const float gi = pick(g, i);
+        const float gii = __shfl_sync(0xffffffffu, gi, i);
+        const float dii = __shfl_sync(0xffffffffu, d0, i);
+        const bool ok = gii > min_rel * dii;
+        good = good && ok;
+        const float ric = (lane >= i && ok) ? gi * rsqrtf(gii) : 0.0f;  // R_ic (R_ii for lane i)
+        Rout[i][lane] = ric;
+        // trailing update; rows k <= i of the column turn to scratch
+#pragma unroll
+        for (int k = 0; k < 32; ++k) g[k] = fmaf(-__shfl_sync(0xffffffffu, ric, k), ric, g[k]);
+    }
+    __syncwarp();
+    const float rl = Rout[lane][lane];
+    rinv[lane] = (rl > 0.0f) ? __frcp_rn(rl) : 1.0f;
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        if (r > lane) Rout[r][lane] = 0.0f;
+    __syncwarp();
+    return __all_sync(0xffffffffu, good);
+}
+
+// Householder reconstruction (see the top of the file), one warp, lane = row
+// (R = R2 R1 already in s.g): Q1 = A1 R^-1; LU of I - Q1 D with the signs
+// d_j chosen on the way; U (with 1 / diag U), V1 and D R into s; tau = diag(U).
+__device__ __noinline__ void reconstruct_warp(GramShared &s, const float *topbuf, float *tau, bool write_tau) {
+    const int lane = threadIdx.x % 32;
+    // Rz = R with its diagonal and lower part zero, into s.W (scratch here)
+#pragma unroll
+    for (int k = 0; k < 32; ++k) s.W[lane][k] = (k > lane) ? s.g[lane][k] : 0.0f;
+    s.rw[lane] = __frcp_rn(s.g[lane][lane]);
+    __syncwarp();
+    // x <- A1 R^-1: step j fixes x_j = x[j] / R_jj and removes it from later columns
+    float x[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] = __ldcg(topbuf + lane * 32 + k);
+#pragma unroll 1
+    for (int j = 0; j < 32; ++j) {
+        const float xj = pick(x, j) * s.rw[j];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) x[k] = fmaf(-xj, s.W[j][k], x[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] *= s.rw[k];
+    // LU of I - Q1 D: step j picks d_j = -sign(w_jj), pivot 1 + |w_jj|,
+    // multipliers l_rj = -d_j w_rj / (1 + |w_jj|) (rows below j), eliminates
+#pragma unroll 1
+    for (int j = 0; j < 32; ++j) {
+        float wj[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) wj[k] = __shfl_sync(0xffffffffu, x[k], j);
+        const float wjj = pick(wj, j);
+        const float dj = (wjj >= 0.0f) ? -1.0f : 1.0f;
+        const float l = (lane > j) ? -dj * pick(x, j) * __frcp_rn(1.0f + fabsf(wjj)) : 0.0f;
+        if (lane > j) s.LR[lane][j] = l;
+        if (lane == j) s.dsign[j] = dj;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) x[k] = fmaf(-l, wj[k], x[k]);
+    }
+    __syncwarp();
+    // lane r's row now holds w_rr and w_rk (k > r) as they stood at step r
+    float (*U)[33] = s.Rm[2];
+    const float xr = pick(x, lane);
+    const float ujj = 1.0f + fabsf(xr), dl = s.dsign[lane];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        U[lane][k] = (k > lane) ? -s.dsign[k] * x[k] : (k == lane ? ujj : 0.0f);
+        if (k >= lane) s.LR[lane][k] = dl * s.g[lane][k];
+    }
+    s.rinv[2][lane] = __frcp_rn(ujj);
+    if (write_tau) tau[lane] = ujj;
+    __syncwarp();
+}
+
+// R = R2 R1 (upper) into s.g, whole CTA.
+__device__ void r_product(GramShared &s) {
+    for (int e = threadIdx.x; e < 1024; e += GQ_THREADS) {
         const int i = e >> 5, k = e & 31;
         float v = 0.0f;
         for (int l = i; l <= k; ++l) v = fmaf(s.Rm[1][i][l], s.Rm[0][l][k], v);
         s.g[i][k] = v;  // zero below the diagonal (empty sum)
-        s.W[i][k] = __ldcg(topbuf + e);
-    }
-    __syncthreads();
-    // W <- W R^-1, column by column
-    for (int j = 0; j < 32; ++j) {
-        if (t < 32) s.W[t][j] = s.W[t][j] / s.g[j][j];
-        __syncthreads();
-        for (int e = t; e < 1024; e += GQ_THREADS) {
-            const int r = e >> 5, k = e & 31;
-            if (k > j) s.W[r][k] = fmaf(-s.W[r][j], s.g[j][k], s.W[r][k]);
-        }
-        __syncthreads();
-    }
-    // LU of I - W D: step j picks d_j = -sign(w_jj), pivot 1 + |w_jj|,
-    // multipliers l_rj = -d_j w_rj / (1 + |w_jj|), then eliminates
-    for (int j = 0; j < 32; ++j) {
-        const float wjj = s.W[j][j];
-        const float dj = (wjj >= 0.0f) ? -1.0f : 1.0f;
-        const float ujj = 1.0f + fabsf(wjj);
-        if (t < 32) {
-            const float l = (t > j) ? (-dj * s.W[t][j]) / ujj : 0.0f;
-            s.rw[t] = l;
-            if (t > j) s.LR[t][j] = l;
-            if (t == j) s.dsign[j] = dj;
-        }
-        __syncthreads();
-        for (int e = t; e < 1024; e += GQ_THREADS) {
-            const int r = e >> 5, k = e & 31;
-            if (r > j && k > j) s.W[r][k] = fmaf(-s.rw[r], s.W[j][k], s.W[r][k]);
-        }
-        __syncthreads();
-    }
-    // U (row j as it stood at step j: w_jk, signs folded in), D R
-    float (*U)[33] = s.Rm[2];
-    for (int e = t; e < 1024; e += GQ_THREADS) {
-        const int j = e >> 5, k = e & 31;
-        U[j][k] = (k > j) ? -s.dsign[k] * s.W[j][k] : (k == j ? 1.0f + fabsf(s.W[j][j]) : 0.0f);
-        if (k >= j) s.LR[j][k] = s.dsign[j] * s.g[j][k];
-    }
-    __syncthreads();
-    if (t < 32) {
-        s.rinv[2][t] = 1.0f / U[t][t];
-        if (write_tau) tau[t] = U[t][t];
     }
     __syncthreads();
 }
@@ -304,13 +329,19 @@ __global__ void __launch_bounds__(GQ_THREADS, 1)
                                bar + 2 * phase, G, st, 40 + 2 * phase))
                 return;
             // after one pass Q^T Q must already be near the identity
-            const bool good = chol_cta(s, s.Rm[phase], s.rinv[phase], phase == 0 ? 2e-5f : 0.25f, phase == 1);
-            if (!good) {
+            if (threadIdx.x < 32) {
+                const bool good = chol_warp(s, s.Rm[phase], s.rinv[phase], phase == 0 ? 2e-5f : 0.25f, phase == 1);
+                if (threadIdx.x == 0) s.bad = good ? 0 : 1;
+            }
+            __syncthreads();
+            if (s.bad) {
                 if (blockIdx.x == 0 && threadIdx.x == 0) *fallback = 1;
                 return;
             }
         } else {
-            reconstruct_cta(s, topbuf, tau + j0, blockIdx.x == 0);
+            r_product(s);
+            if (threadIdx.x < 32) reconstruct_warp(s, topbuf, tau + j0, blockIdx.x == 0);
+            __syncthreads();
 #pragma unroll
             for (int i = 0; i < RPT; ++i)
 #pragma unroll
