@@ -47,6 +47,33 @@ __global__ void to_bf16_kernel(const float *src, int64_t lds, __nv_bfloat16 *dst
     }
 }
 
+// As to_bf16_kernel with 16-byte accesses: each thread converts 8
+// consecutive rows (two float4 loads, one 16-byte store).  Needs src, dst,
+// lds * 4 and ldd * 2 bytes to be multiples of 16.
+__global__ void to_bf16_vec_kernel(const float *src, int64_t lds, __nv_bfloat16 *dst, int64_t ldd,
+                                   int64_t rows, int64_t cols) {
+    const int64_t i = 8 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= rows) return;
+    for (int64_t j = blockIdx.y; j < cols; j += gridDim.y) {
+        const float *sp = src + j * lds + i;
+        __nv_bfloat16 *dp = dst + j * ldd + i;
+        if (i + 8 <= rows) {
+            const float4 a = __ldcs(reinterpret_cast<const float4 *>(sp));
+            const float4 b = __ldcs(reinterpret_cast<const float4 *>(sp + 4));
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(a.x, a.y), p1 = __floats2bfloat162_rn(a.z, a.w);
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(b.x, b.y), p3 = __floats2bfloat162_rn(b.z, b.w);
+            uint4 o;
+            o.x = *reinterpret_cast<const uint32_t *>(&p0);
+            o.y = *reinterpret_cast<const uint32_t *>(&p1);
+            o.z = *reinterpret_cast<const uint32_t *>(&p2);
+            o.w = *reinterpret_cast<const uint32_t *>(&p3);
+            *reinterpret_cast<uint4 *>(dp) = o;
+        } else {
+            for (int64_t r = i; r < rows; ++r) dst[j * ldd + r] = __float2bfloat16_rn(src[j * lds + r]);
+        }
+    }
+}
+
 template <typename T>
 __global__ void fill_zero_kernel(T *dst, int64_t ld, int64_t rows, int64_t cols) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -224,8 +251,15 @@ ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_ki
     const unsigned b = (unsigned)ceil_div(total, 256);
     if (dst_kind == 2) {  // FP32 -> BF16
         if (src_kind != 0) return CT_ERR_ARG;
-        dim3 g2((unsigned)ceil_div(ceil_div(rows, 4), 256), (unsigned)std::min<int64_t>(cols, 32768));
-        to_bf16_kernel<<<g2, 256, 0, s>>>((const float *)src, lds, (__nv_bfloat16 *)dst, ldd, rows, cols);
+        const bool vec = ((uintptr_t)src & 15) == 0 && ((uintptr_t)dst & 15) == 0 && (lds & 3) == 0 &&
+                         (ldd & 7) == 0;
+        if (vec) {
+            dim3 g2((unsigned)ceil_div(ceil_div(rows, 8), 256), (unsigned)std::min<int64_t>(cols, 32768));
+            to_bf16_vec_kernel<<<g2, 256, 0, s>>>((const float *)src, lds, (__nv_bfloat16 *)dst, ldd, rows, cols);
+        } else {
+            dim3 g2((unsigned)ceil_div(ceil_div(rows, 4), 256), (unsigned)std::min<int64_t>(cols, 32768));
+            to_bf16_kernel<<<g2, 256, 0, s>>>((const float *)src, lds, (__nv_bfloat16 *)dst, ldd, rows, cols);
+        }
         count_launch();
     }
     else if (src_kind == 0 && dst_kind == 0) {
