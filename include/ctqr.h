@@ -392,11 +392,12 @@ CT_API void ct_factor_free(ct_factor f);
 CT_API ct_status ct_stats_reset(int32_t timing);
 
 /* Synchronises the device, then returns the number of kernels launched since
- * the last reset and, per class (8 entries each; classes: 0 tensor-core GEMM,
- * 1 CUDA-core GEMM, 2 panel, 3 triangular diagonal blocks, 4 sparse FP64
- * products, 5 Siddon, 6 other, 7 sparse FP32 products), the summed event
- * time in ms, algorithmic
- * flops, algorithmic bytes and launch count.  Any pointer may be NULL. */
+ * the last reset and, per class (9 entries each; classes: 0 tensor-core GEMM
+ * with TF32 operands, 1 CUDA-core GEMM, 2 panel, 3 triangular diagonal
+ * blocks, 4 sparse FP64 products, 5 Siddon, 6 other, 7 sparse FP32 products,
+ * 8 tensor-core GEMM with BF16 operands), the summed event time in ms,
+ * algorithmic flops, algorithmic bytes and launch count.  Any pointer may be
+ * NULL. */
 CT_API ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *bytes,
                                int64_t *count);
 

@@ -406,7 +406,7 @@ class CTSolve:
 
 
 STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other",
-                "spmm_fp32"]
+                "spmm_fp32", "tc_gemm_bf16"]
 
 
 def disk_stats(reset: bool = False) -> dict:
@@ -434,8 +434,9 @@ def stats_read() -> dict:
     """Launches since the last reset and per-class time/flops/bytes/count."""
     import numpy as np
     n = C.c_int64()
-    ms, fl, by = (np.zeros(8) for _ in range(3))
-    cnt = np.zeros(8, np.int64)
+    nc = len(STAT_CLASSES)
+    ms, fl, by = (np.zeros(nc) for _ in range(3))
+    cnt = np.zeros(nc, np.int64)
     _check(lib().ct_stats_read(C.byref(n), ms.ctypes.data, fl.ctypes.data, by.ctypes.data,
                                cnt.ctypes.data))
     out = {"launches": int(n.value)}

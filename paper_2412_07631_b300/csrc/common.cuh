@@ -197,7 +197,7 @@ int num_sms();
 // events on their stream and their algorithmic flops/bytes are recorded.
 enum ProfClass : int {
     PROF_TC_GEMM = 0, PROF_SIMT_GEMM = 1, PROF_PANEL = 2, PROF_TRSM_DIAG = 3, PROF_SPMM = 4,
-    PROF_SIDDON = 5, PROF_OTHER = 6, PROF_SPMM32 = 7, PROF_NCLASS = 8
+    PROF_SIDDON = 5, PROF_OTHER = 6, PROF_SPMM32 = 7, PROF_TC_GEMM_BF16 = 8, PROF_NCLASS = 9
 };
 void count_launch(int n = 1);
 struct ProfScope {

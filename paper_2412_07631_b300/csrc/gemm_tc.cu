@@ -476,7 +476,7 @@ ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t 
         return CT_ERR_ARG;
     }
     const double ebytes = g.kind == GEMM_BF16 ? 2.0 : 4.0;
-    ProfScope prof(PROF_TC_GEMM, s, 2.0 * g.M * g.N * g.K,
+    ProfScope prof(g.kind == GEMM_BF16 ? PROF_TC_GEMM_BF16 : PROF_TC_GEMM, s, 2.0 * g.M * g.N * g.K,
                    ebytes * ((double)g.M * g.K + (double)g.K * g.N) +
                        4.0 * (double)g.M * g.N * splits * (g.beta != 0.0 ? 2 : 1),
                    g.M, g.N, g.K, splits);
