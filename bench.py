@@ -49,6 +49,10 @@ WORKLOADS = {
     # 360 degrees, 512 detectors over a 30-degree fan, source at 720 pixels
     # (the fan covers the image's half-diagonal of 181 pixels)
     "fan256": (256, 360, 512, 0.05, 512, 5e3, 10),
+    # the 256^2 scan (360 views x 364 bins) over a 64^2 image: panels as tall
+    # as the 256^2 workload's (131,072 rows) in a 2.2 GB matrix, for kernel
+    # profiles on a small case
+    "tall64": (64, 360, 364, 0.05, 64, 5e3, 10),
 }
 FAN = {"fan256": (720.0, 30.0)}  # name: (source_dist, fan_deg)
 
