@@ -96,6 +96,92 @@ __global__ void spmm_atr_kernel(int64_t m, int64_t n, int64_t k, T sl, const int
     }
 }
 
+// Variants with 16-byte accesses, for k a multiple of the vector width (4
+// floats, 2 doubles): one warp per row (column), each lane keeping NV
+// vector accumulators, i.e. 512 slices per pass over the row's nonzeros (one
+// pass for k <= 512), so the row's indices are read once per 512 slices and
+// each nonzero gathers its image row with 16-byte loads.  Same FMAs in the
+// same order as the scalar kernels above.
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    using V = float4;
+    static constexpr int W = 4, NV = 4;
+    static __device__ __forceinline__ V fma1(float a, V x, V c) {
+        return make_float4(fmaf(a, x.x, c.x), fmaf(a, x.y, c.y), fmaf(a, x.z, c.z), fmaf(a, x.w, c.w));
+    }
+    static __device__ __forceinline__ V zero() { return make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
+    static __device__ __forceinline__ V axpby(float b, V acc, float a, V y) {
+        return make_float4(b * acc.x + a * y.x, b * acc.y + a * y.y, b * acc.z + a * y.z, b * acc.w + a * y.w);
+    }
+    static __device__ __forceinline__ V scale(float b, V acc) {
+        return make_float4(b * acc.x, b * acc.y, b * acc.z, b * acc.w);
+    }
+};
+template <> struct Vec<double> {
+    using V = double2;
+    static constexpr int W = 2, NV = 8;
+    static __device__ __forceinline__ V fma1(double a, V x, V c) { return make_double2(fma(a, x.x, c.x), fma(a, x.y, c.y)); }
+    static __device__ __forceinline__ V zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ V axpby(double b, V acc, double a, V y) {
+        return make_double2(b * acc.x + a * y.x, b * acc.y + a * y.y);
+    }
+    static __device__ __forceinline__ V scale(double b, V acc) { return make_double2(b * acc.x, b * acc.y); }
+};
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) spmm_vec_kernel(int64_t m, int64_t n, int64_t k, T sl,
+                                                       const int64_t *ptr, const int32_t *idx,
+                                                       const T *val, const T *X, T alpha,
+                                                       const T *Y, T beta, T *out) {
+    using VT = Vec<T>;
+    using V = typename VT::V;
+    constexpr int NV = VT::NV;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t rows = TRANS ? n : m + (sl > T(0) ? n : 0);
+    if (row >= rows) return;
+    const int64_t kv = k / VT::W;
+    for (int64_t c0 = 0; c0 < kv; c0 += 32 * NV) {
+        V acc[NV];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) acc[u] = VT::zero();
+        const bool ray = TRANS || row < m;
+        if (ray) {
+            const int64_t q0 = ptr[row], q1 = ptr[row + 1];
+            for (int64_t q = q0; q < q1; ++q) {
+                const T a = val[q];
+                const V *xr = reinterpret_cast<const V *>(X + (int64_t)idx[q] * k);
+#pragma unroll
+                for (int u = 0; u < NV; ++u) {
+                    const int64_t c = c0 + lane + 32 * u;
+                    if (c < kv) acc[u] = VT::fma1(a, __ldg(xr + c), acc[u]);
+                }
+            }
+        }
+        if (sl > T(0) && (TRANS || !ray)) {  // the sqrt(lambda) I block
+            const V *xr = reinterpret_cast<const V *>(X + (TRANS ? (m + row) : (row - m)) * k);
+#pragma unroll
+            for (int u = 0; u < NV; ++u) {
+                const int64_t c = c0 + lane + 32 * u;
+                if (c < kv) acc[u] = VT::fma1(sl, xr[c], acc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int64_t c = c0 + lane + 32 * u;
+            if (c < kv) {
+                const V v = (alpha != T(0)) ? VT::axpby(beta, acc[u], alpha, reinterpret_cast<const V *>(Y + row * k)[c])
+                                            : VT::scale(beta, acc[u]);
+                reinterpret_cast<V *>(out + row * k)[c] = v;
+            }
+        }
+    }
+}
+
+bool vec_ok(int64_t k, int width, const void *a, const void *b, const void *c) {
+    return k % width == 0 && (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15) == 0;
+}
+
 }  // namespace
 
 ct_status spmm_ax(const SparseSys &S, int64_t k, const double *X, double alpha, const double *Y,
@@ -105,8 +191,12 @@ ct_status spmm_ax(const SparseSys &S, int64_t k, const double *X, double alpha, 
     const unsigned blocks = (unsigned)ceil_div(rows * 32, 256);
     ProfScope prof(PROF_SPMM, s, 2.0 * (S.nnz + (rows - S.m)) * k,
                    12.0 * S.nnz + 8.0 * (double)k * (S.n + rows * (alpha != 0.0 ? 2 : 1)));
-    spmm_ax_kernel<double><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.row_ptr, S.col, S.val,
-                                                  X, alpha, Y, beta, out);
+    if (vec_ok(k, 2, X, alpha != 0.0 ? (const void *)Y : nullptr, out))
+        spmm_vec_kernel<double, false><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.row_ptr, S.col,
+                                                              S.val, X, alpha, Y, beta, out);
+    else
+        spmm_ax_kernel<double><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.row_ptr, S.col, S.val,
+                                                      X, alpha, Y, beta, out);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -119,8 +209,12 @@ ct_status spmm_atr(const SparseSys &S, int64_t k, const double *R, double alpha,
     const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
     ProfScope prof(PROF_SPMM, s, 2.0 * (S.nnz + (rows - S.m)) * k,
                    12.0 * S.nnz + 8.0 * (double)k * (rows + S.n * (alpha != 0.0 ? 2 : 1)));
-    spmm_atr_kernel<double><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.col_ptr, S.csc_row,
-                                                   S.csc_val, R, alpha, Y, beta, out);
+    if (vec_ok(k, 2, R, alpha != 0.0 ? (const void *)Y : nullptr, out))
+        spmm_vec_kernel<double, true><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.col_ptr,
+                                                             S.csc_row, S.csc_val, R, alpha, Y, beta, out);
+    else
+        spmm_atr_kernel<double><<<blocks, 256, 0, s>>>(S.m, S.n, k, S.sqrt_lambda, S.col_ptr, S.csc_row,
+                                                       S.csc_val, R, alpha, Y, beta, out);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -134,8 +228,12 @@ ct_status spmm_ax32(const SparseSys &S, int64_t k, const float *X, float alpha, 
     const unsigned blocks = (unsigned)ceil_div(rows * 32, 256);
     ProfScope prof(PROF_SPMM32, s, 2.0 * (S.nnz + (rows - S.m)) * k,
                    8.0 * S.nnz + 4.0 * (double)k * (S.n + rows * (alpha != 0.0f ? 2 : 1)));
-    spmm_ax_kernel<float><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.row_ptr, S.col,
-                                                 S.val32, X, alpha, Y, beta, out);
+    if (vec_ok(k, 4, X, alpha != 0.0f ? (const void *)Y : nullptr, out))
+        spmm_vec_kernel<float, false><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.row_ptr, S.col,
+                                                        S.val32, X, alpha, Y, beta, out);
+    else
+        spmm_ax_kernel<float><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.row_ptr, S.col,
+                                                     S.val32, X, alpha, Y, beta, out);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -149,8 +247,12 @@ ct_status spmm_atr32(const SparseSys &S, int64_t k, const float *R, float alpha,
     const int64_t rows = S.m + (S.sqrt_lambda > 0.0 ? S.n : 0);
     ProfScope prof(PROF_SPMM32, s, 2.0 * (S.nnz + (rows - S.m)) * k,
                    8.0 * S.nnz + 4.0 * (double)k * (rows + S.n * (alpha != 0.0f ? 2 : 1)));
-    spmm_atr_kernel<float><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.col_ptr,
-                                                  S.csc_row, S.csc_val32, R, alpha, Y, beta, out);
+    if (vec_ok(k, 4, R, alpha != 0.0f ? (const void *)Y : nullptr, out))
+        spmm_vec_kernel<float, true><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.col_ptr,
+                                                       S.csc_row, S.csc_val32, R, alpha, Y, beta, out);
+    else
+        spmm_atr_kernel<float><<<blocks, 256, 0, s>>>(S.m, S.n, k, (float)S.sqrt_lambda, S.col_ptr,
+                                                      S.csc_row, S.csc_val32, R, alpha, Y, beta, out);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
