@@ -110,13 +110,16 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
 // diagonal of T, ld NB) and its Gram matrix G = V^T V (ld NB): for the panel
 // at offset o,  T[0:o, o:o+wp] = -T[0:o, 0:o] * G[0:o, o:o+wp] * T_p,  the
 // off-diagonal block of the product of two block reflectors.
-static ct_status assemble_t(ct_factor f, int64_t wblk, const void *G, void *T, void *Y, cudaStream_t s) {
+// `step` is the width of the diagonal blocks already in place (the panels'
+// T_p, or the mid blocks' T when an outer block is assembled from them).
+static ct_status assemble_t(ct_factor f, int64_t wblk, const void *G, void *T, void *Y, cudaStream_t s,
+                            int64_t step) {
     const size_t es = f->es();
-    const int64_t NB = f->NB, nb = f->nb;
+    const int64_t NB = f->NB;
     const GemmKind small_kind = f->fp64 ? GEMM_F64 : GEMM_F32;
-    for (int64_t o = nb; o < wblk; o += nb) {
-        const int64_t wp = std::min<int64_t>(nb, wblk - o);
-        if (!f->fp64 && (size_t)o * 33 * sizeof(float) <= 200 * 1024) {
+    for (int64_t o = step; o < wblk; o += step) {
+        const int64_t wp = std::min<int64_t>(step, wblk - o);
+        if (!f->fp64 && wp <= 32 && (size_t)o * 33 * sizeof(float) <= 200 * 1024) {
             CT_TRY(t_assemble(o, (int)wp, (const float *)G, NB, (float *)T, NB, s));
             continue;
         }
@@ -179,7 +182,7 @@ ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, 
                 void *Tq = at(TJ, q - j, q - j, NB, es);
                 CT_TRY(extract_vtop(f->fp64, f->VR, lda, q, wq, Vtq, NB, s));
                 CT_TRY(gram(f, q, wq, Vtq, Gq, s));
-                CT_TRY(assemble_t(f, wq, Gq, Tq, Y, s));
+                CT_TRY(assemble_t(f, wq, Gq, Tq, Y, s, nb));
                 CT_TRY(apply_block(f, q, wq, Vtq, Tq, true, at(f->VR, q, q + wq, lda, es), lda, ncols_mid,
                                    s, f->upd_kind, nullptr, 0));
             }
@@ -187,7 +190,16 @@ ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, 
         CT_TRY(extract_vtop(f->fp64, f->VR, lda, j, w, VtJ, NB, s));
         if (w > nb) {
             CT_TRY(gram(f, j, w, VtJ, f->G.ptr, s));
-            CT_TRY(assemble_t(f, w, f->G.ptr, TJ, Y, s));
+            if (MB < NB && w > MB) {
+                // from the mid blocks' T on the diagonal; the last mid block's
+                // own T (not needed inside the loop) first, from its part of G
+                const int64_t ql = (w - 1) / MB * MB, wl = w - ql;
+                if (wl > nb)
+                    CT_TRY(assemble_t(f, wl, at(f->G.ptr, ql, ql, NB, es), at(TJ, ql, ql, NB, es), Y, s, nb));
+                CT_TRY(assemble_t(f, w, f->G.ptr, TJ, Y, s, MB));
+            } else {
+                CT_TRY(assemble_t(f, w, f->G.ptr, TJ, Y, s, nb));
+            }
         }
         if (j + w < n)
             CT_TRY(apply_block(f, j, w, VtJ, TJ, true, at(f->VR, j, j + w, lda, es), lda, n - j - w, s,
