@@ -97,13 +97,17 @@ ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void 
 // tau[j0:j0+nb].  Cooperative kernels: for FP32 panels of 32 columns with
 // use_gram, the Gram-based kernel (two grid exchanges) and, only if it
 // declined the panel, the column-by-column one (one exchange per column).
+// With Tp, Vtp (ld ldt) given, the Gram path (or its fallback) also writes
+// the panel's T_p and the unit-lower top of its V there and sets *made_t.
 ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int nb, void *tau,
-                   Scratch &ws, cudaStream_t s, bool use_gram = true);
+                   Scratch &ws, cudaStream_t s, bool use_gram = true, void *Tp = nullptr,
+                   void *Vtp = nullptr, int64_t ldt = 0, bool *made_t = nullptr);
 // panel_gram.cu: the Gram-based kernel; ws as sized by panel_gram_ws_bytes(G);
 // *fallback is set to 1 if the panel was left for the column-by-column kernel.
 size_t panel_gram_ws_bytes(int G);
 ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
-                     int64_t rows_per, int rpt, int *fallback, cudaStream_t s);
+                     int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
+                     cudaStream_t s);
 // Copy the unit-lower-triangular top block of V (nb x nb at A[j0, j0]) into
 // Vtop (leading dimension ldv): ones on the diagonal, zeros above.
 ct_status extract_vtop(bool fp64, const void *A, int64_t lda, int64_t j0, int nb, void *Vtop,

@@ -311,11 +311,73 @@ __device__ __forceinline__ uint64_t tag(unsigned epoch, float v) {
     return ((uint64_t)epoch << 32) | __float_as_uint(v);
 }
 
+// After a fallback column sweep (the Gram kernel declined the panel), the
+// T_p of the panel's block reflector and the unit-lower top of its V, which
+// the Gram kernel would otherwise have written: each CTA forms the partial
+// V^T V of its rows (read back from A, the top rows as unit lower, rolled
+// loops: this path is rare), takes a ticket, and the last CTA sums the
+// partials in a fixed order and runs the forward columnwise T recurrence
+// T[j, j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j].
+__device__ __noinline__ void fallback_t(const float *A, int64_t lda, int64_t j0, int64_t r0, int64_t nloc,
+                                        const float *tau, float *Tp, float *Vtp, int64_t ldt, float *trec,
+                                        unsigned *tcount) {
+    __shared__ double gs[32][33];
+    __shared__ int last;
+    constexpr int NTRI = 528;
+    for (int e = threadIdx.x; e < NTRI; e += RP_THREADS) {
+        int j = 0;
+        while ((j + 1) * (j + 2) / 2 <= e) ++j;
+        const int i = e - j * (j + 1) / 2;  // i <= j
+        float acc = 0.0f;
+        for (int64_t lr = 0; lr < nloc; ++lr) {
+            const int64_t gr = r0 + lr, r = gr - j0;
+            const float vi = (r > i) ? A[gr + (j0 + i) * lda] : (r == i ? 1.0f : 0.0f);
+            const float vj = (r > j) ? A[gr + (j0 + j) * lda] : (r == j ? 1.0f : 0.0f);
+            acc = fmaf(vi, vj, acc);
+        }
+        trec[(size_t)blockIdx.x * NTRI + e] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(tcount, 1u) == gridDim.x - 1;
+        if (last) __threadfence();
+    }
+    __syncthreads();
+    if (!last) return;
+    for (int e = threadIdx.x; e < NTRI; e += RP_THREADS) {
+        int j = 0;
+        while ((j + 1) * (j + 2) / 2 <= e) ++j;
+        const int i = e - j * (j + 1) / 2;
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += (double)__ldcg(trec + (size_t)b * NTRI + e);
+        gs[i][j] = v;
+        gs[j][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // lane i owns row i of T
+        __shared__ float ts[32][33];
+        const int lane = threadIdx.x;
+        for (int j = 0; j < 32; ++j) {
+            const float tj = __ldcg(tau + j0 + j);
+            double y = 0.0;
+            for (int l = lane; l < j; ++l) y += (double)ts[lane][l] * gs[l][j];
+            ts[lane][j] = (lane < j) ? (float)(-(double)tj * y) : (lane == j ? tj : 0.0f);
+        }
+        __syncwarp();
+        for (int k = 0; k < 32; ++k) {
+            Tp[lane + k * ldt] = ts[lane][k];
+            Vtp[lane + k * ldt] = (lane == k) ? 1.0f : (lane > k ? __ldcg(A + (j0 + lane) + (j0 + k) * lda) : 0.0f);
+        }
+    }
+}
+
 template <int RPT>
 __global__ void __launch_bounds__(RP_THREADS, 1)
     panel_qr_regs_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec,
                          uint64_t *tot, unsigned *counter, DevStatus *st, int64_t rows_per,
-                         const int *only_if) {
+                         const int *only_if, float *Tp, float *Vtp, int64_t ldt, float *trec,
+                         unsigned *tcount) {
     // after the Gram-based kernel: run only if it declined this panel
     if (only_if != nullptr && *only_if == 0) return;
     __shared__ float red[RP_WARPS][32];
@@ -534,11 +596,13 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
             for (int k = 0; k < 32; ++k) A[(r0 + lr) + (j0 + k) * lda] = a[i][k];
         }
     }
+    if (only_if != nullptr && Tp != nullptr) fallback_t(A, lda, j0, r0, nloc, tau, Tp, Vtp, ldt, trec, tcount);
 }
 
 template <int RPT>
 ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, char *wsp,
-                            int G, int64_t rows_per, const int *only_if, cudaStream_t s) {
+                            int G, int64_t rows_per, const int *only_if, float *Tp, float *Vtp, int64_t ldt,
+                            float *trec, unsigned *tcount, cudaStream_t s) {
     const int64_t rows = M - j0;
     auto fn = panel_qr_regs_kernel<RPT>;
     int per_sm = 0;
@@ -555,7 +619,8 @@ ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float 
     float *rec = (float *)(wsp + tot_bytes + cnt_bytes);
     CT_CUDA(cudaMemsetAsync(wsp, 0, tot_bytes + cnt_bytes, s));
     DevStatus *st = device_status();
-    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &counter, &st, &rows_per, (void *)&only_if};
+    void *args[] = {&A,         &lda, &M,   &j0,   &tau,  &rec,  &tot,    &counter,
+                    &st,        &rows_per, (void *)&only_if, &Tp, &Vtp, &ldt, &trec, &tcount};
     ProfScope prof(PROF_PANEL, s, 2.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32, G,
                    2 + RPT);
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(RP_THREADS), args, 0, s));
@@ -648,7 +713,9 @@ size_t regs_ws_bytes(int G) {
 }
 
 ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int nb, void *tau,
-                   Scratch &ws, cudaStream_t s, bool use_gram) {
+                   Scratch &ws, cudaStream_t s, bool use_gram, void *Tp, void *Vtp, int64_t ldt,
+                   bool *made_t) {
+    if (made_t) *made_t = false;
     if (nb <= 0 || nb > 32 || M - j0 < 1) return CT_ERR_ARG;
     if (fp64) {
         if (nb <= 16) return panel_launch<double, 16>((double *)A, lda, M, j0, nb, (double *)tau, ws, s);
@@ -663,24 +730,34 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
         G = (int)ceil_div(rows, rows_per);
         const int64_t rpt = ceil_div(rows_per, RP_THREADS);
         if (rows >= 32 && rpt <= 4 && G <= RP_WARPS * RP_MAX_PER_WARP) {
-            // workspace: fallback flag | column-by-column kernel | Gram kernel
+            // workspace: fallback flag + counter | column-by-column kernel | Gram kernel |
+            // partial Gram records of a fallback's T
             const size_t rb = round_up((int64_t)regs_ws_bytes(G), 256);
-            CT_TRY(ws.ensure(256 + rb + panel_gram_ws_bytes(G)));
+            const size_t gb = round_up((int64_t)panel_gram_ws_bytes(G), 256);
+            CT_TRY(ws.ensure(256 + rb + gb + sizeof(float) * 528 * (size_t)G));
             int *fallback = (int *)ws.ptr;
+            unsigned *tcount = (unsigned *)((char *)ws.ptr + 64);
             char *wr = (char *)ws.ptr + 256;
+            float *trec = (float *)(wr + rb + gb);
             const int *only_if = nullptr;
+            const bool want_t = use_gram && Tp != nullptr && Vtp != nullptr;
             if (use_gram) {
-                CT_CUDA(cudaMemsetAsync(fallback, 0, sizeof(int), s));
+                CT_CUDA(cudaMemsetAsync(ws.ptr, 0, 256, s));
                 ProfScope prof(PROF_PANEL, s, 4.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32,
                                G, 10 + (int)rpt);
                 CT_TRY(panel_gram((float *)A, lda, M, j0, (float *)tau, wr + rb, G, rows_per, (int)rpt,
-                                  fallback, s));
+                                  fallback, want_t ? (float *)Tp : nullptr, (float *)Vtp, ldt, s));
                 only_if = fallback;
             }
-            if (rpt <= 1) return panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
-            if (rpt <= 2) return panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
-            if (rpt <= 3) return panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
-            return panel_regs_launch<4>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, s);
+            float *tp = want_t ? (float *)Tp : nullptr;
+            float *vp = want_t ? (float *)Vtp : nullptr;
+            ct_status st;
+            if (rpt <= 1) st = panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
+            else if (rpt <= 2) st = panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
+            else if (rpt <= 3) st = panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
+            else st = panel_regs_launch<4>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
+            if (st == CT_OK && made_t) *made_t = want_t;
+            return st;
         }
     }
     return panel_launch<float, 32>((float *)A, lda, M, j0, nb, (float *)tau, ws, s);

@@ -228,7 +228,8 @@ __device__ __noinline__ bool chol_warp(GramShared &s, float (*Rout)[33], float *
 // Householder reconstruction (see the top of the file), one warp, lane = row
 // (R = R2 R1 already in s.g): Q1 = A1 R^-1; LU of I - Q1 D with the signs
 // d_j chosen on the way; U (with 1 / diag U), V1 and D R into s; tau = diag(U).
-__device__ __noinline__ void reconstruct_warp(GramShared &s, const float *topbuf, float *tau, bool write_tau) {
+__device__ __noinline__ void reconstruct_warp(GramShared &s, const float *topbuf, float *tau, bool write_tau,
+                                              float *Tp, float *Vtp, int64_t ldt) {
     const int lane = threadIdx.x % 32;
     // Rz = R with its diagonal and lower part zero, into s.W (scratch here)
 #pragma unroll
@@ -275,6 +276,25 @@ __device__ __noinline__ void reconstruct_warp(GramShared &s, const float *topbuf
     s.rinv[2][lane] = __frcp_rn(ujj);
     if (write_tau) tau[lane] = ujj;
     __syncwarp();
+    if (write_tau && Tp != nullptr) {
+        // T = U V1^-T (U = T V1^T), row `lane`: t V1^T = u, forward over the
+        // columns (V1 unit lower, below the diagonal in s.LR)
+        float t[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) t[k] = U[lane][k];
+#pragma unroll 1
+        for (int l = 0; l < 32; ++l) {
+            const float tl = pick(t, l);
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                if (k > l) t[k] = fmaf(-tl, s.LR[k][l], t[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            Tp[lane + k * ldt] = (k >= lane) ? t[k] : 0.0f;
+            Vtp[lane + k * ldt] = (k == lane) ? 1.0f : (k < lane ? s.LR[lane][k] : 0.0f);
+        }
+    }
 }
 
 // R = R2 R1 (upper) into s.g, whole CTA.
@@ -291,7 +311,8 @@ __device__ void r_product(GramShared &s) {
 template <int RPT>
 __global__ void __launch_bounds__(GQ_THREADS, 1)
     panel_gram_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec, double *tot,
-                      float *topbuf, unsigned *bar, int *fallback, DevStatus *st, int64_t rows_per) {
+                      float *topbuf, unsigned *bar, int *fallback, DevStatus *st, int64_t rows_per,
+                      float *Tp, float *Vtp, int64_t ldt) {
     __shared__ GramShared s;
     extern __shared__ float rows_sm[];  // [RPT * GQ_THREADS][GQ_LD], row-major
     const unsigned G = gridDim.x;
@@ -340,7 +361,7 @@ __global__ void __launch_bounds__(GQ_THREADS, 1)
             }
         } else {
             r_product(s);
-            if (threadIdx.x < 32) reconstruct_warp(s, topbuf, tau + j0, blockIdx.x == 0);
+            if (threadIdx.x < 32) reconstruct_warp(s, topbuf, tau + j0, blockIdx.x == 0, Tp, Vtp, ldt);
             __syncthreads();
 #pragma unroll
             for (int i = 0; i < RPT; ++i)
@@ -384,7 +405,7 @@ __global__ void __launch_bounds__(GQ_THREADS, 1)
 
 template <int RPT>
 ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
-                      int64_t rows_per, int *fallback, cudaStream_t s) {
+                      int64_t rows_per, int *fallback, float *Tp, float *Vtp, int64_t ldt, cudaStream_t s) {
     auto fn = panel_gram_kernel<RPT>;
     const size_t dyn = sizeof(float) * GQ_LD * RPT * GQ_THREADS;
     static bool attr = false;
@@ -405,7 +426,7 @@ ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, 
     float *rec = top + 1024;
     CT_CUDA(cudaMemsetAsync(bar, 0, 256, s));
     DevStatus *st = device_status();
-    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &top, &bar, &fallback, &st, &rows_per};
+    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &top, &bar, &fallback, &st, &rows_per, &Tp, &Vtp, &ldt};
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(GQ_THREADS), args, dyn, s));
     count_launch();
     return CT_OK;
@@ -418,12 +439,13 @@ size_t panel_gram_ws_bytes(int G) {
 }
 
 ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
-                     int64_t rows_per, int rpt, int *fallback, cudaStream_t s) {
+                     int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
+                     cudaStream_t s) {
     switch (rpt) {
-        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
-        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
-        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
-        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, G, rows_per, fallback, s);
+        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
         default: return CT_ERR_ARG;
     }
 }

@@ -164,13 +164,17 @@ ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, 
             const int wq = (int)std::min<int64_t>(MB, j + w - q);
             for (int64_t p = q; p < q + wq; p += nb) {
                 const int wp = (int)std::min<int64_t>(nb, q + wq - p);
-                CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s,
-                                f->gram_panel));
-                // T_p of this panel goes straight into its diagonal block of T_J.
+                // T_p of this panel goes straight into its diagonal block of T_J;
+                // the Gram panel kernels write it with the top of V
                 void *Tp = at(TJ, p - j, p - j, NB, es);
-                CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
-                CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
-                CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
+                bool made = false;
+                CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s,
+                                f->gram_panel, Tp, Vtp, NB, &made));
+                if (!made) {
+                    CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
+                    CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
+                    CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
+                }
                 const int64_t ncols_in = q + wq - (p + wp);
                 if (ncols_in > 0)
                     CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,

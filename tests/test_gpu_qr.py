@@ -301,3 +301,25 @@ def test_gram_panel_matches_column_panel(oracle_mod, precision, tol, ns, nv, nb,
     scale = np.abs(Rc).max()
     assert np.abs(sg[:, None] * Rg - Rc).max() <= 2e-3 * scale
     assert not np.array_equal(VRg, VRc)  # a different kernel ran
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_fallback_panels_refine(oracle_mod, precision):
+    """Panels too ill-conditioned for the Gram route (32x32 image, 30 views,
+    no regularisation: condition number about 3e4) fall back to the
+    column-by-column sweep, which then also builds the panel's T and the top
+    of its V; the refined solve reaches the oracle solution as with the
+    sweep alone."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g, csr, X, B = _case(O, 32, 30, 46, 0.0, 3, False)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    for column in (False, True):
+        sysg = ct.System(ct.make_geometry(32, 30, 46, 0.0), "fp32")
+        F = sysg.factor(precision, nb_outer=64, column_panel=column)
+        Xg = F.solve(Bt, max_iter=12, tol=1e-12, allow_noconv=True).cpu().numpy().T
+        print(precision, column, rel_err_cols(Xg, Xo).max(), F.last_info)
+        assert rel_err_cols(Xg, Xo).max() <= 1e-8
