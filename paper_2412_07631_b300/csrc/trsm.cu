@@ -148,8 +148,12 @@ __global__ void scatter_diag_kernel(int64_t nblk, int TB, int SB, const T *Rinv,
 // doubling from the TB x TB inverses,
 //   inv([A B; 0 C]) = [inv(A), -inv(A) B inv(C); 0, inv(C)],
 // with the products on the FP32 CUDA cores (exact transposes of each other
-// are kept for R^-1 and R^-T, so the two applications stay adjoint).
+// are kept for R^-1 and R^-T, so the two applications stay adjoint).  The
+// superblocks are independent: their chains of small products run on
+// kInvStreams side streams (each with its own scratch), forked from and
+// joined back to the caller's stream.
 static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
+    constexpr int kInvStreams = 8;
     const int TB = f->trsm_tb;
     const int64_t n = f->n;
     const int SB = (int)std::min<int64_t>(1024, round_up(n, TB));
@@ -162,31 +166,60 @@ static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
                                                               (float *)f->RinvB);
     count_launch();
     CT_CUDA(cudaGetLastError());
-    CT_TRY(f->misc2.ensure(es * blk));
-    void *Y = f->misc2.ptr;
     auto inv_at = [&](int64_t t, int64_t r, int64_t c) {
         return (char *)f->RinvB + es * (t * blk + (size_t)r + (size_t)c * SB);
     };
-    for (int64_t b = TB; b < SB; b *= 2) {
-        for (int64_t t = 0; t < nsb; ++t) {
-            const int64_t s0 = t * SB, s1 = std::min<int64_t>(n, s0 + SB);
-            for (int64_t p = s0; p + b < s1; p += 2 * b) {
-                const int64_t bb = std::min<int64_t>(b, s1 - p - b);
-                // Y = R[p:p+b, p+b:p+b+bb] inv(C)
-                GemmArgs g1{GEMM_F32, false, false, b, bb, bb, 1.0,
-                            (char *)f->Rm + es * (size_t)(p + (p + b) * f->ldr), f->ldr,
-                            inv_at(t, p + b - s0, p + b - s0), SB, 0.0, Y, SB};
-                CT_TRY(gemm(g1, f->trsm_ws, s));
-                // inv block (p, p+b) = -inv(A) Y
-                GemmArgs g2{GEMM_F32, false, false, b, bb, b, -1.0, inv_at(t, p - s0, p - s0), SB, Y, SB,
-                            0.0, inv_at(t, p - s0, p + b - s0), SB};
-                CT_TRY(gemm(g2, f->trsm_ws, s));
-            }
+    const int ns = (int)std::min<int64_t>(kInvStreams, nsb);
+    Scratch ws[kInvStreams], ys[kInvStreams];
+    cudaStream_t st[kInvStreams] = {};
+    cudaEvent_t ev[kInvStreams + 1] = {};
+    ct_status rc = CT_OK;
+    auto run = [&]() -> ct_status {
+        CT_CUDA(cudaEventCreateWithFlags(&ev[kInvStreams], cudaEventDisableTiming));
+        CT_CUDA(cudaEventRecord(ev[kInvStreams], s));
+        for (int i = 0; i < ns; ++i) {
+            CT_CUDA(cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking));
+            CT_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+            CT_CUDA(cudaStreamWaitEvent(st[i], ev[kInvStreams], 0));
+            CT_TRY(ys[i].ensure(es * blk));
         }
+        for (int64_t t = 0; t < nsb; ++t) {
+            const int i = (int)(t % ns);
+            void *Y = ys[i].ptr;
+            const int64_t s0 = t * SB, s1 = std::min<int64_t>(n, s0 + SB);
+            for (int64_t b = TB; b < SB; b *= 2) {
+                for (int64_t p = s0; p + b < s1; p += 2 * b) {
+                    const int64_t bb = std::min<int64_t>(b, s1 - p - b);
+                    // Y = R[p:p+b, p+b:p+b+bb] inv(C)
+                    GemmArgs g1{GEMM_F32, false, false, b, bb, bb, 1.0,
+                                (char *)f->Rm + es * (size_t)(p + (p + b) * f->ldr), f->ldr,
+                                inv_at(t, p + b - s0, p + b - s0), SB, 0.0, Y, SB};
+                    CT_TRY(gemm(g1, ws[i], st[i]));
+                    // inv block (p, p+b) = -inv(A) Y
+                    GemmArgs g2{GEMM_F32, false, false, b, bb, b, -1.0, inv_at(t, p - s0, p - s0), SB, Y, SB,
+                                0.0, inv_at(t, p - s0, p + b - s0), SB};
+                    CT_TRY(gemm(g2, ws[i], st[i]));
+                }
+            }
+            CT_TRY(transpose_any(0, (char *)f->RinvB + es * t * blk, SB, 0, (char *)f->RinvTB + es * t * blk,
+                                 SB, SB, SB, st[i]));
+        }
+        for (int i = 0; i < ns; ++i) {
+            CT_CUDA(cudaEventRecord(ev[i], st[i]));
+            CT_CUDA(cudaStreamWaitEvent(s, ev[i], 0));
+        }
+        return CT_OK;
+    };
+    rc = run();
+    // the side streams' work is complete before their scratch goes away
+    for (int i = 0; i < ns; ++i)
+        if (st[i]) cudaStreamSynchronize(st[i]);
+    for (int i = 0; i < ns; ++i) {
+        if (st[i]) cudaStreamDestroy(st[i]);
+        if (ev[i]) cudaEventDestroy(ev[i]);
     }
-    for (int64_t t = 0; t < nsb; ++t)
-        CT_TRY(transpose_any(0, (char *)f->RinvB + es * t * blk, SB, 0, (char *)f->RinvTB + es * t * blk,
-                             SB, SB, SB, s));
+    if (ev[kInvStreams]) cudaEventDestroy(ev[kInvStreams]);
+    CT_TRY(rc);
     f->trsm_sb = SB;
     return CT_OK;
 }
