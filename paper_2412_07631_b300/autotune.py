@@ -15,7 +15,7 @@ import json
 import os
 import time
 
-DEFAULT_CANDIDATES = (768, 1024, 1280)
+DEFAULT_CANDIDATES = (1024, 1536, 2048, 2560)
 
 
 def cache_path() -> str:

@@ -526,7 +526,7 @@ ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_fact
     f->lda = sys->lda;
     int nb = o.nb_inner > 0 ? o.nb_inner : (f->fp64 ? 16 : 32);
     nb = std::min(nb, 32);
-    int NB = o.nb_outer > 0 ? o.nb_outer : (f->fp64 ? 32 : (f->kind == GEMM_F32 ? 128 : (f->upd_kind == GEMM_BF16 ? 1280 : 1024)));
+    int NB = o.nb_outer > 0 ? o.nb_outer : (f->fp64 ? 32 : (f->kind == GEMM_F32 ? 128 : (f->upd_kind == GEMM_BF16 ? 2048 : 1536)));
     NB = (int)round_up(std::max(NB, nb), nb);
     if (NB % 32) NB = (int)round_up(NB, 32);
     f->nb = nb;

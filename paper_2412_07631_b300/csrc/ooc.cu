@@ -491,7 +491,7 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
     f->n = sys->n;
     f->m = sys->m;
     f->lda = sys->lda;
-    int NB = o.nb_outer > 0 ? o.nb_outer : (f->fp64 ? 32 : (f->kind == GEMM_F32 ? 128 : (f->upd_kind == GEMM_BF16 ? 1280 : 1024)));
+    int NB = o.nb_outer > 0 ? o.nb_outer : (f->fp64 ? 32 : (f->kind == GEMM_F32 ? 128 : (f->upd_kind == GEMM_BF16 ? 2048 : 1536)));
     if (d) NB = d->bw();
     NB = (int)round_up(std::max(NB, nb), nb);
     if (NB % 32) NB = (int)round_up(NB, 32);

@@ -12,20 +12,20 @@ def test_autotune_picks_fastest_and_caches(tmp_path):
 
     def timer(geom, prec, nb):
         calls.append(nb)
-        return {768: 9.0, 1024: 7.5, 1280: 8.0}[nb]
+        return {1024: 9.0, 1536: 7.5, 2048: 8.0, 2560: 8.5}[nb]
 
     path = str(tmp_path / "tune.json")
-    assert autotune.outer_block(g, "tf32", path=path, timer=timer) == 1024
-    assert sorted(calls) == [768, 1024, 1280]
+    assert autotune.outer_block(g, "tf32", path=path, timer=timer) == 1536
+    assert sorted(calls) == [1024, 1536, 2048, 2560]
     d = json.load(open(path))
     (entry,) = d.values()
-    assert entry["nb_outer"] == 1024 and set(entry["ms"]) == {"768", "1024", "1280"}
+    assert entry["nb_outer"] == 1536 and set(entry["ms"]) == {"1024", "1536", "2048", "2560"}
     # second call: from the cache, no timing
     calls.clear()
-    assert autotune.outer_block(g, "tf32", path=path, timer=timer) == 1024
+    assert autotune.outer_block(g, "tf32", path=path, timer=timer) == 1536
     assert calls == []
     # another precision or geometry is a different key
-    assert autotune.outer_block(g, "bf16", path=path, timer=lambda *a: 1.0) == 768
+    assert autotune.outer_block(g, "bf16", path=path, timer=lambda *a: 1.0) == 1024
     assert len(json.load(open(path))) == 2
 
 
