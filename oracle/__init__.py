@@ -28,6 +28,7 @@ from __future__ import annotations
 import ctypes as C
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -37,9 +38,12 @@ _lib = None
 
 
 def lib():
+    """The compiled oracle.  CTQR_ORACLE_LIB names another build of
+    ctqr_oracle.c instead (the mutation tests load deliberately broken copies
+    this way to show that the pins reject them)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        _lib = C.CDLL(os.environ.get("CTQR_ORACLE_LIB") or _build.build())
         dp = C.POINTER(C.c_double)
         i32p = C.POINTER(C.c_int32)
         i64p = C.POINTER(C.c_int64)
