@@ -28,7 +28,8 @@ struct ct_system_s {
     float *val32 = nullptr, *csc_val32 = nullptr;  // FP32 copies (inner refinement solves)
     ctqr::Scratch tmp, tmp2;
     ctqr::SparseSys sparse() const {
-        return {m, n, nnz, geom.sqrt_lambda, row_ptr, col, val, col_ptr, csc_row, csc_val, val32, csc_val32};
+        return {m, n, nnz, geom.sqrt_lambda, row_ptr, col, val, col_ptr, csc_row, csc_val, val32, csc_val32,
+                (int64_t)geom.n_bins, (int64_t)geom.n_side};
     }
 };
 

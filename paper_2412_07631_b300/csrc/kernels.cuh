@@ -163,6 +163,8 @@ struct SparseSys {
     const double *csc_val;
     const float *val32;      // FP32 copies of val / csc_val (NULL until made)
     const float *csc_val32;
+    int64_t n_bins;          // ray rows are i = v * n_bins + d (0: no such order known)
+    int64_t n_side;          // pixel columns are j = iy * n_side + ix (0: no such order known)
 };
 // Row-major (slice-fastest) k-column operands:  Y[i*k + s].
 // out = alpha*Y + beta*(A~ X)   (rows m+n if sqrt_lambda > 0, else m)
