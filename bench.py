@@ -3,9 +3,9 @@
 
 One step = the whole hot path for one batch: build the Siddon system matrix
 A~ = [A; sqrt(lambda) I] on the GPU, factor it by blocked Householder QR with
-TF32 tensor-core trailing updates (FP32 storage, FP64 column norms), and solve
-k noisy sinograms x = R^-1 Q^T b~ with FP64 Krylov refinement on the
-low-precision factors.
+BF16 (default) or TF32 tensor-core trailing updates (FP32 storage), and solve
+k noisy sinograms x = R^-1 Q^T b~ with FP64 refinement on the low-precision
+factors.
 
 Workload (default): 256 x 256 image (n = 65,536), 360 views x 364 bins
 (m = 131,040) + 65,536 regularisation rows (sqrt(lambda) = 0.05), 512
@@ -244,7 +244,27 @@ def cpu_oracle_sample(name, cols=None):
     fl = 2.0 * M * w * w - 2.0 / 3.0 * w ** 3 + 4.0 * M * w - w * w
     desc = (f"oracle plain Householder QR of the first {w} of {n} columns of A~ "
             f"({M} x {w}), Q^T applied to one sinogram, back-substitution")
-    return fl / dt / 1e12, dt, desc, os.cpu_count()
+    return fl / dt / 1e12, dt, desc, oracle_threads()
+
+
+def oracle_threads():
+    """Threads the oracle's OpenMP loops use: OMP_NUM_THREADS if set, else the
+    CPUs this process may run on."""
+    env = os.environ.get("OMP_NUM_THREADS", "").split(",")[0].strip()
+    if env.isdigit() and int(env) > 0:
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def workload_config(name):
+    """The `config` keys both arms report for a workload."""
+    ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
+    M, n, _, _ = flops_of(ns, nv, nb, sl, k)
+    return {"workload": workload_desc(name), "n_side": ns, "views": nv, "bins": nb, "rows": M,
+            "unknowns": n, "slices": k}
 
 
 # ---------------------------------------------------------------------------
@@ -342,7 +362,8 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_desc(args.workload)},
+                "config": dict(workload_config(args.workload), precision="fp64 (oracle)",
+                               parallelism="host cores"),
                 "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                                  "sample": desc},
                 "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -505,8 +526,7 @@ def main():
                       "bf16x3": "bf16x3 split trailing updates (FP32 storage, tf32 solve) + f64 refinement",
                       "fp32": "f32", "fp64": "f64"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": workload_desc(args.workload), "n_side": ns, "views": nv,
-                       "bins": nb, "rows": M, "unknowns": n, "slices": k,
+            "config": {**workload_config(args.workload),
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "out_of_core": ({"device_budget_gb": args.ooc_budget_gb,
                                         "host_matrix": (("file on local disk + %.0f GB pinned block cache"

@@ -1,0 +1,72 @@
+"""bench.py's host-side contract, on the CPU: the reference arm (the oracle
+timed on the host cores, one bounded sample of the 256x256 workload per
+step) prints one JSON line with the keys the benchmark contract asks for,
+on the same metric, unit and workload as the GPU arm; ranks other than 0
+print nothing; the flop counts follow their closed forms."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _run(*args, env=None):
+    e = dict(os.environ, **(env or {}))
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, env=e,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_line():
+    res = _run("--impl", "reference", "--steps", "1", "--warmup", "0")
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == "TFLOP/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
+    assert d["config"]["workload"] == bench.workload_desc("c3")
+    assert {k: d["config"][k] for k in ("n_side", "views", "bins", "rows", "unknowns", "slices")} == \
+        {"n_side": 256, "views": 360, "bins": 364, "rows": 196576, "unknowns": 65536, "slices": 512}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    res = _run("--impl", "reference", "--steps", "1", "--warmup", "0",
+               env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert res.returncode == 0, res.stderr[-2000:]
+    assert res.stdout.strip() == ""
+
+
+def test_oracle_threads_follow_omp_num_threads(monkeypatch):
+    monkeypatch.setenv("OMP_NUM_THREADS", "3")
+    assert bench.oracle_threads() == 3
+    monkeypatch.delenv("OMP_NUM_THREADS")
+    assert bench.oracle_threads() >= 1
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3"])
+def test_flop_counts(name):
+    ns, nv, nb, sl, k, _, _ = bench.WORKLOADS[name]
+    n, m = ns * ns, nv * nb
+    M, n2, qr_d, solve_d = bench.flops_of(ns, nv, nb, sl, k, dense=True)
+    assert (M, n2) == (m + (n if sl > 0 else 0), n)
+    assert qr_d == pytest.approx(2.0 * M * n * n - 2.0 / 3.0 * n ** 3, rel=1e-12)
+    assert solve_d == pytest.approx(k * (4.0 * M * n - n * n), rel=1e-12)
+    _, _, qr_s, solve_s = bench.flops_of(ns, nv, nb, sl, k)
+    if sl > 0:
+        # column j's reflector spans the m - j ray rows below the diagonal and
+        # the j + 1 regularisation rows filled so far: 4 (m + 1) flops per
+        # remaining column, summed over j
+        assert qr_s == pytest.approx(sum(4.0 * (m + 1) * (n - j - 1) for j in range(n)), rel=1e-12)
+        assert qr_s < qr_d
+    else:
+        assert (qr_s, solve_s) == (qr_d, solve_d)
