@@ -156,7 +156,7 @@ static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
     constexpr int kInvStreams = 8;
     const int TB = f->trsm_tb;
     const int64_t n = f->n;
-    const int SB = (int)std::min<int64_t>(1024, round_up(n, TB));
+    const int SB = (int)std::min<int64_t>(2048, round_up(n, TB));
     const int64_t nsb = ceil_div(n, SB), nblk = ceil_div(n, TB);
     const size_t es = f->es(), blk = (size_t)SB * SB;
     CT_CUDA(cudaMalloc(&f->RinvB, es * nsb * blk));
