@@ -207,7 +207,8 @@ CT_API ct_status ct_system_export(ct_system sys, int64_t *row_ptr, int32_t *col_
                            void *dense, int64_t ldd);
 
 /* P = A X on the device (forward projection with the CSR, FP64):
- * X: device double, n x k, ldx >= n; P: device double, m x k, ldp >= m. */
+ * X: device double, n x k, ldx >= n; P: device double, m x k, ldp >= m.
+ * k = 0 does nothing (X and P may then be NULL). */
 CT_API ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx, int32_t k, double *P,
                              int64_t ldp, void *stream);
 
@@ -245,7 +246,9 @@ CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau)
  * each step computes the residual b~ - A~ x and A~^T of it in FP64 with the
  * sparse Siddon matrix, then adds a correction found by FP32 CGLS on the
  * problem preconditioned with R~ (the low-precision factor), until the
- * stopping quantity of opts->refine_tol is met or refine_max_iter steps.  opts may be NULL (factor's precision, defaults).  info may be NULL.
+ * stopping quantity of opts->refine_tol is met or refine_max_iter steps.
+ * opts may be NULL (factor's precision, defaults).  info may be NULL.  k = 0
+ * does nothing (B and X may then be NULL).
  * Synchronises `stream` at the end (to read the convergence state).
  * Errors: CT_ERR_ARG, CT_ERR_NOCONV (X still holds the best iterate),
  * CT_ERR_NONFINITE, CT_ERR_TIMEOUT, CT_ERR_OOM, CT_ERR_CUDA. */

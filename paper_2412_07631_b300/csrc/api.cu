@@ -472,8 +472,9 @@ ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau) {
 
 ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx, int32_t k, double *P,
                              int64_t ldp, void *stream) {
-    if (!sys || !X || !P || k < 0 || ldx < sys->n || ldp < sys->m) return CT_ERR_ARG;
+    if (!sys || k < 0 || ldx < sys->n || ldp < sys->m) return CT_ERR_ARG;
     if (k == 0) return CT_OK;
+    if (!X || !P) return CT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     // column-major in, column-major out: go through slice-fastest staging.
     double *xr = nullptr, *pr = nullptr;
