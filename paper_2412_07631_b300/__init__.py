@@ -57,7 +57,8 @@ SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info"
            "ct_solve_adjoint", "ct_system_free", "ct_factor_free", "ct_gemm", "ct_stats_reset",
            "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc", "ct_factor_save",
            "ct_factor_load", "ct_build_system_host", "ct_qr_factor_ooc", "ct_host_cache_release",
-           "ct_build_system_disk", "ct_system_open_disk", "ct_disk_progress", "ct_disk_stats"]
+           "ct_build_system_disk", "ct_system_open_disk", "ct_disk_progress", "ct_disk_stats",
+           "ct_selftest_wait_timeout"]
 
 
 def lib_path() -> str:
@@ -102,6 +103,12 @@ def lib():
     L.ct_stats_reset.argtypes = [I32]
     L.ct_stats_read.argtypes = [C.POINTER(I64), vp, vp, vp, vp]
     L.ct_stats_dump.argtypes = [C.c_char_p]
+    L.ct_build_system_disk.argtypes = [C.POINTER(Geometry), C.c_int, C.c_char_p, I32, C.c_size_t, vp,
+                                       C.POINTER(vp)]
+    L.ct_system_open_disk.argtypes = [C.c_char_p, C.c_size_t, vp, C.POINTER(vp)]
+    L.ct_disk_progress.argtypes = [vp, C.POINTER(I32), C.POINTER(I64)]
+    L.ct_disk_stats.argtypes = [I32] + [C.POINTER(I64)] * 5 + [C.POINTER(C.c_double)] * 2
+    L.ct_selftest_wait_timeout.argtypes = [vp]
     for name in SYMBOLS:
         if name not in ("ct_status_str", "ct_last_error", "ct_system_free", "ct_factor_free"):
             getattr(L, name).restype = C.c_int
@@ -407,6 +414,14 @@ class CTSolve:
 
 STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other",
                 "spmm_fp32", "tc_gemm_bf16"]
+
+
+def selftest_wait_timeout(stream=None) -> str:
+    """Run one device wait that cannot complete (a grid meet of a one-CTA grid
+    that expects two) and return the status name the library reports for it:
+    "CT_ERR_TIMEOUT" once the bounded wait has given up (about 4 s)."""
+    st = lib().ct_selftest_wait_timeout(_stream(stream))
+    return lib().ct_status_str(st).decode()
 
 
 def disk_stats(reset: bool = False) -> dict:

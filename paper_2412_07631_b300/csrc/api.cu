@@ -470,6 +470,8 @@ ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau) {
     return CT_OK;
 }
 
+ct_status ct_selftest_wait_timeout(void *stream) { return wait_selftest((cudaStream_t)stream); }
+
 ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx, int32_t k, double *P,
                              int64_t ldp, void *stream) {
     if (!sys || k < 0 || ldx < sys->n || ldp < sys->m) return CT_ERR_ARG;

@@ -108,6 +108,9 @@ size_t panel_gram_ws_bytes(int G);
 ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
                      int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
                      cudaStream_t s);
+// One grid meet that cannot complete (failure-detection check): returns
+// CT_ERR_TIMEOUT once the bounded wait has given up.
+ct_status wait_selftest(cudaStream_t s);
 // Copy the unit-lower-triangular top block of V (nb x nb at A[j0, j0]) into
 // Vtop (leading dimension ldv): ones on the diagonal, zeros above.
 ct_status extract_vtop(bool fp64, const void *A, int64_t lda, int64_t j0, int nb, void *Vtop,

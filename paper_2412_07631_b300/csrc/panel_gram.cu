@@ -79,6 +79,13 @@ __device__ bool grid_meet(unsigned *ctr, unsigned G, DevStatus *st, int site, in
     return *ok_s != 0;
 }
 
+// A grid meet that cannot complete: one CTA waits for a second that is never
+// launched, so the bounded wait gives up (failure-detection check).
+__global__ void meet_timeout_kernel(unsigned *ctr, DevStatus *st) {
+    __shared__ int ok_s;
+    grid_meet(ctr, 2u, st, 90, &ok_s);
+}
+
 struct GramShared {
     float g[32][33];             // Gram totals (symmetric), then scratch
     float W[32][33];             // Q1 and its eliminations
@@ -433,6 +440,22 @@ ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, 
 }
 
 }  // namespace
+
+ct_status wait_selftest(cudaStream_t s) {
+    CT_TRY(check_device_status(s));  // start from a clear status word
+    unsigned *ctr = nullptr;
+    CT_CUDA(cudaMalloc((void **)&ctr, 256));
+    ct_status st = CT_OK;
+    if (cudaMemsetAsync(ctr, 0, 256, s) != cudaSuccess) st = CT_ERR_CUDA;
+    if (st == CT_OK) {
+        meet_timeout_kernel<<<1, 32, 0, s>>>(ctr, device_status());
+        count_launch();
+        st = cudaGetLastError() == cudaSuccess ? check_device_status(s) : CT_ERR_CUDA;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(ctr);
+    return st;
+}
 
 size_t panel_gram_ws_bytes(int G) {
     return 256 + sizeof(double) * 2 * GQ_TRI + sizeof(float) * (1024 + 2 * (size_t)G * GQ_TRI);
