@@ -66,6 +66,22 @@ MUTANTS = [
 ]
 
 
+# Mistakes planted in the oracle's Python layer (oracle/__init__.py): the
+# package is copied, patched, and loaded by the pin suites in place of the
+# original (the compiled C part is the unmodified one).
+PY_MUTANTS = [
+    ("certificate_lambda_not_squared", "lam = g.sqrt_lambda ** 2\n    xn", "lam = g.sqrt_lambda\n    xn", 0),
+    ("certificate_without_lambda", "np.linalg.norm(gg, axis=0) / lam / np.maximum(xn, 1e-300)",
+     "np.linalg.norm(gg, axis=0) / np.maximum(xn, 1e-300)", 0),
+    ("rhs_zero_rows_on_top", "Bt[: g.m] = B", "Bt[g.rows - g.m:] = B", 0),
+    ("lapack_route_transposed_solve", "lower=0, trans=0", "lower=0, trans=1", 0),
+    ("joseph_bin_offset", "t = (d - 0.5 * (g.n_bins - 1)) * g.bin_width",
+     "t = (d - 0.5 * g.n_bins) * g.bin_width", 0),
+    ("psnr_amplitude_form", "10.0 * math.log10(max_val ** 2 / mse)", "20.0 * math.log10(max_val ** 2 / mse)", 0),
+    ("snr_inverted", "10.0 * math.log10(sig / err)", "10.0 * math.log10(err / sig)", 0),
+]
+
+
 def _plant(text, old, new, occurrence):
     at = -1
     for _ in range(occurrence + 1):
@@ -82,8 +98,10 @@ def _build(tmp_path, name, text):
     return ob.compile_source(str(src), str(tmp_path / f"lib{name}.so"))
 
 
-def _run_pins(lib):
+def _run_pins(lib, pkg=None):
     env = dict(os.environ, CTQR_ORACLE_LIB=lib)
+    if pkg:
+        env["CTQR_ORACLE_PKG"] = pkg
     return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PIN_SUITES],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
@@ -99,3 +117,27 @@ def test_pins_reject_mutant(tmp_path, name, old, new, occurrence):
     res = _run_pins(_build(tmp_path, name, text))
     # 1: some pin failed (not a collection or usage error, which would be 2-4)
     assert res.returncode == 1, f"{name} survived the pins:\n{res.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name,old,new,occurrence", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_reject_python_mutant(tmp_path, name, old, new, occurrence):
+    sys.path.insert(0, ROOT)
+    from oracle import build as ob
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    src = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    (pkg / "__init__.py").write_text(_plant(src, old, new, occurrence))
+    (pkg / "build.py").write_text(open(os.path.join(ROOT, "oracle", "build.py")).read())
+    res = _run_pins(ob.build(), str(pkg))
+    assert res.returncode == 1, f"{name} survived the pins:\n{res.stdout[-2000:]}"
+
+
+def test_unmodified_python_copy_passes_the_pins(tmp_path):
+    sys.path.insert(0, ROOT)
+    from oracle import build as ob
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    for f in ("__init__.py", "build.py"):
+        (pkg / f).write_text(open(os.path.join(ROOT, "oracle", f)).read())
+    res = _run_pins(ob.build(), str(pkg))
+    assert res.returncode == 0, res.stdout[-2000:]

@@ -118,6 +118,28 @@ def test_certificate_bounds_true_error(oracle_mod):
     assert O.certificate(g, csr, b, Xs)[0] <= 1e-10
 
 
+def test_certificate_closed_form_along_singular_vectors(oracle_mod):
+    """For x = x* + e with e along a right singular vector v of A~ (singular
+    value s), A~^T(b~ - A~ x) = -s^2 e, so the certificate equals
+    s^2 ||e|| / (lambda ||x||) exactly; along the smallest singular vector the
+    bound ||e|| / ||x|| <= certificate is nearly attained.  The singular
+    vectors come from LAPACK's SVD of the dense A~."""
+    O = oracle_mod
+    g = O.Geometry(16, 24, 24, sqrt_lambda=0.05)
+    csr = O.siddon_csr(g)
+    A = O.dense_system(g, csr)
+    x = synth.phantom_batch(16, 1, 6)
+    b = synth.poisson_sinogram(O.forward(csr, x), 16, 1e3, seed=5)
+    Xs = O.normal_eq_ld(g, csr, b)
+    _, S, Vt = np.linalg.svd(A, full_matrices=False)
+    lam = g.sqrt_lambda ** 2
+    for i in (len(S) - 1, len(S) // 2, 0):
+        eps = 1e-3 * np.linalg.norm(Xs)
+        Xp = Xs + eps * Vt[i][:, None]
+        want = S[i] ** 2 * eps / (lam * np.linalg.norm(Xp))
+        assert abs(O.certificate(g, csr, b, Xp)[0] / want - 1.0) <= 1e-9
+
+
 def test_adjoint_matches_normal_equation_form(oracle_mod):
     """grad_b of <x(b), y> is [Q R^{-T} y]_{0:m}; the same vector is
     A (A~^T A~)^{-1} y, formed here from the long-double normal equations."""

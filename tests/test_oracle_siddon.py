@@ -260,3 +260,19 @@ def test_joseph_same_line_same_row(oracle_mod):
         assert set(a) == set(b)
         for k in a:
             assert abs(a[k] - b[k]) <= 1e-12
+
+
+@pytest.mark.parametrize("n_side,n_views,n_bins", [(32, 60, 46), (16, 24, 20)])
+def test_joseph_axis_views_equal_siddon(oracle_mod, n_side, n_views, n_bins):
+    """At 0 and 90 degrees every ray runs along a pixel row (column) through
+    the pixel centres, where both projectors are exact: Joseph's weight and
+    Siddon's length are 1 in each pixel the ray crosses, so the two system
+    matrices agree on those views entry for entry (and differ elsewhere)."""
+    O = oracle_mod
+    As = O.dense_system(O.Geometry(n_side, n_views, n_bins))
+    Aj = O.dense_system(O.Geometry(n_side, n_views, n_bins, projector="joseph"))
+    for v in (0, n_views // 2):
+        rows = slice(v * n_bins, (v + 1) * n_bins)
+        np.testing.assert_array_equal(Aj[rows], As[rows])
+        assert np.count_nonzero(Aj[rows]) == n_side * n_side
+    assert not np.array_equal(Aj, As)
