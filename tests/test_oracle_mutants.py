@@ -63,6 +63,14 @@ MUTANTS = [
     ("residual_sign", "acc -= (long double)val[q] * (long double)x[col_idx[q] + s * ldx];",
      "acc += (long double)val[q] * (long double)x[col_idx[q] + s * ldx];", 0),
     ("certificate_drops_lambda_rows", "gs[j] += (long double)sqrt_lambda * rj;", "gs[j] += 0.0L * rj;", 0),
+    # more: clipping, norms, spacing, brute force
+    ("ray_exit_from_near_side", "s_out = fmin(s_out, fmax(sa, sb));", "s_out = fmin(s_out, fmin(sa, sb));", 1),
+    ("norm_drops_head", "double norm = sqrt(alpha * alpha + ss);", "double norm = sqrt(ss);", 0),
+    ("rt_solve_drops_diagonal", "b[j] = acc / A[j + j * lda];", "b[j] = acc;", 0),
+    ("joseph_fraction_sign", "const double f = fp - fl;", "const double f = fl - fp;", 0),
+    ("fan_detector_spacing", "(fan_deg / (double)(n_det - 1))", "(fan_deg / (double)n_det)", 0),
+    ("cholesky_drops_square", "d -= G[j + p * n] * G[j + p * n];", "d -= G[j + p * n];", 0),
+    ("normal_eq_rhs_slice_zero", "(long double)b[i + s * ldb];", "(long double)b[i];", 0),
 ]
 
 
