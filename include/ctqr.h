@@ -351,19 +351,6 @@ CT_API ct_status ct_system_open_disk(const char *path, size_t host_cache_bytes, 
  * factor has taken it over). */
 CT_API ct_status ct_disk_progress(ct_system sys, int32_t *state, int64_t *done_cols);
 
-/* Failure detection check.  Every device-side spin wait of the library
- * (grid meets of the cooperative panel kernels, mbarrier phases of the
- * tensor-core GEMMs) gives up after 4 s, records DEV_TIMEOUT and the site in
- * the device status word and lets its kernel return, so that a stalled
- * launch surfaces as CT_ERR_TIMEOUT instead of a hang.  This call runs the
- * panel kernels' grid meet on a grid that cannot complete it (one CTA
- * waiting for a second that is never launched) and returns what the next
- * synchronisation point reads: CT_ERR_TIMEOUT after about 4 s, with
- * ct_last_error naming site 90.  The status word is cleared on return and
- * the context stays usable.  The paper has no counterpart.
- * Errors: CT_ERR_TIMEOUT (expected), CT_ERR_CUDA, CT_ERR_OOM. */
-CT_API ct_status ct_selftest_wait_timeout(void *stream);
-
 /* Process-wide disk-tier counters since the last reset: bytes read and
  * written, cache hits (block resident), prefetched (read already in flight),
  * misses (read on demand), and the summed seconds of the I/O threads' reads
@@ -396,8 +383,27 @@ CT_API ct_status ct_factor_save(ct_factor f, const char *path);
  * geometry or precision mismatch), CT_ERR_OOM, CT_ERR_CUDA. */
 CT_API ct_status ct_factor_load(ct_system sys, const char *path, void *stream, ct_factor *out);
 
+/* Release a system or a factor and what the library allocated for it.  A
+ * factor owns the dense storage it took over from its system (V and R); a
+ * refining factor reads its system's sparse rows, so free a factor before
+ * its system.  Pinned host blocks of out-of-core systems go to the reuse
+ * cache (see ct_host_cache_release); a disk-backed file is closed and stays
+ * on disk.  NULL is ignored. */
 CT_API void ct_system_free(ct_system sys);
 CT_API void ct_factor_free(ct_factor f);
+
+/* Failure detection check.  Every device-side spin wait of the library
+ * (grid meets of the cooperative panel kernels, mbarrier phases of the
+ * tensor-core GEMMs) gives up after 4 s, records DEV_TIMEOUT and the site in
+ * the device status word and lets its kernel return, so that a stalled
+ * launch surfaces as CT_ERR_TIMEOUT instead of a hang.  This call runs the
+ * panel kernels' grid meet on a grid that cannot complete it (one CTA
+ * waiting for a second that is never launched) and returns what the next
+ * synchronisation point reads: CT_ERR_TIMEOUT after about 4 s, with
+ * ct_last_error naming site 90.  The status word is cleared on return and
+ * the context stays usable.  The paper has no counterpart.
+ * Errors: CT_ERR_TIMEOUT (expected), CT_ERR_CUDA, CT_ERR_OOM. */
+CT_API ct_status ct_selftest_wait_timeout(void *stream);
 
 /* ---- Benchmark accounting (not part of the method) ---------------------- */
 
