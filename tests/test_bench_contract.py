@@ -70,3 +70,27 @@ def test_flop_counts(name):
         assert qr_s < qr_d
     else:
         assert (qr_s, solve_s) == (qr_d, solve_d)
+
+
+def test_oracle_certificate_bounds_the_error(monkeypatch):
+    """The bench's error-vs-oracle figure on a small geometry: it is tiny for
+    the oracle's own least-squares solution, and it bounds the true error of
+    a perturbed solution."""
+    import numpy as np
+    import oracle as O
+    monkeypatch.setitem(bench.WORKLOADS, "t12", (12, 20, 18, 0.05, 3, None, 4))
+    g = bench.oracle_geometry_of(O, "t12")
+    csr = O.siddon_csr(g)
+    rng = np.random.default_rng(3)
+    B = rng.random((g.m, 3))
+    Xs, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    assert bench.oracle_certificate("t12", B.T, Xs) <= 1e-10
+    # the bound is ||A~^T A~ e|| / (lambda ||x||): at least the error, at most
+    # sigma_max^2 / lambda times it, and linear in the perturbation e
+    E = rng.standard_normal(Xs.shape)
+    Xp = Xs + 1e-3 * E
+    err = np.linalg.norm(Xp - Xs, axis=0) / np.linalg.norm(Xp, axis=0)
+    bound = bench.oracle_certificate("t12", B.T, Xp)
+    assert err.max() <= bound
+    Xq = Xs + 1e-5 * E
+    assert bench.oracle_certificate("t12", B.T, Xq) == pytest.approx(bound / 100, rel=2e-2)

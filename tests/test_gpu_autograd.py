@@ -1,11 +1,12 @@
-"""Differentiation through the reconstruction (the benchmark spec's third form):
-the solve as a torch.autograd.Function whose backward pass is the
-hand-written adjoint grad_b = [Q R^-T grad_x]_{0:m}, refined in FP64 for the
-TF32 factors.  Loss = mean squared error to the phantom.  Checks: central
-finite differences (h = 1e-3, FP64; the loss is quadratic in b, so the
-central difference is exact up to rounding) <= 1e-4 relative; an FP64
-reference gradient from the oracle (Q R^-T applied by the plain Householder
-route) <= 1e-6; the adjoint identity <solve(b), y> = <b, adjoint(y)>."""
+"""Differentiation through the reconstruction (not in the paper; the solve
+used as a layer of a trained model): the solve as a torch.autograd.Function
+whose backward pass is the hand-written adjoint grad_b = [Q R^-T grad_x]_{0:m},
+refined in FP64 for the TF32 factors.  Loss = mean squared error to the
+phantom.  Checks: central finite differences (h = 1e-3, FP64; the loss is
+quadratic in b, so the central difference is exact up to rounding) <= 1e-4
+relative; an FP64 reference gradient from the oracle (Q R^-T applied by the
+plain Householder route) <= 1e-6; the adjoint identity
+<solve(b), y> = <b, adjoint(y)>."""
 import numpy as np
 import pytest
 
