@@ -53,6 +53,9 @@ WORKLOADS = {
     # as the 256^2 workload's (131,072 rows) in a 2.2 GB matrix, for kernel
     # profiles on a small case
     "tall64": (64, 360, 364, 0.05, 64, 5e3, 10),
+    # the differentiation workload: the 128^2 geometry, 256 sinograms through
+    # the autograd solve layer (bench.py --diff)
+    "c4": (128, 180, 182, 0.05, 256, 1e4, 10),
 }
 FAN = {"fan256": (720.0, 30.0)}  # name: (source_dist, fan_deg)
 
@@ -314,6 +317,82 @@ def gemm_only(args):
                       "steps": args.steps, "warmup": args.warmup}))
 
 
+def diff_only(args):
+    """The differentiation workload: the 128x128 geometry (180 views x 182
+    bins + sqrt(lambda) = 0.05 I rows), a batch of 256 noisy sinograms through
+    the autograd solve layer (CTSolve): forward X = R^-1 Q^T b~ refined in
+    FP64, loss = mean squared error to the phantoms, backward grad_b =
+    [Q R^-T grad_x]_{0:m} refined in FP64.  The factorisation is made once,
+    untimed (the layer reuses it for every batch of the geometry); `warmup`
+    untimed and `steps` timed forward + backward passes, CUDA events on the
+    launching stream.  After timing, <grad_b, d> is checked against a
+    central difference of the loss along one random unit direction (h =
+    1e-3; the loss is quadratic in b).  One JSON line."""
+    import torch
+    import paper_2412_07631_b300 as ct
+    name = "c4"
+    ns, nv, nb, sl, k, i0, ne = WORKLOADS[name]
+    M, n, _, solve_fl = flops_of(ns, nv, nb, sl, k)
+    precision = args.precision
+    Xtrue, Bh = make_inputs(ct, torch, name)
+    io_dt = torch.float32 if precision == "fp32" else torch.float64
+    B = torch.from_numpy(Bh).to(io_dt).cuda()
+    Xt = torch.from_numpy(np.ascontiguousarray(Xtrue.T)).to(io_dt).cuda()
+    sysg = ct.System(geometry_of(ct, name), "fp64" if precision == "fp64" else "fp32")
+    F = sysg.factor(precision, nb_outer=args.nb_outer)
+    it, tol = args.max_iter, args.tol
+
+    def step():
+        Bv = B.detach().requires_grad_(True)
+        Xr = ct.CTSolve.apply(Bv, F, it, tol)
+        fwd = dict(F.last_info or {})
+        loss = ((Xr - Xt) ** 2).mean()
+        loss.backward()
+        return loss, Bv.grad, fwd, dict(F.last_info or {})
+
+    for _ in range(args.warmup):
+        step()
+    ct.stats_reset(False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = []
+    for _ in range(args.steps):
+        loss, grad, fwd, bwd = step()
+        infos.append((fwd, bwd))
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ct.stats_read()["launches"]
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    with torch.no_grad():
+        rng = np.random.default_rng(11)
+        d = torch.from_numpy(rng.standard_normal(tuple(B.shape))).to(io_dt).cuda()
+        d /= d.norm()
+        h = 1e-3
+        lp = ((F.solve((B + h * d).contiguous(), max_iter=it, tol=tol) - Xt) ** 2).mean().item()
+        lm = ((F.solve((B - h * d).contiguous(), max_iter=it, tol=tol) - Xt) ** 2).mean().item()
+        fd = (lp - lm) / (2 * h)
+        an = float((grad * d).sum())
+    F.free()
+    sysg.free()
+    print(json.dumps({
+        "mode": "differentiation (autograd solve layer, forward + backward)",
+        "workload": workload_desc(name), "precision": precision,
+        "slices_per_s": k / (ms * 1e-3), "ms_per_step": ms,
+        "tflops_direct": 2 * solve_fl / (ms * 1e-3) / 1e12,
+        "tflops_note": "algorithmic flops of one direct solve and one direct adjoint per slice "
+                       "(refinement not counted)",
+        "refine_iters": [[f.get("iterations"), b.get("iterations")] for f, b in infos],
+        "refine_inner_iters": [[f.get("inner_iterations"), b.get("inner_iterations")] for f, b in infos],
+        "backward_stop_measure": infos[-1][1].get("stop_measure") if infos else None,
+        "loss": float(loss.detach()), "fd_check": {"analytic": an, "central_difference": fd,
+                                          "rel": abs(fd - an) / max(abs(an), 1e-300)},
+        "gpu_launches": launches, "clocks": clk, "steps": args.steps, "warmup": args.warmup}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,8 +400,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="bf16",
-                    choices=["tf32", "bf16", "tf32x3", "bf16x3", "fp32", "fp64"])
+    ap.add_argument("--precision", default=None,
+                    choices=["tf32", "bf16", "tf32x3", "bf16x3", "fp32", "fp64"],
+                    help="default: bf16 for the full step, tf32 for --diff")
     ap.add_argument("--max-iter", type=int, default=40)
     ap.add_argument("--tol", type=float, default=5e-7)
     ap.add_argument("--no-e2e", action="store_true")
@@ -339,9 +419,16 @@ def main():
     ap.add_argument("--gemm", type=str, default="",
                     help="time only the GEMM engine on one shape, 'KIND:TA TB:M,N,K' (e.g. "
                          "'tf32:TN:768,16384,32768'), beta = 1; for kernel profiling")
+    ap.add_argument("--diff", action="store_true",
+                    help="time the autograd solve layer (forward + backward) on the 128x128 "
+                         "differentiation workload instead of the full step")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "tf32" if args.diff else "bf16"
     if args.gemm:
         return gemm_only(args)
+    if args.diff:
+        return diff_only(args)
     global NB_OUTER, OOC_BUDGET, DISK_PATH, HOST_CACHE
     NB_OUTER = args.nb_outer
     OOC_BUDGET = int(args.ooc_budget_gb * (1 << 30))
