@@ -94,3 +94,15 @@ def test_oracle_certificate_bounds_the_error(monkeypatch):
     assert err.max() <= bound
     Xq = Xs + 1e-5 * E
     assert bench.oracle_certificate("t12", B.T, Xq) == pytest.approx(bound / 100, rel=2e-2)
+
+
+def test_paper_context_rates():
+    """The paper's printed seconds (Sec. 3.1, 512^2, 2048 slices) turned into
+    rates: 2.46e16 QR flops in 3439.7 s (FP64) and 2444.9 s (FP32); 2048
+    slices in 148.1 s and 76.1 s."""
+    pc = bench.paper_context()
+    assert pc["fp64"]["qr_tflops_derived"] == pytest.approx(7.157, rel=1e-3)
+    assert pc["fp32"]["qr_tflops_derived"] == pytest.approx(10.069, rel=1e-3)
+    assert pc["fp64"]["slices_per_s_derived"] == pytest.approx(13.83, rel=1e-3)
+    assert pc["fp32"]["slices_per_s_derived"] == pytest.approx(26.91, rel=1e-3)
+    assert pc["fp32"]["solve_tflops_derived"] == pytest.approx(5.67, rel=2e-3)
