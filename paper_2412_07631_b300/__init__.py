@@ -123,6 +123,19 @@ def _check(st: int, allow=()):
     raise CTQRError(st, L.ct_status_str(st).decode(), (L.ct_last_error() or b"").decode())
 
 
+def _check_factor(st: int, h, system, precision: str):
+    """_check for the factorisations.  A rank-deficient system (CT_ERR_RANK)
+    still returns its factor; it travels with the exception as `.factor`
+    (freed with it) so the caller can inspect |R_jj|."""
+    if st == RANK and h.value:
+        try:
+            _check(st)
+        except CTQRError as e:
+            e.factor = Factor(h, system, precision)
+            raise
+    _check(st)
+
+
 def _stream(stream=None):
     import torch
     if stream is None:
@@ -152,6 +165,7 @@ def make_geometry(n_side, n_views, n_bins, sqrt_lambda=0.0, pixel_width=1.0, bin
 
 
 INTERRUPTED = 12  # ct_status CT_ERR_INTERRUPTED
+RANK = 4  # ct_status CT_ERR_RANK
 
 
 class System:
@@ -242,7 +256,8 @@ class System:
             nb_outer = autotune.outer_block(self.geom, precision)
         o = Opts(PRECISIONS[precision], 0, 0.0, nb_outer, nb_inner, 2 if column_panel else 0)
         h = C.c_void_p()
-        _check(lib().ct_qr_factor(self.h, C.byref(o), _stream(stream), C.byref(h)))
+        st = lib().ct_qr_factor(self.h, C.byref(o), _stream(stream), C.byref(h))
+        _check_factor(st, h, self, precision)
         return Factor(h, self, precision)
 
     def factor_ooc(self, precision: str | None = None, device_budget: int = 16 << 30,
@@ -260,7 +275,7 @@ class System:
                                     C.byref(h))
         if st == INTERRUPTED:
             return None
-        _check(st)
+        _check_factor(st, h, self, precision)
         return Factor(h, self, precision)
 
     def free(self):

@@ -1,8 +1,17 @@
-"""Failure detection on the GPU without a fault: a device-side wait that
-cannot complete (the panel kernels' grid meet on a grid missing a CTA) gives
-up after its time limit, the library reports CT_ERR_TIMEOUT with the site at
-the next synchronisation point, and the context stays usable: the status
-word is clear and the next factorisation and solve match the oracle."""
+"""Failure detection on the GPU without a fault.
+
+* A device-side wait that cannot complete (the panel kernels' grid meet on a
+  grid missing a CTA) gives up after its time limit, the library reports
+  CT_ERR_TIMEOUT with the site at the next synchronisation point, and the
+  context stays usable: the status word is clear and the next factorisation
+  and solve match the oracle.
+* A numerically rank-deficient system (one view of a 4 x 4 image: rank 4 of
+  16, R with exact zeros on its diagonal) is reported as CT_ERR_RANK by the
+  |R_jj| >= n u max|R_jj| test, with the factor kept for inspection.
+* Refinement stopped short of its tolerance returns CT_ERR_NOCONV with the
+  best iterate written and its stopping measure reported; a sinogram with a
+  NaN gives an infinite stopping measure and CT_ERR_NOCONV instead of a
+  silently wrong image.  The same factor then solves normally."""
 import time
 
 import numpy as np
@@ -32,4 +41,64 @@ def test_stalled_wait_surfaces_as_timeout(oracle_mod):
     F = sysg.factor("tf32")
     Xg = F.solve(torch.from_numpy(np.ascontiguousarray(B.T)).cuda(), max_iter=20,
                  tol=1e-10).cpu().numpy().T
+    assert rel_err_cols(Xg, Xo).max() <= 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("storage,precision", [("fp64", "fp64"), ("fp32", "fp32"), ("fp32", "tf32")])
+def test_rank_deficient_system_is_reported(storage, precision):
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    # one view at 0 degrees, 20 bins: the rays through the four pixel columns
+    # each cover one column of the image, so A has four distinct rows
+    sysg = ct.System(ct.make_geometry(4, 1, 20), storage)
+    with pytest.raises(ct.CTQRError) as ei:
+        sysg.factor(precision)
+    assert ei.value.name == "CT_ERR_RANK", str(ei.value)
+    assert "rank deficient" in str(ei.value)
+    assert ei.value.factor.h
+    ei.value.factor.free()
+    sysg.free()
+    # the context is unaffected: a full-rank system factors and solves
+    sysg = ct.System(ct.make_geometry(4, 6, 8, 0.05), storage)
+    F = sysg.factor(precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    X = F.solve(torch.ones((1, sysg.m), dtype=dt, device="cuda"), max_iter=20, tol=1e-10,
+                allow_noconv=True)
+    assert torch.isfinite(X).all()
+
+
+@pytest.mark.gpu
+def test_refinement_short_of_tolerance_reports_noconv(oracle_mod):
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g = O.Geometry(12, 20, 18, sqrt_lambda=0.05)
+    csr = O.siddon_csr(g)
+    B = synth.poisson_sinogram(O.forward(csr, synth.phantom_batch(12, 2, 6, 9)), 12, 1e4, seed=9)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    sysg = ct.System(ct.make_geometry(12, 20, 18, 0.05), "fp32")
+    F = sysg.factor("tf32")
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    with pytest.raises(ct.CTQRError) as ei:
+        F.solve(Bt, max_iter=1, tol=1e-300)
+    assert ei.value.name == "CT_ERR_NOCONV"
+    X1 = F.solve(Bt, max_iter=1, tol=1e-300, allow_noconv=True)
+    assert F.last_info["iterations"] == 1
+    assert 1e-300 < F.last_info["stop_measure"] < 1.0
+    assert torch.isfinite(X1).all()
+    gX = torch.from_numpy(np.random.default_rng(2).standard_normal((2, sysg.n))).cuda()
+    with pytest.raises(ct.CTQRError) as ei:
+        F.adjoint(gX, max_iter=1, tol=1e-300)
+    assert ei.value.name == "CT_ERR_NOCONV"
+    # a NaN in one sinogram: the FP64 stopping measure is not finite
+    Bn = Bt.clone()
+    Bn[1, 5] = float("nan")
+    with pytest.raises(ct.CTQRError) as ei:
+        F.solve(Bn, max_iter=2, tol=1e-10)
+    assert ei.value.name == "CT_ERR_NOCONV"
+    F.solve(Bn, max_iter=2, tol=1e-10, allow_noconv=True)
+    assert F.last_info["stop_measure"] == float("inf")
+    # the factor and the context are intact
+    Xg = F.solve(Bt, max_iter=20, tol=1e-10).cpu().numpy().T
     assert rel_err_cols(Xg, Xo).max() <= 1e-6
