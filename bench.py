@@ -344,6 +344,42 @@ def gemm_only(args):
                       "steps": args.steps, "warmup": args.warmup}))
 
 
+# CUDA-core peaks of the FP32 and FP64 paths, whose GEMMs run on the CUDA
+# cores: FP32 = 148 SMs x 128 FMA lanes x 2 flops x 2.032 GHz (the maximum SM
+# clock); FP64 = the part's nominal dense FP64 rate.
+ALU_PEAKS = {"fp32": 148 * 128 * 2 * 2.032e9 / 1e12, "fp64": 1.25}
+
+
+def roofline_of(prof, precision, peaks, peak_src):
+    """The roofline object of a step's dominant kernel class, from the
+    per-class CUDA-event timing of a profiled step (`prof` =
+    stats_read() after stats_reset(True) and one step): achieved =
+    algorithmic flops of all the class's launches / their summed duration.
+    The class is the trailing-update GEMMs: BF16-operand tcgen05 GEMMs for
+    the BF16 paths (the TF32-operand class beside it as `tf32_class`),
+    TF32-operand tcgen05 GEMMs for the TF32 paths, CUDA-core GEMMs for the
+    plain FP32 and FP64 paths."""
+    def roof(cls, bound, peak, src, kernel):
+        t = prof[cls]
+        ach = t["flops"] / (t["ms"] * 1e-3) / 1e12 if t["ms"] > 0 else 0.0
+        return {"bound": bound, "kernel": f"{kernel} ({cls}, all launches of a step)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if peak else None,
+                "traffic": None, "peak_source": src, "launches_per_step": t["count"], "ms_per_step": t["ms"]}
+    tf32_peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+    tf32_src = f"{peak_src} bf16 sustained x nominal TF32/BF16 ratio {TF32_OVER_BF16:.3f}"
+    if precision in ("bf16", "bf16x3"):
+        r = roof("tc_gemm_bf16", "tensor", peaks["bf16_tflops_sustained"], f"{peak_src} bf16 sustained",
+                 "tcgen05 GEMMs")
+        if prof["tc_gemm"]["count"]:
+            r["tf32_class"] = roof("tc_gemm", "tensor", tf32_peak, tf32_src, "tcgen05 GEMMs")
+        return r
+    if precision in ("tf32", "tf32x3"):
+        return roof("tc_gemm", "tensor", tf32_peak, tf32_src, "tcgen05 GEMMs")
+    src = ("148 SMs x 128 FP32 lanes x 2 flops x 2.032 GHz" if precision == "fp32"
+           else "nominal dense FP64 rate of the part")
+    return roof("simt_gemm", "alu", ALU_PEAKS[precision], src, "CUDA-core GEMMs")
+
+
 def diff_only(args):
     """The differentiation workload: the 128x128 geometry (180 views x 182
     bins + sqrt(lambda) = 0.05 I rows), a batch of 256 noisy sinograms through
@@ -562,24 +598,7 @@ def main():
     run_step(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
     prof = ct.stats_read()
     ct.stats_reset(False)
-    # the dominant kernel class: the trailing-update GEMMs (BF16 operands for
-    # the BF16 paths, TF32 otherwise); the other tensor-core class beside it
-    def tensor_roof(cls, peak, src):
-        t = prof[cls]
-        ach = t["flops"] / (t["ms"] * 1e-3) / 1e12 if t["ms"] > 0 else 0.0
-        return {"bound": "tensor", "kernel": f"tcgen05 GEMMs ({cls}, all launches of a step)",
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if peak else None,
-                "traffic": None, "peak_source": src, "launches_per_step": t["count"], "ms_per_step": t["ms"]}
-    tf32_peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-    tf32_src = f"{peak_src} bf16 sustained x nominal TF32/BF16 ratio {TF32_OVER_BF16:.3f}"
-    bf16_peak = peaks["bf16_tflops_sustained"]
-    bf16_src = f"{peak_src} bf16 sustained"
-    if args.precision in ("bf16", "bf16x3"):
-        roofline = tensor_roof("tc_gemm_bf16", bf16_peak, bf16_src)
-        if prof["tc_gemm"]["count"]:
-            roofline["tf32_class"] = tensor_roof("tc_gemm", tf32_peak, tf32_src)
-    else:
-        roofline = tensor_roof("tc_gemm", tf32_peak, tf32_src)
+    roofline = roofline_of(prof, args.precision, peaks, peak_src)
     breakdown = {c: {"ms": round(prof[c]["ms"], 3), "count": prof[c]["count"]}
                  for c in ct.STAT_CLASSES if prof[c]["count"]}
 

@@ -106,3 +106,32 @@ def test_paper_context_rates():
     assert pc["fp64"]["slices_per_s_derived"] == pytest.approx(13.83, rel=1e-3)
     assert pc["fp32"]["slices_per_s_derived"] == pytest.approx(26.91, rel=1e-3)
     assert pc["fp32"]["solve_tflops_derived"] == pytest.approx(5.67, rel=2e-3)
+
+
+def _prof(**cls):
+    import paper_2412_07631_b300 as ct
+    out = {c: {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "count": 0} for c in ct.STAT_CLASSES}
+    for c, (ms, fl, n) in cls.items():
+        out[c] = {"ms": ms, "flops": fl, "bytes": 0.0, "count": n}
+    return out
+
+
+def test_roofline_arithmetic():
+    """achieved = class flops / class time, frac = achieved / peak; the class
+    and the peak follow the precision (BF16 sustained for the BF16 paths,
+    BF16 sustained x 1.1/2.25 for TF32, CUDA-core peaks for FP32/FP64)."""
+    peaks = {"bf16_tflops_sustained": 1357.3}
+    prof = _prof(tc_gemm_bf16=(1000.0, 1.2e15, 4000), tc_gemm=(500.0, 2.0e14, 900),
+                 simt_gemm=(100.0, 5.0e12, 50))
+    r = bench.roofline_of(prof, "bf16", peaks, "measured")
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s" and r["launches_per_step"] == 4000
+    assert r["achieved"] == pytest.approx(1200.0) and r["peak"] == 1357.3
+    assert r["frac"] == pytest.approx(1200.0 / 1357.3)
+    assert r["tf32_class"]["achieved"] == pytest.approx(400.0)
+    assert r["tf32_class"]["peak"] == pytest.approx(1357.3 * 1.1 / 2.25)
+    r = bench.roofline_of(prof, "tf32", peaks, "measured")
+    assert r["achieved"] == pytest.approx(400.0) and "tf32_class" not in r
+    r = bench.roofline_of(prof, "fp32", peaks, "measured")
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(50.0)
+    assert r["peak"] == pytest.approx(148 * 128 * 2 * 2.032e9 / 1e12)
+    assert bench.roofline_of(prof, "fp64", peaks, "measured")["peak"] == 1.25
