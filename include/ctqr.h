@@ -58,7 +58,7 @@ typedef enum {
     CT_ERR_RANK = 4,        /* |R_jj| < n * u * max|R_jj|: A~ is numerically rank deficient */
     CT_ERR_NOCONV = 5,      /* refinement hit its step limit; best X still written */
     CT_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired; the kernel returned early */
-    CT_ERR_NONFINITE = 7,   /* NaN/Inf met in the input or in a reflector */
+    CT_ERR_NONFINITE = 7,   /* NaN/Inf met in the matrix being factored (a reflector, R's diagonal) */
     CT_ERR_HOSTMEM = 8,     /* host memory (pinned/registered) could not be obtained */
     CT_ERR_STATE = 9,       /* handle in the wrong state (e.g. system already consumed) */
     CT_ERR_UNSUPPORTED = 10, /* option not available in this build */
@@ -250,6 +250,10 @@ CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau)
  * opts may be NULL (factor's precision, defaults).  info may be NULL.  k = 0
  * does nothing (B and X may then be NULL).
  * Synchronises `stream` at the end (to read the convergence state).
+ * B is not scanned for NaN/Inf: with a refining factor a non-finite
+ * sinogram makes the FP64 stopping quantity non-finite, so the call returns
+ * CT_ERR_NOCONV after refine_max_iter steps (info->stop_measure = inf); the
+ * direct FP64/FP32 solves have no such check.
  * Errors: CT_ERR_ARG, CT_ERR_NOCONV (X still holds the best iterate),
  * CT_ERR_NONFINITE, CT_ERR_TIMEOUT, CT_ERR_OOM, CT_ERR_CUDA. */
 CT_API ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
