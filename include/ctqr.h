@@ -61,7 +61,7 @@ typedef enum {
     CT_ERR_NONFINITE = 7,   /* NaN/Inf met in the matrix being factored (a reflector, R's diagonal) */
     CT_ERR_HOSTMEM = 8,     /* host memory (pinned/registered) could not be obtained */
     CT_ERR_STATE = 9,       /* handle in the wrong state (e.g. system already consumed) */
-    CT_ERR_UNSUPPORTED = 10, /* option not available in this build */
+    CT_ERR_UNSUPPORTED = 10, /* option or combination the library does not support */
     CT_ERR_IO = 11,         /* a file read, write or sync failed (disk tier) */
     CT_ERR_INTERRUPTED = 12 /* stopped early on request (ct_opts.stop_after); resumable */
 } ct_status;
