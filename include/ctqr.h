@@ -169,11 +169,13 @@ typedef struct {
 typedef struct ct_system_s *ct_system;
 typedef struct ct_factor_s *ct_factor;
 
-/* Human-readable name of a status code (static string). */
+/* Human-readable name of a status code (static string; "CT_ERR_UNKNOWN" for
+ * a value outside ct_status).  Error reporting of the library; the paper has
+ * no counterpart.  Cannot fail. */
 CT_API const char *ct_status_str(ct_status s);
 
 /* Detail of the last error raised on the calling thread (static per-thread
- * buffer, "" if none). */
+ * buffer, "" if none).  The paper has no counterpart.  Cannot fail. */
 CT_API const char *ct_last_error(void);
 
 /* Build the system matrix (Sec. 2 Eq. 1: a_ij = contribution of ray i to
@@ -186,18 +188,22 @@ CT_API const char *ct_last_error(void);
 CT_API ct_status ct_build_system(const ct_geometry *geom, ct_precision storage, void *stream,
                           ct_system *out);
 
-/* Sizes of a built system. Any output pointer may be NULL. */
+/* Sizes of a built system: m rays and n pixels of A (Sec. 2 Eq. 1), the
+ * rows M' of A~, the dense leading dimension and the CSR's nonzero count.
+ * Any output pointer may be NULL.  Errors: CT_ERR_ARG (NULL handle). */
 CT_API ct_status ct_system_info(ct_system sys, int64_t *m_rays, int64_t *n_pixels, int64_t *rows,
                          int64_t *lda, int64_t *nnz);
 
-/* Device pointers to the system's storage (owned by the library, valid until
- * ct_system_free; the dense pointer is NULL once ct_qr_factor consumed it).
+/* Device pointers to the system matrix of Sec. 2 Eq. 1 (owned by the
+ * library, valid until ct_system_free; the dense pointer is NULL once ct_qr_factor consumed it).
  * row_ptr: int64[m+1]; col_idx: int32[nnz]; val: double[nnz] (CSR of A, ray
- * rows only, entries of a row in Siddon walk order).  Any output may be NULL. */
+ * rows only, entries of a row in Siddon walk order).  Any output may be NULL.
+ * Errors: CT_ERR_ARG (NULL handle). */
 CT_API ct_status ct_system_device_ptrs(ct_system sys, void **dense, const int64_t **row_ptr,
                                 const int32_t **col_idx, const double **val);
 
-/* Copy the system to HOST buffers (synchronous; any pointer may be NULL):
+/* Copy the system matrix of Sec. 2 Eq. 1 to HOST buffers (synchronous; any
+ * pointer may be NULL):
  * row_ptr int64[m+1], col_idx int32[nnz], val double[nnz] (CSR of the ray
  * rows, each row in Siddon walk order); dense: the column-major M' x n matrix
  * A~ in the storage type (double for CT_FP64, float otherwise) with leading
@@ -206,9 +212,10 @@ CT_API ct_status ct_system_device_ptrs(ct_system sys, void **dense, const int64_
 CT_API ct_status ct_system_export(ct_system sys, int64_t *row_ptr, int32_t *col_idx, double *val,
                            void *dense, int64_t ldd);
 
-/* P = A X on the device (forward projection with the CSR, FP64):
- * X: device double, n x k, ldx >= n; P: device double, m x k, ldp >= m.
- * k = 0 does nothing (X and P may then be NULL). */
+/* P = A X on the device: the forward model of Sec. 2 Eq. 1 (sinograms of
+ * images), with the CSR in FP64.  X: device double, n x k, ldx >= n; P:
+ * device double, m x k, ldp >= m.  k = 0 does nothing (X and P may then be
+ * NULL).  Errors: CT_ERR_ARG, CT_ERR_CUDA. */
 CT_API ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx, int32_t k, double *P,
                              int64_t ldp, void *stream);
 
@@ -227,15 +234,20 @@ CT_API ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx,
  * CT_ERR_NONFINITE, CT_ERR_TIMEOUT, CT_ERR_OOM, CT_ERR_CUDA. */
 CT_API ct_status ct_qr_factor(ct_system sys, const ct_opts *opts, void *stream, ct_factor *out);
 
-/* Device pointers of the factor: VR (M' x n, leading dimension lda, R in the
- * upper triangle, Householder vectors below), tau[n] (same element type as
- * VR).  For tests and checkpointing; owned by the library. */
+/* Device pointers of the factors of Sec. 2 Eq. 2: VR (M' x n, leading
+ * dimension lda, R in the upper triangle, Householder vectors below), tau[n]
+ * (same element type as VR).  For tests and checkpointing; owned by the
+ * library.  Any output may be NULL.  Errors: CT_ERR_ARG (NULL handle),
+ * CT_ERR_UNSUPPORTED (out-of-core factor: V and R are in host memory). */
 CT_API ct_status ct_factor_device_ptrs(ct_factor f, void **VR, int64_t *lda, void **tau);
 
-/* Copy the factor to HOST buffers (synchronous; any pointer may be NULL):
+/* Copy the factors of Sec. 2 Eq. 2 to HOST buffers (synchronous; any
+ * pointer may be NULL):
  * VR (M' x n, leading dimension ldv >= M', R on and above the diagonal,
  * Householder vectors below it), tau[n]; element type double for CT_FP64,
- * float otherwise. */
+ * float otherwise.  Works for in-core, host-resident and disk-backed
+ * factors.  Errors: CT_ERR_ARG (NULL handle, ldv < M'), CT_ERR_IO (disk
+ * tier), CT_ERR_CUDA. */
 CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau);
 
 /* X = R^-1 (Q^T b~) for k sinograms (Sec. 2 Eq. 3: C = Q^T B, then R X = C;
@@ -259,13 +271,15 @@ CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau)
 CT_API ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
                    const ct_opts *opts, void *stream, ct_solve_info *info);
 
-/* As ct_solve, but B and X are HOST buffers; the host-to-device copy of B
+/* Sec. 2 Eq. 3 as ct_solve, but B and X are HOST buffers; the host-to-device copy of B
  * and the device-to-host copy of X are part of the call (staged through
- * library-owned pinned buffers).  Blocks until X is written. */
+ * library-owned pinned buffers).  Blocks until X is written.
+ * Errors: as ct_solve. */
 CT_API ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
                         const ct_opts *opts, void *stream, ct_solve_info *info);
 
-/* Adjoint of the (unrefined) solve map b -> x = R^-1 [Q^T b~]_{0:n}:
+/* Adjoint of the solve map of Sec. 2 Eq. 3, b -> x = R^-1 [Q^T b~]_{0:n}
+ * (the paper has no adjoint; it serves differentiation through the solve):
  * gB = [Q [R^-T gX; 0]]_{0:m}  (the gradient of a loss L(x) with respect to
  * b, given gX = dL/dx).  gX: device, n x k, ldgx >= n; gB: device, m x k,
  * ldgb >= m; element type as ct_solve.  For refining factors the adjoint is
@@ -287,8 +301,8 @@ CT_API ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int
 CT_API ct_status ct_build_system_host(const ct_geometry *geom, ct_precision storage,
                                       size_t device_budget, void *stream, ct_system *out);
 
-/* Blocked Householder QR of a host-resident system with a bounded device
- * working set: left-looking superpanels of W columns (W a multiple of the
+/* Blocked Householder QR (Sec. 2 Eq. 2) of a host-resident system with a
+ * bounded device working set, the paper's out-of-core setting (Sec. 2.2): left-looking superpanels of W columns (W a multiple of the
  * outer block, as wide as device_budget allows after two staging buffers of
  * one outer block of V each); each superpanel is copied in, updated by every
  * earlier block reflector (V streamed from host memory on a second stream,
@@ -341,7 +355,8 @@ CT_API ct_status ct_build_system_disk(const ct_geometry *geom, ct_precision stor
                                       const char *path, int32_t block_cols,
                                       size_t host_cache_bytes, void *stream, ct_system *out);
 
-/* Reopen a file written by ct_build_system_disk (any state: assembled,
+/* Reopen a file written by ct_build_system_disk (the matrix in secondary
+ * storage, Sec. 2.2) in any state (assembled,
  * partly or fully factored): header checked (magic, version, checksum), the
  * sparse rows rebuilt on the device from the stored geometry.
  * Errors: CT_ERR_ARG (missing or foreign file, checksum mismatch),
@@ -349,23 +364,28 @@ CT_API ct_status ct_build_system_disk(const ct_geometry *geom, ct_precision stor
 CT_API ct_status ct_system_open_disk(const char *path, size_t host_cache_bytes, void *stream,
                                      ct_system *out);
 
-/* State of a disk-backed system's file: *state 0 = A~ assembled, 1 =
+/* Progress of the out-of-core factorisation from disk (Sec. 2.2; the
+ * resume records have no counterpart in the paper).  State of a
+ * disk-backed system's file: *state 0 = A~ assembled, 1 =
  * factorisation in progress, 2 = factored; *done_cols = columns whose
  * factors are final on disk.  CT_ERR_STATE if the system has no file (or a
  * factor has taken it over). */
 CT_API ct_status ct_disk_progress(ct_system sys, int32_t *state, int64_t *done_cols);
 
-/* Process-wide disk-tier counters since the last reset: bytes read and
+/* Process-wide counters of the disk tier (Sec. 2.2: the host cache of
+ * blocks read from disk) since the last reset: bytes read and
  * written, cache hits (block resident), prefetched (read already in flight),
  * misses (read on demand), and the summed seconds of the I/O threads' reads
- * and writes.  reset != 0 zeroes them after reading.  Any pointer may be NULL. */
+ * and writes.  reset != 0 zeroes them after reading.  Any pointer may be NULL.
+ * Always returns CT_OK. */
 CT_API ct_status ct_disk_stats(int32_t reset, int64_t *bytes_read, int64_t *bytes_written,
                                int64_t *hits, int64_t *prefetched, int64_t *misses,
                                double *read_s, double *write_s);
 
-/* Pinned host blocks of freed out-of-core systems and factors are kept (at
- * most two) for reuse by the next ct_build_system_host, since pinning tens
- * of GB takes seconds; this unpins and frees them. */
+/* Host memory of the out-of-core tier (Sec. 2.2).  Pinned host blocks of
+ * freed out-of-core systems and factors are kept (at most two) for reuse by
+ * the next ct_build_system_host, since pinning tens of GB takes seconds;
+ * this unpins and frees them.  Cannot fail (no return value). */
 CT_API void ct_host_cache_release(void);
 
 /* Checkpoint of a factorisation: the paper recomputes A = QR only when A
@@ -377,7 +397,8 @@ CT_API void ct_host_cache_release(void);
  * memory).  Errors: CT_ERR_ARG (bad path), CT_ERR_HOSTMEM, CT_ERR_CUDA. */
 CT_API ct_status ct_factor_save(ct_factor f, const char *path);
 
-/* Read a factor written by ct_factor_save into *out.  `sys` must have been
+/* Read a factor written by ct_factor_save into *out (the reuse of A = QR
+ * across runs, Sec. 2, text after Eq. 3).  `sys` must have been
  * built with the same geometry and storage precision; its sparse rows serve
  * the refinement, so it must outlive the factor.  Like ct_qr_factor, the
  * factor takes over the system's dense storage (overwritten by V and R); if
@@ -387,12 +408,13 @@ CT_API ct_status ct_factor_save(ct_factor f, const char *path);
  * geometry or precision mismatch), CT_ERR_OOM, CT_ERR_CUDA. */
 CT_API ct_status ct_factor_load(ct_system sys, const char *path, void *stream, ct_factor *out);
 
-/* Release a system or a factor and what the library allocated for it.  A
+/* Release a system or a factor and what the library allocated for it
+ * (ownership of the library; the paper has no counterpart).  A
  * factor owns the dense storage it took over from its system (V and R); a
  * refining factor reads its system's sparse rows, so free a factor before
  * its system.  Pinned host blocks of out-of-core systems go to the reuse
  * cache (see ct_host_cache_release); a disk-backed file is closed and stays
- * on disk.  NULL is ignored. */
+ * on disk.  NULL is ignored.  Cannot fail (no return value). */
 CT_API void ct_system_free(ct_system sys);
 CT_API void ct_factor_free(ct_factor f);
 
@@ -411,29 +433,35 @@ CT_API ct_status ct_selftest_wait_timeout(void *stream);
 
 /* ---- Benchmark accounting (not part of the method) ---------------------- */
 
-/* Zero the launch counter; timing != 0 also brackets every tensor-core GEMM,
+/* Benchmark accounting; the paper has no counterpart.  Zero the launch
+ * counter; timing != 0 also brackets every tensor-core GEMM,
  * CUDA-core GEMM, panel, triangular-diagonal, sparse-product and Siddon launch
  * with CUDA events on its stream, recording its algorithmic flops and bytes
- * (adds a little launch overhead; off by default). */
+ * (adds a little launch overhead; off by default).  Always returns CT_OK. */
 CT_API ct_status ct_stats_reset(int32_t timing);
 
-/* Synchronises the device, then returns the number of kernels launched since
+/* Benchmark accounting; the paper has no counterpart.  Synchronises the
+ * device, then returns the number of kernels launched since
  * the last reset and, per class (9 entries each; classes: 0 tensor-core GEMM
  * with TF32 operands, 1 CUDA-core GEMM, 2 panel, 3 triangular diagonal
  * blocks, 4 sparse FP64 products, 5 Siddon, 6 other, 7 sparse FP32 products,
  * 8 tensor-core GEMM with BF16 operands), the summed event time in ms,
  * algorithmic flops, algorithmic bytes and launch count.  Any pointer may be
- * NULL. */
+ * NULL.  Errors: CT_ERR_CUDA (the synchronisation or an event query failed). */
 CT_API ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *bytes,
                                int64_t *count);
 
-/* Write one CSV line per timed launch since the last ct_stats_reset(1):
- * class, four shape fields (GEMM: M, N, K, splits), ms, flops, bytes. */
+/* Benchmark accounting; the paper has no counterpart.  Write one CSV line
+ * per timed launch since the last ct_stats_reset(1): class, four shape
+ * fields (GEMM: M, N, K, splits), ms, flops, bytes.
+ * Errors: CT_ERR_ARG (NULL path or a file that cannot be written), CT_ERR_CUDA. */
 CT_API ct_status ct_stats_dump(const char *path);
 
 /* ---- Kernel-level entry points (used by the parity tests) --------------- */
 
-/* GEMM engine behind the WY updates: C = alpha * op(A) * op(B) + beta * C,
+/* GEMM engine behind the compact-WY trailing updates and the Q^T and R^-1
+ * applications (Sec. 2.1, the BLAS-3 products inside 'dgeqrf', 'dormqr'
+ * and 'dtrsm'): C = alpha * op(A) * op(B) + beta * C,
  * column-major, op = 'N' or 'T'.  kind: 0 = FP64 (DFMA), 1 = FP32 (FFMA),
  * 2 = TF32 tensor cores (tcgen05, FP32 accumulate), 3 = BF16 tensor cores,
  * 4 = TF32x3 and 5 = BF16x3 split-precision products on the tensor cores

@@ -70,3 +70,20 @@ def test_disk_tier_refuses_bad_files_and_blocks_without_a_gpu(tmp_path):
     assert L.ct_build_system_disk(ctypes.byref(g), 1, None, 64, 0, None, ctypes.byref(h)) == 1
     assert L.ct_status_str(11) == b"CT_ERR_IO"
     assert L.ct_status_str(12) == b"CT_ERR_INTERRUPTED"
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration's comment names the passage of the paper that defines
+    the operation (a section or an equation), or says that the paper has no
+    counterpart, and states its errors or that it cannot fail."""
+    text = open(os.path.join(ROOT, "include", "ctqr.h")).read()
+    uncited = []
+    for m in re.finditer(r"CT_API[^;(]*?\b(ct_[a-z_0-9]+)\s*\(", text):
+        end = text.rfind("*/", 0, m.start())
+        comment = text[text.rfind("/*", 0, end):end]
+        comment = re.sub(r"\s*\n\s*\*\s?", " ", comment)
+        if not re.search(r"Sec\. \d|Eq\. \d|no counterpart", comment):
+            uncited.append(m.group(1))
+        if not re.search(r"Errors|CT_ERR_|CT_OK|Cannot fail", comment):
+            uncited.append(m.group(1) + " (errors)")
+    assert not uncited, uncited
