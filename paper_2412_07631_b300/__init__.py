@@ -478,3 +478,139 @@ def stats_read() -> dict:
 
 __all__ = ["CTSolve", "disk_stats", "stats_reset", "stats_read", "stats_dump", "STAT_CLASSES", "Geometry", "Opts", "SolveInfo", "CTQRError", "System", "Factor", "gemm", "lib",
            "lib_path", "make_geometry", "PRECISIONS", "SYMBOLS"]
+
+
+# ---- The C entry points under their own names (the ct_ prefix dropped) -----
+# Thin marshalling over the classes above; every one maps to one call of
+# include/ctqr.h.
+
+def status_str(st: int) -> str:
+    """ct_status_str."""
+    return lib().ct_status_str(st).decode()
+
+
+def last_error() -> str:
+    """ct_last_error (the calling thread's last error detail)."""
+    return (lib().ct_last_error() or b"").decode()
+
+
+def build_system(geom: Geometry, storage: str = "fp32", stream=None) -> System:
+    """ct_build_system: A~ on the device (Sec. 2 Eq. 1)."""
+    return System(geom, storage, stream)
+
+
+def build_system_host(geom: Geometry, storage: str, device_budget: int, stream=None) -> System:
+    """ct_build_system_host: A~ in pinned host memory, built in device slabs."""
+    return System(geom, storage, stream, host_budget=device_budget)
+
+
+def build_system_disk(geom: Geometry, storage: str, path: str, block_cols: int = 0,
+                      host_cache: int = 1 << 30, stream=None) -> System:
+    """ct_build_system_disk: A~ in a file of column blocks."""
+    return System(geom, storage, stream, disk_path=path, host_cache=host_cache, block_cols=block_cols)
+
+
+def system_open_disk(path: str, host_cache: int = 1 << 30, stream=None) -> System:
+    """ct_system_open_disk."""
+    return System.open_disk(path, host_cache, stream)
+
+
+def system_info(system: System) -> dict:
+    """ct_system_info: m rays, n pixels, M' rows, dense leading dimension, nnz."""
+    return {"m": system.m, "n": system.n, "rows": system.rows, "lda": system.lda, "nnz": system.nnz}
+
+
+def system_device_ptrs(system: System) -> dict:
+    """ct_system_device_ptrs: device addresses (ints) of the dense A~ (0 once
+    factored) and the CSR arrays."""
+    p = [C.c_void_p() for _ in range(4)]
+    _check(lib().ct_system_device_ptrs(system.h, *[C.byref(x) for x in p]))
+    return dict(zip(("dense", "row_ptr", "col_idx", "val"), (x.value or 0 for x in p)))
+
+
+def system_export(system: System, dense: bool = False):
+    """ct_system_export: the CSR of A (row_ptr, col_idx, val) as numpy
+    arrays, or with dense=True the column-major A~."""
+    return system.export_dense() if dense else system.export_csr()
+
+
+def forward_project(system: System, X, stream=None):
+    """ct_forward_project: P = A X (X: float64 CUDA tensor (k, n) -> (k, m))."""
+    return system.forward(X, stream)
+
+
+def qr_factor(system: System, precision: str | None = None, **kw) -> "Factor":
+    """ct_qr_factor (Sec. 2 Eq. 2); keywords as System.factor."""
+    return system.factor(precision, **kw)
+
+
+def qr_factor_ooc(system: System, precision: str | None = None, device_budget: int = 16 << 30,
+                  **kw) -> "Factor | None":
+    """ct_qr_factor_ooc (Sec. 2.2); keywords as System.factor_ooc."""
+    return system.factor_ooc(precision, device_budget, **kw)
+
+
+def factor_device_ptrs(factor: "Factor") -> dict:
+    """ct_factor_device_ptrs: device addresses (ints) of VR and tau, and lda."""
+    vr, tau, lda = C.c_void_p(), C.c_void_p(), C.c_int64()
+    _check(lib().ct_factor_device_ptrs(factor.h, C.byref(vr), C.byref(lda), C.byref(tau)))
+    return {"VR": vr.value or 0, "lda": lda.value, "tau": tau.value or 0}
+
+
+def factor_export(factor: "Factor"):
+    """ct_factor_export: (VR, tau) as numpy arrays."""
+    return factor.export()
+
+
+def solve(factor: "Factor", B, **kw):
+    """ct_solve (Sec. 2 Eq. 3); keywords as Factor.solve."""
+    return factor.solve(B, **kw)
+
+
+def solve_host(factor: "Factor", B, **kw):
+    """ct_solve_host; keywords as Factor.solve_host."""
+    return factor.solve_host(B, **kw)
+
+
+def solve_adjoint(factor: "Factor", gX, **kw):
+    """ct_solve_adjoint; keywords as Factor.adjoint."""
+    return factor.adjoint(gX, **kw)
+
+
+def factor_save(factor: "Factor", path: str):
+    """ct_factor_save."""
+    factor.save(path)
+
+
+def factor_load(system: System, path: str, stream=None) -> "Factor":
+    """ct_factor_load."""
+    return Factor.load(system, path, stream)
+
+
+def disk_progress(system: System) -> tuple[int, int]:
+    """ct_disk_progress: (state, done_cols)."""
+    return system.disk_progress()
+
+
+def host_cache_release():
+    """ct_host_cache_release."""
+    lib().ct_host_cache_release()
+
+
+def system_free(system: System):
+    """ct_system_free."""
+    system.free()
+
+
+def factor_free(factor: "Factor"):
+    """ct_factor_free."""
+    factor.free()
+
+
+def gemm_noalloc(kind: str, transa: str, transb: str, M: int, N: int, K: int, alpha: float, A,
+                 lda: int, B, ldb: int, beta: float, Cm, ldc: int, stream=None):
+    """ct_gemm_noalloc: as gemm() for callers that cannot allocate device
+    memory (the library's scratch is a fixed 16 MiB static device array);
+    kinds fp64, fp32 and tf32."""
+    _check(lib().ct_gemm_noalloc(GEMM_KINDS[kind], transa.encode(), transb.encode(), M, N, K, alpha,
+                                 _ptr(A), lda, _ptr(B), ldb, beta, _ptr(Cm), ldc, _stream(stream)))

@@ -87,3 +87,13 @@ def test_every_entry_point_cites_its_passage():
         if not re.search(r"Errors|CT_ERR_|CT_OK|Cannot fail", comment):
             uncited.append(m.group(1) + " (errors)")
     assert not uncited, uncited
+
+
+def test_binding_names_every_entry_point():
+    """The Python binding carries each C entry point under its own name (the
+    ct_ prefix dropped)."""
+    import paper_2412_07631_b300 as ct
+    missing = [s for s in declared_symbols() if not callable(getattr(ct, s[3:], None))]
+    assert not missing, missing
+    assert ct.status_str(4) == "CT_ERR_RANK"
+    assert isinstance(ct.last_error(), str)
