@@ -195,7 +195,11 @@ class System:
             _check(lib().ct_build_system(C.byref(geom), PRECISIONS[storage], _stream(stream), C.byref(h)))
         self.h = h
         vals = [C.c_int64() for _ in range(5)]
-        _check(lib().ct_system_info(h, *[C.byref(v) for v in vals]))
+        try:
+            _check(lib().ct_system_info(h, *[C.byref(v) for v in vals]))
+        except CTQRError:
+            self.free()
+            raise
         self.m, self.n, self.rows, self.lda, self.nnz = (v.value for v in vals)
 
     @classmethod
