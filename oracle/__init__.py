@@ -19,6 +19,7 @@ Functions and the passage they follow:
   householder_qr .......................... Sec. 2 Eq. 2, Sec. 2.1 (dgeqrf)
   apply_qt / apply_q ...................... Sec. 2 Eq. 3 (C = Q^T B), Q implicit
   backsolve ............................... Sec. 2 Eq. 3 (R X = C), Sec. 2.1 (dtrsm)
+  lapack_qr_gradient ...................... the transpose of Eq. 3's steps (loss gradient)
   normal_eq_ld ............................ brute force, (A~^T A~) x = A~^T b~
   residual_ld / certificate ............... ||x - x*|| <= ||A~^T(b~ - A~ x)|| / lambda
   quality ................................. Sec. 3.1.3, Eqs. for SNR, MSE, PSNR
@@ -309,6 +310,39 @@ def lapack_qr_solve(g: Geometry, A: np.ndarray, B: np.ndarray, overwrite: bool =
     X, info = lapack.dtrtrs(R, np.asfortranarray(c[:n]), lower=0, trans=0)
     assert info == 0, info
     return X, R
+
+
+def lapack_qr_gradient(g: Geometry, A: np.ndarray, B: np.ndarray, X_true: np.ndarray, k_total: int,
+                       overwrite: bool = False):
+    """Gradient of the loss L = ||X - X_true||_F^2 / (n k_total) with respect
+    to the sinograms, through x = R^-1 Q1^T b~ (Sec. 2 Eq. 3) on the LAPACK
+    route of Sec. 2.1.  With g = dL/dx = 2 (x - x_true) / (n k_total) the
+    gradient is [Q [R^-T g; 0]]_{0:m}: the transposes of Eq. 3's two steps
+    in reverse order (dtrtrs transposed, then dormqr 'N').  B and X_true hold
+    the sampled slices as columns; k_total is the batch size the loss
+    averages over.  Returns (grad_b (m x s), x (n x s))."""
+    from scipy.linalg import lapack
+    A = np.asfortranarray(A, dtype=np.float64)
+    qr, tau, work, info = lapack.dgeqrf(A, overwrite_a=overwrite)
+    assert info == 0, info
+    n, m = g.n, g.m
+
+    def ormqr(trans, C_):
+        lwork = max(1, int(lapack.dormqr("L", trans, qr, tau, C_, -1)[1][0].real))
+        out, _, inf = lapack.dormqr("L", trans, qr, tau, C_, lwork, overwrite_c=True)
+        assert inf == 0, inf
+        return out
+
+    R = np.triu(qr[:n, :n])
+    c = ormqr("T", extend_rhs(g, B))
+    X, info = lapack.dtrtrs(R, np.asfortranarray(c[:n]), lower=0, trans=0)
+    assert info == 0, info
+    gx = 2.0 * (X - np.asarray(X_true, np.float64).reshape(n, -1, order="F")) / (n * k_total)
+    z, info = lapack.dtrtrs(R, np.asfortranarray(gx), lower=0, trans=1)
+    assert info == 0, info
+    full = np.zeros((g.rows, z.shape[1]), np.float64, order="F")
+    full[:n] = z
+    return np.asfortranarray(ormqr("N", full)[:m]), X
 
 
 def normal_eq_ld(g: Geometry, csr: CSR, B: np.ndarray) -> np.ndarray:

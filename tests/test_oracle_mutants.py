@@ -87,6 +87,9 @@ PY_MUTANTS = [
      "t = (d - 0.5 * g.n_bins) * g.bin_width", 0),
     ("psnr_amplitude_form", "10.0 * math.log10(max_val ** 2 / mse)", "20.0 * math.log10(max_val ** 2 / mse)", 0),
     ("snr_inverted", "10.0 * math.log10(sig / err)", "10.0 * math.log10(err / sig)", 0),
+    ("gradient_rt_solve_untransposed", "lower=0, trans=1)", "lower=0, trans=0)", 0),
+    ("gradient_q_transposed", 'ormqr("N", full)', 'ormqr("T", full)', 0),
+    ("gradient_drops_factor_two", "gx = 2.0 * (X - ", "gx = 1.0 * (X - ", 0),
 ]
 
 

@@ -166,6 +166,41 @@ def test_adjoint_matches_normal_equation_form(oracle_mod):
     np.testing.assert_allclose(np.sum(X * y, axis=0), np.sum(b * gb, axis=0), rtol=1e-11)
 
 
+def test_lapack_gradient_is_the_loss_gradient(oracle_mod):
+    """The LAPACK-route gradient of L(B) = ||X(B) - X_true||^2 / (n k) (the
+    stored differentiation-workload gradient is made by it) against facts it
+    does not compute: L is quadratic in B, so a central difference along any
+    direction equals <grad, d> up to rounding; and the gradient equals
+    A (A~^T A~)^-1 dL/dx, with the inverse taken from the dense Gram matrix,
+    for the images the plain C route reconstructs."""
+    O = oracle_mod
+    g = O.Geometry(12, 18, 18, sqrt_lambda=0.05)
+    csr = O.siddon_csr(g)
+    A = O.dense_system(g, csr)
+    k = 5  # the loss averages over 5 slices; 3 are sampled
+    Xt = synth.phantom_batch(12, 3, 8)
+    B = synth.poisson_sinogram(O.forward(csr, Xt), 12, 1e4, seed=2)
+    grad, X = O.lapack_qr_gradient(g, A, B, Xt, k)
+    Xp, VR, tau = O.qr_solve(g, A, B)
+    np.testing.assert_allclose(X, Xp, rtol=0, atol=1e-11 * np.abs(Xp).max())
+    gx = 2.0 * (Xp - Xt) / (g.n * k)
+    want = csr.to_scipy() @ np.linalg.solve(A.T @ A, gx)
+    np.testing.assert_allclose(grad, want, rtol=0, atol=1e-9 * np.abs(want).max())
+
+    def loss(Bv):
+        Xv = O.backsolve(VR, O.apply_qt(VR, tau, O.extend_rhs(g, Bv)))
+        return float(np.sum((Xv - Xt) ** 2)) / (g.n * k)
+
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        d = rng.standard_normal(B.shape)
+        d /= np.linalg.norm(d)
+        h = 1e-3
+        fd = (loss(B + h * d) - loss(B - h * d)) / (2 * h)
+        an = float(np.sum(grad * d))
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-12), (fd, an)
+
+
 def test_quality_metrics_hand_values(oracle_mod):
     q = oracle_mod.quality(np.ones(4), 0.9 * np.ones(4))
     assert abs(q["mse"] - 0.01) < 1e-15
