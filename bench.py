@@ -74,7 +74,46 @@ def oracle_geometry_of(O, name):
         sid, fan = FAN[name]
         return O.Geometry(ns, nv, nb, arc_deg=360.0, sqrt_lambda=sl, kind="fan", source_dist=sid, fan_deg=fan)
     return O.Geometry(ns, nv, nb, sqrt_lambda=sl)
-TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate (fallback only)
+
+
+def measure_tf32_peaks(torch, n=8192, seconds=4.0):
+    """TF32 tensor-core peaks of this GPU, measured the way the BF16 peaks
+    beside them were: cuBLAS (torch.matmul with TF32 allowed) on n^3 FP32
+    operands, 2 n^3 flops per product; burst = best of 10 single products
+    (CUDA events), sustained = products back to back for `seconds`."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        g = torch.Generator(device="cuda").manual_seed(1)
+        a = torch.randn((n, n), device="cuda", generator=g)
+        b = torch.randn((n, n), device="cuda", generator=g)
+        c = torch.empty((n, n), device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        best = float("inf")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(10):
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        fl = 2.0 * n ** 3
+        reps = max(1, int(seconds * 1e3 / best))
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        sus = fl * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del a, b, c
+        return {"tf32_tflops": fl / (best * 1e-3) / 1e12, "tf32_tflops_sustained": sus,
+                "how": f"torch.matmul TF32 {n}^3 (2*N^3): best of 10 (burst) and {reps} back to back "
+                       f"(sustained), CUDA events, in this run"}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 # The paper's own timings (Sec. 3.1, the table of residuals and times for
 # 2048 simultaneous slices; the machine from the opening of Sec. 3).  Another
@@ -213,9 +252,14 @@ DISK_PATH = ""  # out of core with A~ in this file (disk tier) instead of pinned
 HOST_CACHE = 0  # pinned block cache of the disk tier (bytes)
 
 
-def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=None, out=None):
-    """One pass of the hot path.  Returns (X, info, per-phase ms)."""
+def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, prof=None, out=None):
+    """One pass of the hot path.  Returns (X, info, per-phase ms).  With a
+    dict `prof`, the library's per-kernel-class accounting is read after the
+    factorisation (prof["qr"], build included) and after the solve
+    (prof["solve"])."""
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    if prof is not None:
+        ct.stats_reset(True)
     ev[0].record()
     storage = "fp64" if precision == "fp64" else "fp32"
     if OOC_BUDGET > 0 and DISK_PATH:  # out of core, disk tier: A~ in a file + block cache
@@ -232,11 +276,17 @@ def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=No
         ev[1].record()
         F = sysg.factor(precision, nb_outer=NB_OUTER)
     ev[2].record()
+    if prof is not None:
+        prof["qr"] = ct.stats_read()
+        ct.stats_reset(True)
     if host:
         X = F.solve_host(B, out=out, max_iter=max_iter, tol=tol)
     else:
         X = F.solve(B, max_iter=max_iter, tol=tol, allow_noconv=True)
     ev[3].record()
+    if prof is not None:
+        prof["solve"] = ct.stats_read()
+        ct.stats_reset(False)
     info = dict(F.last_info or {})
     F.free()
     sysg.free()
@@ -244,6 +294,23 @@ def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, timing=No
     ph = {"build": ev[0].elapsed_time(ev[1]), "qr": ev[1].elapsed_time(ev[2]),
           "solve": ev[2].elapsed_time(ev[3])}
     return X, info, ph
+
+
+def run_step_kept(ct, torch, geom, precision, B, max_iter, tol):
+    """run_step that returns the system and factor as well (untimed uses:
+    accuracy figures need the forward projector and further solves)."""
+    storage = "fp64" if precision == "fp64" else "fp32"
+    if OOC_BUDGET > 0 and DISK_PATH:
+        sysg = ct.System(geom, storage, disk_path=DISK_PATH, host_cache=HOST_CACHE, block_cols=NB_OUTER)
+        F = sysg.factor_ooc(precision, device_budget=OOC_BUDGET)
+    elif OOC_BUDGET > 0:
+        sysg = ct.System(geom, storage, host_budget=OOC_BUDGET)
+        F = sysg.factor_ooc(precision, device_budget=OOC_BUDGET, nb_outer=NB_OUTER)
+    else:
+        sysg = ct.System(geom, storage)
+        F = sysg.factor(precision, nb_outer=NB_OUTER)
+    X = F.solve(B, max_iter=max_iter, tol=tol, allow_noconv=True)
+    return X, sysg, F
 
 
 # ---------------------------------------------------------------------------
@@ -365,8 +432,12 @@ def roofline_of(prof, precision, peaks, peak_src):
         return {"bound": bound, "kernel": f"{kernel} ({cls}, all launches of a step)",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak if peak else None,
                 "traffic": None, "peak_source": src, "launches_per_step": t["count"], "ms_per_step": t["ms"]}
-    tf32_peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-    tf32_src = f"{peak_src} bf16 sustained x nominal TF32/BF16 ratio {TF32_OVER_BF16:.3f}"
+    if "tf32_tflops_sustained" in peaks:
+        tf32_peak = peaks["tf32_tflops_sustained"]
+        tf32_src = "measured tf32 sustained (" + peaks.get("tf32_how", "cuBLAS") + ")"
+    else:
+        tf32_peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+        tf32_src = f"{peak_src} bf16 sustained x nominal TF32/BF16 ratio {TF32_OVER_BF16:.3f}"
     if precision in ("bf16", "bf16x3"):
         r = roof("tc_gemm_bf16", "tensor", peaks["bf16_tflops_sustained"], f"{peak_src} bf16 sustained",
                  "tcgen05 GEMMs")
@@ -378,6 +449,133 @@ def roofline_of(prof, precision, peaks, peak_src):
     src = ("148 SMs x 128 FP32 lanes x 2 flops x 2.032 GHz" if precision == "fp32"
            else "nominal dense FP64 rate of the part")
     return roof("simt_gemm", "alu", ALU_PEAKS[precision], src, "CUDA-core GEMMs")
+
+
+def quality_of(Xtrue, X):
+    """Image quality of reconstructions X against the phantoms Xtrue (both
+    n x k), with the equations of Sec. 3.1.3 per slice: MSE over the pixels,
+    RMSE, PSNR = 10 log10(MAX^2 / MSE) with MAX = 1 (the phantoms' range) and
+    SNR = 10 log10(sum x_true^2 / sum (x_true - x)^2); means over the slices."""
+    Xtrue = np.asarray(Xtrue, np.float64)
+    X = np.asarray(X, np.float64)
+    err = np.sum((X - Xtrue) ** 2, axis=0)
+    sig = np.sum(Xtrue ** 2, axis=0)
+    mse = err / Xtrue.shape[0]
+    with np.errstate(divide="ignore"):
+        psnr = 10.0 * np.log10(1.0 / mse)
+        snr = 10.0 * np.log10(sig / err)
+    return {"rmse_mean": float(np.sqrt(mse).mean()), "psnr_mean": float(psnr.mean()),
+            "snr_mean": float(snr.mean())}
+
+
+def residual_rel(AX, B):
+    """The paper's accuracy figure ||A X - B||_F / ||B||_F over the batch
+    (Sec. 3.1.2, table of residuals and times): A the ray rows, AX the
+    forward projection of the reconstructed images and B the sinograms, both
+    k x m."""
+    AX = np.asarray(AX, np.float64)
+    B = np.asarray(B, np.float64)
+    return float(np.linalg.norm(AX - B) / np.linalg.norm(B))
+
+
+def solve_roofline_of(prof_solve, solve_ms, k, M, n, solve_fl, precision, peaks):
+    """Roofline of the solve phase (k slices).  The direct solve
+    x = R^-1 Q^T b~ of a batch costs solve_fl flops and must read the factors
+    (V and R: M' n elements) once, so its floor is max(flops / tensor peak,
+    bytes / HBM peak) (CUDA-core FP64 peak for the FP64 path, FP32 for FP32);
+    slices/s at that floor is the roofline the measured slices/s (refinement
+    included) is set against.  The solve's own kernel classes beside it:
+    its tensor-core GEMMs (Q^T sweep, TRSM, inner correction solves) against
+    the TF32 peak, its FP64 and FP32 sparse products against the FP64 and
+    FP32 CUDA-core rates."""
+    es = 8 if precision == "fp64" else 4
+    if precision in ("fp64", "fp32"):
+        peak, src = ALU_PEAKS[precision], "CUDA-core peak"
+    else:
+        peak, src = peaks.get("tf32_tflops_sustained", peaks["bf16_tflops_sustained"] * TF32_OVER_BF16), \
+            "tf32 sustained"
+    t_flops = solve_fl / (peak * 1e12)
+    t_bytes = M * n * es / (peaks["hbm_gbs"] * 1e9)
+    floor_s = max(t_flops, t_bytes)
+    sps = k / (solve_ms * 1e-3)
+    out = {"bound": "tensor" if t_flops >= t_bytes and precision not in ("fp64", "fp32")
+           else ("alu" if t_flops >= t_bytes else "hbm"),
+           "direct_flops_per_batch": solve_fl, "factor_bytes_per_batch": M * n * es,
+           "floor_ms": floor_s * 1e3, "floor_peak": f"{peak:.1f} TFLOP/s ({src}), "
+           f"{peaks['hbm_gbs']:.0f} GB/s HBM", "slices_per_s": sps,
+           "slices_per_s_roofline": k / floor_s, "frac": sps * floor_s / k,
+           "note": "measured time includes the FP64 refinement; the roofline counts the direct solve only"}
+
+    def cls(name, pk):
+        t = prof_solve[name]
+        if not t["count"] or t["ms"] <= 0:
+            return None
+        ach = t["flops"] / (t["ms"] * 1e-3) / 1e12
+        return {"achieved_tflops": ach, "peak": pk, "frac": ach / pk, "ms": t["ms"],
+                "launches": t["count"]}
+
+    tc_peak = peaks.get("tf32_tflops_sustained", peaks["bf16_tflops_sustained"] * TF32_OVER_BF16)
+    out["classes"] = {"tc_gemm": cls("tc_gemm", tc_peak),
+                      "spmm_fp64": cls("spmm_fp64", ALU_PEAKS["fp64"]),
+                      "spmm_fp32": cls("spmm_fp32", ALU_PEAKS["fp32"]),
+                      "simt_gemm": cls("simt_gemm", ALU_PEAKS["fp64" if precision == "fp64" else "fp32"])}
+    out["classes"] = {c: v for c, v in out["classes"].items() if v}
+    return out
+
+
+def measure_host_link(torch, nbytes=1 << 30):
+    """Pinned host <-> device copy rates of this machine (GB/s): best of 5
+    copies of nbytes each way, CUDA events."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        best = float("inf")
+        for _ in range(5):
+            e0.record()
+            dst.copy_(src, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = nbytes / (best * 1e-3) / 1e9
+    out["how"] = f"pinned <-> device copies of {nbytes >> 20} MiB, best of 5, CUDA events"
+    return out
+
+
+def host_link_of(prof_qr, qr_ms, link):
+    """Host-link evidence of the out-of-core factorisation, from the copy
+    classes of one profiled QR: bytes and achieved GB/s of the V blocks
+    streamed on the copy stream, of the superpanel columns loaded and of the
+    factored columns written back (both on the compute stream); the compute
+    stream's stalls on streamed V blocks, and the overlap = the share of the
+    V-streaming time hidden behind compute (1 - stall / streaming time); the
+    link floor = all host bytes over the measured pinned copy rates, against
+    the QR time."""
+    v, c_in, c_out, wait = (prof_qr[c] for c in ("h2d_v", "h2d_cols", "d2h_cols", "copy_wait"))
+    if not (v["count"] or c_in["count"]):
+        return None
+
+    def one(t):
+        return {"gb": t["bytes"] / 1e9, "ms": t["ms"], "copies": t["count"],
+                "gbs": t["bytes"] / (t["ms"] * 1e-3) / 1e9 if t["ms"] > 0 else None}
+
+    h2d = v["bytes"] + c_in["bytes"]
+    floor_ms = (h2d / (link["h2d_gbs"] * 1e9) + c_out["bytes"] / (link["d2h_gbs"] * 1e9)) * 1e3
+    return {"h2d_v": one(v), "h2d_cols": one(c_in), "d2h_cols": one(c_out),
+            "copy_wait_ms": wait["ms"],
+            "overlap": 1.0 - wait["ms"] / v["ms"] if v["ms"] > 0 else None,
+            "link_peak": link, "link_floor_ms": floor_ms, "qr_ms": qr_ms,
+            "link_floor_frac_of_qr": floor_ms / qr_ms if qr_ms > 0 else None}
+
+
+def merge_prof(a, b):
+    """Sum of two per-class accounting reads (stats_read())."""
+    out = {"launches": a["launches"] + b["launches"]}
+    for c, v in a.items():
+        if c != "launches":
+            out[c] = {f: v[f] + b[c][f] for f in ("ms", "flops", "bytes", "count")}
+    return out
 
 
 def diff_only(args):
@@ -472,6 +670,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cert", action="store_true")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="skip the profiled step, the TF32 peak measurement and the accuracy run "
+                         "(for the long FP64 runs at 256^2)")
     ap.add_argument("--nb-outer", type=int, default=0, help="outer WY block width (0: default)")
     ap.add_argument("--ooc-budget-gb", type=float, default=0.0,
                     help="run the out-of-core path: A~ in pinned host memory, this many GB of device working set")
@@ -593,14 +794,23 @@ def main():
     solve_ms = float(np.median([p["solve"] for p in phases]))
     build_ms = float(np.median([p["build"] for p in phases]))
 
-    # ---- profiled step (per-kernel-class CUDA events, not part of the timing) ----
-    ct.stats_reset(True)
-    run_step(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
-    prof = ct.stats_read()
-    ct.stats_reset(False)
-    roofline = roofline_of(prof, args.precision, peaks, peak_src)
-    breakdown = {c: {"ms": round(prof[c]["ms"], 3), "count": prof[c]["count"]}
-                 for c in ct.STAT_CLASSES if prof[c]["count"]}
+    # ---- profiled step (per-kernel-class CUDA events, not part of the timing),
+    #      then the TF32 tensor peaks of this GPU (cuBLAS, as the BF16 peaks) ----
+    roofline = breakdown = solve_roof = host_link = None
+    if not args.no_profile:
+        pr = {}
+        _, _, pph = run_step(ct, torch, geom, args.precision, B, args.max_iter, args.tol, prof=pr)
+        if OOC_BUDGET > 0:
+            host_link = host_link_of(pr["qr"], pph["qr"], measure_host_link(torch))
+        prof = merge_prof(pr["qr"], pr["solve"])
+        tf = measure_tf32_peaks(torch)
+        peaks = dict(peaks, tf32_tflops=tf["tf32_tflops"], tf32_tflops_sustained=tf["tf32_tflops_sustained"],
+                     tf32_how=tf["how"])
+        roofline = roofline_of(prof, args.precision, peaks, peak_src)
+        roofline["tf32_peaks_measured"] = tf
+        breakdown = {c: {"ms": round(prof[c]["ms"], 3), "count": prof[c]["count"]}
+                     for c in ct.STAT_CLASSES if prof[c]["count"]}
+        solve_roof = solve_roofline_of(pr["solve"], solve_ms, k, M, n, solve_fl, args.precision, peaks)
 
     # ---- end-to-end arm: pinned host sinograms in, host images out ----
     e2e = None
@@ -620,16 +830,35 @@ def main():
                "d2h_bytes_per_step": int(k * n * es), "ms_per_step": e2e_ms,
                "api": "ct_build_system + ct_qr_factor + ct_solve_host"}
 
-    # ---- accuracy: quality vs phantom (the error vs the oracle is part of
-    #      the oracle leg below) ----
+    # ---- accuracy (untimed): quality vs phantom (Sec. 3.1.3), the paper's
+    #      residual ||AX - B|| / ||B|| (Sec. 3.1.2), for the noisy sinograms of
+    #      the step and for noiseless sinograms of the same phantoms (the
+    #      setting of the paper's quality tables); the error vs the oracle is
+    #      part of the oracle leg below ----
     Xn = X.double().cpu().numpy().T
-    acc = {}
-    rmse = np.sqrt(np.mean((Xn - Xtrue) ** 2, axis=0))
-    acc["rmse_vs_phantom_mean"] = float(rmse.mean())
-    acc["psnr_vs_phantom_mean"] = float(np.mean(20 * np.log10(1.0 / rmse)))
+    q = quality_of(Xtrue, Xn)
+    acc = {"rmse_vs_phantom_mean": q["rmse_mean"], "psnr_vs_phantom_mean": q["psnr_mean"],
+           "snr_mean": q["snr_mean"]}
+    if not args.no_profile:
+        Xa, sysa, Fa = run_step_kept(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
+        acc["residual_rel"] = residual_rel(sysa.forward(Xa.double()).cpu().numpy(), Bh)
+        Xt_dev = torch.from_numpy(np.ascontiguousarray(Xtrue.T)).cuda()
+        P0 = sysa.forward(Xt_dev)
+        X0 = Fa.solve(P0.to(io_dt).contiguous(), max_iter=args.max_iter, tol=args.tol, allow_noconv=True)
+        q0 = quality_of(Xtrue, X0.double().cpu().numpy().T)
+        acc["noiseless"] = {**q0, "residual_rel": residual_rel(sysa.forward(X0.double()).cpu().numpy(),
+                                                               P0.cpu().numpy()),
+                            "note": "the same phantoms, sinograms A x_true without noise"}
+        acc["residual_note"] = ("noisy data: the residual holds the noise, which no image removes; "
+                                "A is the ray rows only (the regularisation rows excluded)")
+        Fa.free()
+        sysa.free()
+        del Xa, X0, P0, Xt_dev
 
-    # ---- FP64 GPU path vs mixed path on the 128x128 geometry (FP64 at 256^2
-    #      takes tens of minutes at the FP64 rate of this part) ----
+    # ---- FP64 GPU path vs mixed path, measured on the 128x128 geometry and
+    #      extrapolated to this workload by the flop ratio (FP64 at 256^2 takes
+    #      about half an hour at the FP64 rate of this part: bench.py
+    #      --precision fp64 --steps 1 --warmup 0 --no-profile measures it) ----
     cmp = None
     if rank == 0 and not args.no_fp64_compare and args.workload == "c3":
         cns, cnv, cnb, csl, ck, ci0, cne = WORKLOADS["c2"]
@@ -646,6 +875,20 @@ def main():
                          "slices_per_s": ck / (ph["solve"] * 1e-3),
                          "refine_iters": inf.get("iterations", 0),
                          "inner_iters": inf.get("inner_iterations", 0)}
+        # the FP64 path at this workload: its 128^2 QR rate over this
+        # workload's QR flops, its 128^2 per-slice solve time scaled by the
+        # per-slice flop ratio
+        per_slice = solve_fl / k
+        c_per_slice = csolve / ck
+        f64 = cmp["fp64"]
+        cmp["this_workload"] = {
+            "workload": workload_desc(args.workload),
+            "fp64": {"qr_tflops": f64["qr_tflops"], "qr_s": qr_fl / (f64["qr_tflops"] * 1e12),
+                     "slices_per_s": f64["slices_per_s"] * c_per_slice / per_slice,
+                     "extrapolated": True,
+                     "how": "128x128 FP64 rates measured above, scaled by the QR and per-slice solve flop ratios"},
+            args.precision: {"qr_tflops": qr_fl / (qr_ms * 1e-3) / 1e12, "qr_s": qr_ms * 1e-3,
+                             "slices_per_s": k / (solve_ms * 1e-3), "extrapolated": False}}
 
     # ---- the oracle leg (rank 0, after every GPU measurement): the oracle
     #      timed on the host cores, and the certified error bound of sampled
@@ -689,6 +932,7 @@ def main():
             "refine_inner_iters": [i.get("inner_iterations") for i in infos],
             "accuracy": acc,
             "roofline": roofline,
+            "solve_roofline": solve_roof,
             "kernel_breakdown_ms": breakdown,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -697,6 +941,7 @@ def main():
             "fp64_vs_mixed": cmp,
             "paper_context": paper_context(),
             "disk_io": disk_io,
+            "host_link": host_link,
         }
         print(json.dumps(line))
     if dist:

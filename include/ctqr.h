@@ -58,7 +58,8 @@ typedef enum {
     CT_ERR_RANK = 4,        /* |R_jj| < n * u * max|R_jj|: A~ is numerically rank deficient */
     CT_ERR_NOCONV = 5,      /* refinement hit its step limit; best X still written */
     CT_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired; the kernel returned early */
-    CT_ERR_NONFINITE = 7,   /* NaN/Inf met in the matrix being factored (a reflector, R's diagonal) */
+    CT_ERR_NONFINITE = 7,   /* NaN/Inf in the matrix being factored (a reflector, R's diagonal)
+                               or in the right-hand sides of a solve */
     CT_ERR_HOSTMEM = 8,     /* host memory (pinned/registered) could not be obtained */
     CT_ERR_STATE = 9,       /* handle in the wrong state (e.g. system already consumed) */
     CT_ERR_UNSUPPORTED = 10, /* option or combination the library does not support */
@@ -262,10 +263,10 @@ CT_API ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau)
  * opts may be NULL (factor's precision, defaults).  info may be NULL.  k = 0
  * does nothing (B and X may then be NULL).
  * Synchronises `stream` at the end (to read the convergence state).
- * B is not scanned for NaN/Inf: with a refining factor a non-finite
- * sinogram makes the FP64 stopping quantity non-finite, so the call returns
- * CT_ERR_NOCONV after refine_max_iter steps (info->stop_measure = inf); the
- * direct FP64/FP32 solves have no such check.
+ * B is scanned on the device for NaN/Inf (one read of B): a non-finite
+ * sinogram makes the call return CT_ERR_NONFINITE (X then holds what the
+ * arithmetic produced; a refining factor stops refining at the first
+ * non-finite stopping measure, info->stop_measure = inf).
  * Errors: CT_ERR_ARG, CT_ERR_NOCONV (X still holds the best iterate),
  * CT_ERR_NONFINITE, CT_ERR_TIMEOUT, CT_ERR_OOM, CT_ERR_CUDA. */
 CT_API ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
@@ -284,7 +285,8 @@ CT_API ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t 
  * b, given gX = dL/dx).  gX: device, n x k, ldgx >= n; gB: device, m x k,
  * ldgb >= m; element type as ct_solve.  For refining factors the adjoint is
  * taken in FP64 arithmetic on the FP32 factors followed by the same FP64
- * refinement applied to the transposed problem.
+ * refinement applied to the transposed problem.  gX is scanned for NaN/Inf
+ * as ct_solve scans B (CT_ERR_NONFINITE).
  * Errors: as ct_solve. */
 CT_API ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
                            int64_t ldgb, const ct_opts *opts, void *stream, ct_solve_info *info);
@@ -436,18 +438,22 @@ CT_API ct_status ct_selftest_wait_timeout(void *stream);
 /* Benchmark accounting; the paper has no counterpart.  Zero the launch
  * counter; timing != 0 also brackets every tensor-core GEMM,
  * CUDA-core GEMM, panel, triangular-diagonal, sparse-product and Siddon launch
- * with CUDA events on its stream, recording its algorithmic flops and bytes
+ * and every out-of-core host copy with CUDA events on its stream, recording
+ * its algorithmic flops and bytes
  * (adds a little launch overhead; off by default).  Always returns CT_OK. */
 CT_API ct_status ct_stats_reset(int32_t timing);
 
 /* Benchmark accounting; the paper has no counterpart.  Synchronises the
  * device, then returns the number of kernels launched since
- * the last reset and, per class (9 entries each; classes: 0 tensor-core GEMM
+ * the last reset and, per class (13 entries each; classes: 0 tensor-core GEMM
  * with TF32 operands, 1 CUDA-core GEMM, 2 panel, 3 triangular diagonal
  * blocks, 4 sparse FP64 products, 5 Siddon, 6 other, 7 sparse FP32 products,
- * 8 tensor-core GEMM with BF16 operands), the summed event time in ms,
- * algorithmic flops, algorithmic bytes and launch count.  Any pointer may be
- * NULL.  Errors: CT_ERR_CUDA (the synchronisation or an event query failed). */
+ * 8 tensor-core GEMM with BF16 operands; out-of-core host traffic: 9 V blocks
+ * streamed host to device, 10 superpanel columns host to device, 11 factored
+ * columns device to host, 12 the compute stream's waits for a streamed V
+ * block), the summed event time in ms, algorithmic flops, algorithmic bytes
+ * (bytes copied for classes 9-11) and launch count (copies for 9-11, waits
+ * for 12).  Any pointer may be NULL.  Errors: CT_ERR_CUDA (the synchronisation or an event query failed). */
 CT_API ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *bytes,
                                int64_t *count);
 
@@ -478,16 +484,22 @@ CT_API ct_status ct_gemm(int32_t kind, char transa, char transb, int64_t M, int6
  * scratch the library allocates; a caller whose device memory all belongs to
  * its own pool, or that must not allocate at run time (cudaMalloc can fail
  * under memory pressure and synchronises the device), uses this variant
- * instead: same arguments, same kernels, same results within rounding, and
- * the scratch is one fixed 16 MiB array in the library's static device
- * memory, held by every GPU that loads the library until the process exits.
+ * instead: same arguments, same kernels and tile choice, results equal
+ * within rounding, and the scratch is one fixed 16 MiB array in the
+ * library's static device memory, held by every GPU that loads the library
+ * until the process exits.
+ * kind: 0 = FP64, 1 = FP32, 2 = TF32 only; kinds 3 (BF16), 4 (TF32x3) and
+ * 5 (BF16x3) are refused with CT_ERR_ARG (their operand copies are as large
+ * as the operands).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.
- * A product whose K-major operand copies would not fit in the array is
- * refused with CT_ERR_ARG (ct_last_error says how much it needs); split-K
- * depth is reduced to what fits.  kind 3 (BF16) is not offered.
- * Synchronises `stream` before returning. */
+ * (cudaGetSymbolAddress) with that device current, and again after that
+ * device's context has been re-created; make it before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race.  A product
+ * whose K-major operand copies would not fit in the array is refused with
+ * CT_ERR_ARG (ct_last_error says how much it needs); the split-K depth of
+ * ct_gemm's plan is reduced until the partial products fit.
+ * Waits for `stream` before returning (it reads the call's device status).
+ * Errors: CT_ERR_ARG, CT_ERR_TIMEOUT, CT_ERR_CUDA. */
 CT_API ct_status ct_gemm_noalloc(int32_t kind, char transa, char transb, int64_t M, int64_t N,
                                  int64_t K, double alpha, const void *A, int64_t lda,
                                  const void *B, int64_t ldb, double beta, void *C, int64_t ldc,

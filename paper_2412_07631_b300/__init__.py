@@ -432,7 +432,7 @@ class CTSolve:
 
 
 STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other",
-                "spmm_fp32", "tc_gemm_bf16"]
+                "spmm_fp32", "tc_gemm_bf16", "h2d_v", "h2d_cols", "d2h_cols", "copy_wait"]
 
 
 def selftest_wait_timeout(stream=None) -> str:

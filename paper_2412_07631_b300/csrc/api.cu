@@ -27,6 +27,30 @@ ct_status cuda_status(cudaError_t e, const char *what, const char *file, int lin
     return CT_ERR_CUDA;
 }
 
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrentFn)(CUcontext *);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr, *q = nullptr;
+        cudaDriverEntryPointQueryResult r1, r2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &r1) ==
+                cudaSuccess && r1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &q, 12000, cudaEnableDefault, &r2) ==
+                cudaSuccess && r2 == cudaDriverEntryPointSuccess) {
+            get_current = (GetCurrentFn)p;
+            get_id = (GetIdFn)q;
+        }
+    });
+    if (!get_current) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
 int num_sms() {
     static int sms[64] = {0};
     int dev = 0;

@@ -5,7 +5,10 @@
 // File layout (little-endian): FileHeader, then VR column by column (M' x n,
 // no leading-dimension padding), tau[n], T blocks (nblocks x NB x NB), V tops
 // (nblocks x NB x NB); elements in the factor's storage type.  The header
-// carries an FNV-1a 64-bit checksum of everything after it.
+// carries an FNV-1a 64-bit checksum of the header itself (with the checksum
+// field zeroed) followed by everything after it, and a loader accepts block
+// sizes only in the form the factorisation produces them.
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -16,7 +19,7 @@ namespace ctqr {
 namespace {
 
 constexpr char kMagic[8] = {'C', 'T', 'Q', 'R', 'F', 'A', 'C', '1'};
-constexpr uint32_t kVersion = 3;  // 2: fan-beam geometry fields; 3: projector
+constexpr uint32_t kVersion = 4;  // 2: fan-beam geometry fields; 3: projector; 4: header checksummed
 constexpr size_t kChunk = (size_t)64 << 20;
 
 struct FileHeader {
@@ -60,6 +63,24 @@ struct Region {
     int64_t rows, cols, ld;
 };
 
+// Block sizes as ct_qr_factor / ct_qr_factor_ooc make them: panel width nb in
+// [1, 32], outer width NB a multiple of both nb and 32, and one T / V-top
+// block per NB columns.  Anything else would index T and the V tops past their
+// allocations in the solve.
+bool blocks_valid(const FileHeader &hd) {
+    return hd.nb_inner >= 1 && hd.nb_inner <= 32 && hd.nb_outer >= 32 && hd.nb_outer <= (1 << 15) &&
+           hd.nb_outer % 32 == 0 && hd.nb_outer % hd.nb_inner == 0 && hd.n > 0 &&
+           hd.nblocks == ceil_div(hd.n, hd.nb_outer);
+}
+
+// Hash of the header with its checksum field zeroed.
+void hash_header(Fnv &fnv, const FileHeader &hd) {
+    unsigned char b[sizeof(FileHeader)];
+    memcpy(b, &hd, sizeof(hd));  // bytes as written, padding included
+    memset(b + offsetof(FileHeader, checksum), 0, sizeof(hd.checksum));
+    fnv.add(b, sizeof(b));
+}
+
 int regions(ct_factor f, Region *out) {
     out[0] = {f->ooc ? f->VR_host : f->VR, f->M, f->n, f->lda};  // host memory for out-of-core factors
     out[1] = {f->tau, f->n, 1, f->n};
@@ -102,6 +123,7 @@ extern "C" ct_status ct_factor_save(ct_factor f, const char *path) {
     ct_status st = CT_OK;
     PinnedBuf buf;
     Fnv fnv;
+    hash_header(fnv, hd);
     if (fwrite(&hd, sizeof(hd), 1, fp) != 1) st = CT_ERR_ARG;
     if (st == CT_OK && cudaMallocHost(&buf.p, kChunk) != cudaSuccess) st = CT_ERR_HOSTMEM;
     const size_t es = f->es();
@@ -152,6 +174,12 @@ extern "C" ct_status ct_factor_load(ct_system sys, const char *path, void *strea
         set_error("checkpoint %s does not match this system's geometry/precision", path);
         return CT_ERR_ARG;
     }
+    if (!blocks_valid(hd)) {
+        fclose(fp);
+        set_error("checkpoint %s has invalid block sizes (nb_outer %lld, nb_inner %lld, %lld blocks)",
+                  path, (long long)hd.nb_outer, (long long)hd.nb_inner, (long long)hd.nblocks);
+        return CT_ERR_ARG;
+    }
     ct_factor f = new (std::nothrow) ct_factor_s;
     if (!f) {
         fclose(fp);
@@ -195,6 +223,7 @@ extern "C" ct_status ct_factor_load(ct_system sys, const char *path, void *strea
         st = st == CT_OK ? CT_ERR_OOM : st;
     PinnedBuf buf;
     Fnv fnv;
+    hash_header(fnv, hd);
     if (st == CT_OK && cudaMallocHost(&buf.p, kChunk) != cudaSuccess) st = CT_ERR_HOSTMEM;
     if (st == CT_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) st = CT_ERR_CUDA;
     Region rg[4];

@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "../../include/ctqr.h"
 
 namespace ctqr {
@@ -191,13 +193,48 @@ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 int num_sms();
 
+// Process-unique identity of the calling thread's current CUDA context (0 if
+// the driver cannot report one).  State that a context owns -- the device
+// addresses of static device arrays, kernel attributes -- is keyed on it, so
+// that a context created anew (after cudaDeviceReset) is set up again
+// instead of being handed stale addresses or settings.
+unsigned long long current_context_id();
+
+// Runs a set-up step once per device and context: the first time it is
+// asked for with a device current, and again once that device's context has
+// been replaced.  The step's error is returned to every caller until it is
+// retried under a new context.
+struct PerContextOnce {
+    std::mutex mu;
+    unsigned long long ctx[64] = {};
+    cudaError_t err[64] = {};
+    template <class F>
+    cudaError_t run(F set_up) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        const unsigned long long id = current_context_id();
+        std::lock_guard<std::mutex> lk(mu);
+        if (id == 0 || ctx[dev] != id) {
+            err[dev] = set_up();
+            ctx[dev] = id;
+        }
+        return err[dev];
+    }
+};
+
 // ---- benchmark accounting (not part of the method) -------------------------------
 // Every kernel launch of the library increments a process-wide counter; when
 // timing is enabled, launches of the classes below are bracketed by CUDA
 // events on their stream and their algorithmic flops/bytes are recorded.
 enum ProfClass : int {
     PROF_TC_GEMM = 0, PROF_SIMT_GEMM = 1, PROF_PANEL = 2, PROF_TRSM_DIAG = 3, PROF_SPMM = 4,
-    PROF_SIDDON = 5, PROF_OTHER = 6, PROF_SPMM32 = 7, PROF_TC_GEMM_BF16 = 8, PROF_NCLASS = 9
+    PROF_SIDDON = 5, PROF_OTHER = 6, PROF_SPMM32 = 7, PROF_TC_GEMM_BF16 = 8,
+    // out-of-core host traffic (bytes = bytes copied): V blocks streamed to
+    // the device, superpanel columns loaded, factored columns written back,
+    // and the compute stream's stalls waiting for a streamed V block
+    PROF_H2D_V = 9, PROF_H2D_COLS = 10, PROF_D2H_COLS = 11, PROF_COPY_WAIT = 12, PROF_NCLASS = 13
 };
 void count_launch(int n = 1);
 struct ProfScope {

@@ -17,14 +17,21 @@
 // process exits.  Host code cannot pass the array's name to a kernel (in host
 // code it is a host-side stand-in, not a device address), so the first call
 // on each device -- with that device current -- looks up the device addresses
-// with cudaGetSymbolAddress and keeps them.  Make that first call before any
-// stream capture.
+// with cudaGetSymbolAddress and keeps them for that device's context (a
+// context created anew, after cudaDeviceReset, is looked up again).  Make that
+// first call before any stream capture.
+//
+// Accepted kinds: 0 (FP64), 1 (FP32) and 2 (TF32); the BF16 and split
+// products (kinds 3-5) need operand copies as large as the operands and are
+// refused.  Split-K follows the allocating engine's plan, with the depth
+// reduced until the partial products fit in the room the copies leave.
 //
 // All calls share the array and keep the last call's contents; calls that
 // overlap on the GPU (two streams, two threads) race on it.  The status word
 // is cleared at the start of each call; the partial-product area is fully
 // overwritten by each split-K launch before it is read, so it needs no
-// clearing.
+// clearing.  Each call waits for its stream before returning, to read the
+// status word back.
 #include <algorithm>
 #include <mutex>
 
@@ -47,18 +54,18 @@ struct NoAllocPtrs {
 
 ct_status noalloc_setup(NoAllocPtrs *out) {
     static NoAllocPtrs per_dev[64];
-    static std::mutex mu;
+    static PerContextOnce once;
     int dev = 0;
     CT_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return CT_ERR_ARG;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!per_dev[dev].scratch) {
+    CT_CUDA(once.run([dev]() -> cudaError_t {
         void *p = nullptr, *q = nullptr;
-        CT_CUDA(cudaGetSymbolAddress(&p, g_scratch));
-        CT_CUDA(cudaGetSymbolAddress(&q, g_status));
-        per_dev[dev].scratch = (unsigned char *)p;
-        per_dev[dev].status = (DevStatus *)q;
-    }
+        per_dev[dev] = NoAllocPtrs{};
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_status);
+        if (e == cudaSuccess) per_dev[dev] = NoAllocPtrs{(unsigned char *)p, (DevStatus *)q};
+        return e;
+    }));
     *out = per_dev[dev];
     return CT_OK;
 }
@@ -125,25 +132,23 @@ extern "C" ct_status ct_gemm_noalloc(int32_t kind, char transa, char transb, int
             }
             used = abytes + bbytes;
         }
-        // split-K as in the allocating engine, capped by the room left in the array
+        // split-K as planned by the allocating engine, then made shallower
+        // until the partial products fit in the room left in the array
         const int64_t BM = tc ? 128 : (fp64 ? 64 : 128);
         const int64_t BN = tc ? 256 : (fp64 ? 64 : 128);
-        const int64_t tiles = ceil_div(M, BM) * ceil_div(N, BN);
-        const int64_t target = 2 * (int64_t)num_sms();
-        const int64_t kMinChunk = tc ? 1024 : 512;
-        int64_t splits = 1;
-        if (tiles < target)
-            splits = std::min(ceil_div(target, tiles), std::max<int64_t>(1, K / kMinChunk));
-        splits = std::min<int64_t>(splits, 64);
+        const int64_t align = tc ? 32 : 16;
+        int64_t splits, kchunk;
+        plan_splits(ceil_div(M, BM) * ceil_div(N, BN), K, tc ? 256 : 128, align, &splits, &kchunk);
         const size_t room = kScratchBytes - used;
-        while (splits > 1 && es * (size_t)(M * N * splits) > room) --splits;
+        if (splits > 1 && es * (size_t)(M * N * splits) > room) {
+            splits = std::max<int64_t>(1, (int64_t)(room / (es * (size_t)(M * N))));
+            kchunk = round_up(ceil_div(K, splits), align);
+            splits = ceil_div(K, kchunk);
+        }
         if (splits <= 1) {
             CT_TRY(tc ? gemm_tc_launch_status(g, 1, K, 0, P.status, s)
                       : gemm_simt_launch(g, 1, K, 0, s));
         } else {
-            const int64_t align = tc ? 32 : 16;
-            int64_t kchunk = round_up(ceil_div(K, splits), align);
-            splits = ceil_div(K, kchunk);
             void *part = P.scratch + used;
             GemmArgs p = g;
             p.alpha = 1.0;

@@ -1,13 +1,12 @@
 // gemm_simt.cu -- CUDA-core GEMM for the FP64 and FP32 paths, and the
 // split-K reduction shared with the tensor-core engine.
 //
-// C = alpha * op(A) * op(B) + beta * C, column-major.  Block tile BM x BN,
-// 256 threads, each owning a TM x TN register tile; op(A)/op(B) tiles staged
-// in shared memory with the M (resp. N) index fastest so the inner product
-// loop reads contiguous vectors.  FP64 on B300 runs at roughly 1/64 of the
+// C = alpha * op(A) * op(B) + beta * C, column-major.  Block tile BM x BN
+// (simt_tile.cuh); split-K over blockIdx.z.  FP64 on B300 runs at roughly 1/64 of the
 // FP32 rate, so the FP64 instance is bound by the DFMA pipe, not by memory.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "simt_tile.cuh"
 
 #include <algorithm>
 
@@ -22,72 +21,10 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(bool ta, bool tb, int64_
                                                         const T *__restrict__ B, int64_t ldb,
                                                         T beta, T *C, int64_t ldc,
                                                         int64_t split_stride) {
-    static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
-    __shared__ T As[BK][BM];
-    __shared__ T Bs[BK][BN];
-    const int tid = threadIdx.x;
-    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
-    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
     const int64_t kb = (int64_t)blockIdx.z * kchunk;
-    const int64_t ke = min(K, kb + kchunk);
-    C += (int64_t)blockIdx.z * split_stride;
-
-    T acc[TM][TN];
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-
-    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
-        // op(A) tile: element (i, kk) = A(m0+i, k0+kk) or A(k0+kk, m0+i).
-        for (int idx = tid; idx < BM * BK; idx += 256) {
-            int i, kk;
-            if (!ta) { i = idx % BM; kk = idx / BM; }
-            else { kk = idx % BK; i = idx / BK; }
-            int64_t gm = m0 + i, gk = k0 + kk;
-            T v = T(0);
-            if (gm < M && gk < ke) v = ta ? A[gk + gm * lda] : A[gm + gk * lda];
-            As[kk][i] = v;
-        }
-        // op(B) tile: element (kk, j) = B(k0+kk, n0+j) or B(n0+j, k0+kk).
-        for (int idx = tid; idx < BN * BK; idx += 256) {
-            int j, kk;
-            if (!tb) { kk = idx % BK; j = idx / BK; }
-            else { j = idx % BN; kk = idx / BN; }
-            int64_t gn = n0 + j, gk = k0 + kk;
-            T v = T(0);
-            if (gn < N && gk < ke) v = tb ? B[gn + gk * ldb] : B[gk + gn * ldb];
-            Bs[kk][j] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            T a[TM], b[TN];
-#pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
-#pragma unroll
-            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-        int64_t gn = n0 + tx * TN + j;
-        if (gn >= N) continue;
-#pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            int64_t gm = m0 + ty * TM + i;
-            if (gm >= M) continue;
-            T *c = C + gm + gn * ldc;
-            T v = alpha * acc[i][j];
-            if (beta != T(0)) v += beta * *c;
-            *c = v;
-        }
-    }
+    simt_tile<T, BM, BN, BK, TM, TN>(ta, tb, M, N, kb, min(K, kb + kchunk), alpha, A, lda, B, ldb, beta,
+                                     C + (int64_t)blockIdx.z * split_stride, ldc, (int64_t)blockIdx.x * BM,
+                                     (int64_t)blockIdx.y * BN);
 }
 
 template <typename T>
@@ -151,14 +88,13 @@ ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void 
     return CT_OK;
 }
 
-// Split-K policy: enough CTAs to cover the machine about twice, each split
-// at least kMinChunk deep.  All scratch of one call (K-major operand copies
-// for the tensor cores, then split-K partial products) lives in `ws`, which
-// belongs to the caller; nothing process-wide is used, so a captured graph
-// that replays this call references only its caller's buffers.
 // Split-K depth for a tile grid (enough CTAs to cover the machine about
 // twice, each split at least min_chunk deep, chunks multiples of align).
-static void plan_splits(int64_t tiles, int64_t K, int64_t min_chunk, int64_t align,
+// All scratch of one engine call (K-major operand copies for the tensor
+// cores, then split-K partial products) lives in the caller's `ws`; nothing
+// process-wide is used, so a captured graph that replays such a call
+// references only its caller's buffers.
+void plan_splits(int64_t tiles, int64_t K, int64_t min_chunk, int64_t align,
                         int64_t *splits_out, int64_t *kchunk_out) {
     const int64_t target = 2 * (int64_t)num_sms();
     int64_t splits = 1;

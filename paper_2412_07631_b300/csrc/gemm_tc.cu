@@ -439,13 +439,11 @@ int pick_epilogue(const GemmArgs &g, int splits, int64_t split_stride) {
 template <int OP>
 ct_status launch_tc(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
                     DevStatus *status, cudaStream_t s) {
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(gemm_tc_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        SMEM_BYTES);
-    });
-    CT_CUDA(attr_err);
+    static PerContextOnce once;  // the attribute belongs to each device's context
+    CT_CUDA(once.run([] {
+        return cudaFuncSetAttribute(gemm_tc_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES);
+    }));
     constexpr int BK = OpTraits<OP>::BK;
     CUtensorMap ma, mb, mc;
     // op(A) = A^T, A stored K x M (K contiguous): box {BK (K), 128 (M)}.
@@ -489,12 +487,14 @@ ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t 
                                : launch_tc<0>(g, splits, kchunk, split_stride, device_status(), s);
 }
 
-// Same kernel and tile choice as gemm_tc_launch (TF32), with the status word
+// Same kernels and tile choice as gemm_tc_launch (TF32), with the status word
 // given by the caller and no accounting scope; used by the allocation-free
 // entry point.
 ct_status gemm_tc_launch_status(const GemmArgs &g, int splits, int64_t kchunk,
                                 int64_t split_stride, DevStatus *status, cudaStream_t s) {
     if (g.kind != GEMM_TF32 || !g.ta || g.tb) return CT_ERR_ARG;
+    if (g.K > kTmaAddMaxK && gemm_pair_tiles(g.M, g.N) * splits >= num_sms() / 2)
+        return gemm_pair_launch(g, splits, kchunk, split_stride, s, status);
     return launch_tc<0>(g, splits, kchunk, split_stride, status, s);
 }
 

@@ -409,15 +409,20 @@ ct_status make_map2(CUtensorMap *map, bool bf16, const void *base, int64_t rows,
     return CT_OK;
 }
 
-// Co-resident 2-CTA clusters of this kernel (the persistent grid), per kernel.
+// Co-resident 2-CTA clusters of this kernel (the persistent grid), per kernel;
+// the shared-memory attribute and the occupancy query run once per device and
+// context (both belong to the context).
 template <int OP>
 int max_pairs() {
-    static std::once_flag once;
-    static int pairs = 0;
-    std::call_once(once, [] {
-        if (cudaFuncSetAttribute(gemm_pair_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM_BYTES) != cudaSuccess)
-            return;
+    static PerContextOnce once;
+    static int pairs[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    const cudaError_t e = once.run([dev]() -> cudaError_t {
+        pairs[dev] = 0;
+        cudaError_t err = cudaFuncSetAttribute(gemm_pair_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               SMEM_BYTES);
+        if (err != cudaSuccess) return err;
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -430,14 +435,16 @@ int max_pairs() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, gemm_pair_kernel<OP>, &cfg) == cudaSuccess) pairs = n;
+        err = cudaOccupancyMaxActiveClusters(&n, gemm_pair_kernel<OP>, &cfg);
+        if (err == cudaSuccess) pairs[dev] = n;
+        return err;
     });
-    return pairs;
+    return e == cudaSuccess ? pairs[dev] : 0;
 }
 
 template <int OP>
 ct_status launch_pair(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
-                      cudaStream_t s) {
+                      DevStatus *status, cudaStream_t s) {
     const int pairs_max = max_pairs<OP>();
     if (pairs_max <= 0) {
         cudaGetLastError();
@@ -464,7 +471,7 @@ ct_status launch_pair(const GemmArgs &g, int splits, int64_t kchunk, int64_t spl
     cfg.numAttrs = 1;
     CT_CUDA(cudaLaunchKernelEx(&cfg, gemm_pair_kernel<OP>, ma, mb, g.M, g.N, g.K, kchunk, splits,
                                (float)g.alpha, (float)g.beta, (float *)g.C, g.ldc, split_stride,
-                               device_status()));
+                               status));
     count_launch();
     return CT_OK;
 }
@@ -472,12 +479,14 @@ ct_status launch_pair(const GemmArgs &g, int splits, int64_t kchunk, int64_t spl
 }  // namespace
 
 // Paired (2-SM) launch of a K-major TF32/BF16 product; callers pick it when
-// the product has enough 256 x 256 tiles to occupy the machine.
+// the product has enough 256 x 256 tiles to occupy the machine.  Device
+// errors go to `status` (NULL: the library's status word).
 ct_status gemm_pair_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
-                           cudaStream_t s) {
+                           cudaStream_t s, DevStatus *status) {
     if ((g.kind != GEMM_TF32 && g.kind != GEMM_BF16) || !g.ta || g.tb) return CT_ERR_ARG;
-    return g.kind == GEMM_BF16 ? launch_pair<1>(g, splits, kchunk, split_stride, s)
-                               : launch_pair<0>(g, splits, kchunk, split_stride, s);
+    if (!status) status = device_status();
+    return g.kind == GEMM_BF16 ? launch_pair<1>(g, splits, kchunk, split_stride, status, s)
+                               : launch_pair<0>(g, splits, kchunk, split_stride, status, s);
 }
 
 int64_t gemm_pair_tiles(int64_t M, int64_t N) { return ceil_div(M, 2 * BMC) * ceil_div(N, BN); }

@@ -76,6 +76,11 @@ ct_status gemm(const GemmArgs &g, Scratch &ws, cudaStream_t s);
 
 // Kernel-level launchers (no split logic): partial products over K range
 // [k0, k0 + kc) of split z written to C + z*split_stride (alpha/beta applied).
+// Split-K plan of the GEMM engine: the number of K splits and the depth of
+// each (a multiple of align, at least min_chunk) for a grid of `tiles` output
+// tiles, so that about two CTAs per SM are busy.
+void plan_splits(int64_t tiles, int64_t K, int64_t min_chunk, int64_t align, int64_t *splits_out,
+                 int64_t *kchunk_out);
 ct_status gemm_simt_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
                            cudaStream_t s);
 ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
@@ -83,7 +88,7 @@ ct_status gemm_tc_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t 
 // The same product on SM pairs (2-CTA clusters, 256 x 256 tiles); and the
 // number of such tiles of an M x N output.
 ct_status gemm_pair_launch(const GemmArgs &g, int splits, int64_t kchunk, int64_t split_stride,
-                           cudaStream_t s);
+                           cudaStream_t s, DevStatus *status = nullptr);
 int64_t gemm_pair_tiles(int64_t M, int64_t N);
 // As gemm_tc_launch, with an explicit device status word and no accounting.
 ct_status gemm_tc_launch_status(const GemmArgs &g, int splits, int64_t kchunk,
@@ -151,6 +156,10 @@ ct_status transpose_d(const double *src, int64_t lds, double *dst, int64_t ldd, 
                       int64_t cols, cudaStream_t s);
 ct_status fill_zero_2d(bool fp64, void *dst, int64_t ld, int64_t rows, int64_t cols,
                        cudaStream_t s);
+// Device status DEV_NONFINITE (site `where`) if the rows x cols block (kind
+// 0 float, 1 double; column-major, leading dimension ld) holds a NaN or Inf.
+ct_status scan_finite(int kind, const void *A, int64_t ld, int64_t rows, int64_t cols, int where,
+                      cudaStream_t s);
 ct_status rdiag_minmax(bool fp64, const void *A, int64_t lda, int64_t n, double *dmin_dmax_dev,
                        cudaStream_t s);
 

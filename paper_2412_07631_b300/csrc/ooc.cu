@@ -266,6 +266,7 @@ ct_status load_cols(ct_factor f, int64_t c0, int64_t c1, int64_t rows, void *sp,
     const size_t es = f->es();
     const size_t col_bytes = es * (size_t)f->lda;
     DiskStore *d = f->store;
+    ProfScope prof(PROF_H2D_COLS, s, 0.0, (double)es * rows * (c1 - c0));
     if (!d) {
         CT_CUDA(cudaMemcpy2DAsync(sp, col_bytes, (char *)f->VR_host + col_bytes * (size_t)c0, col_bytes,
                                   es * (size_t)rows, c1 - c0, cudaMemcpyHostToDevice, s));
@@ -294,6 +295,7 @@ ct_status store_cols(ct_factor f, int64_t c0, int64_t c1, int64_t rows, const vo
     const size_t es = f->es();
     const size_t col_bytes = es * (size_t)f->lda;
     DiskStore *d = f->store;
+    ProfScope prof(PROF_D2H_COLS, s, 0.0, (double)es * rows * (c1 - c0));
     if (!d) {
         CT_CUDA(cudaMemcpy2DAsync((char *)f->VR_host + col_bytes * (size_t)c0, col_bytes, sp, col_bytes,
                                   es * (size_t)rows, c1 - c0, cudaMemcpyDeviceToHost, s));
@@ -611,7 +613,12 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
         if (J0 > 0 && (st = prefetch(0)) != CT_OK) return fail(st);
         for (int64_t J = 0; J < J0; ++J) {
             const int b = (int)(J & 1);
-            if (cudaStreamWaitEvent(s, ready[b], 0) != cudaSuccess) return fail(CT_ERR_CUDA);
+            {
+                // timed (when accounting is on) from before to after the wait:
+                // the stall of the compute stream on this block's copy
+                ProfScope stall(PROF_COPY_WAIT, s, 0.0, 0.0);
+                if (cudaStreamWaitEvent(s, ready[b], 0) != cudaSuccess) return fail(CT_ERR_CUDA);
+            }
             const int64_t j = J * NB;
             const int w = (int)std::min<int64_t>(NB, f->n - j);
             const void *VtJ = (char *)f->Vtop + es * (size_t)J * NB * NB;

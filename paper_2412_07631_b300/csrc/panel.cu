@@ -674,12 +674,9 @@ ct_status panel_launch(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau,
     const size_t slab = (size_t)rows_per * nb * sizeof(T);
     const int use_smem = slab <= 200 * 1024 ? 1 : 0;
     const size_t dyn = use_smem ? slab : 0;
-    static bool attr[2] = {false, false};
+    static PerContextOnce attr;  // per instantiation; the attribute belongs to each device's context
     auto fn = panel_qr_kernel<T, NB>;
-    if (!attr[NB == 32]) {
-        CT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr[NB == 32] = true;
-    }
+    CT_CUDA(attr.run([&] { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); }));
     int per_sm = 0;
     CT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PANEL_THREADS, dyn));
     if (per_sm * sms < G) {
@@ -859,11 +856,10 @@ ct_status t_assemble(int64_t o, int wp, const float *G, int64_t ldg, float *Tm, 
     if (wp > 32) return CT_ERR_ARG;
     const size_t smem = sizeof(float) * (size_t)o * 33;
     if (smem > 200 * 1024) return CT_ERR_UNSUPPORTED;
-    static bool attr = false;
-    if (!attr) {
-        CT_CUDA(cudaFuncSetAttribute(tassemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    static PerContextOnce attr;
+    CT_CUDA(attr.run([] {
+        return cudaFuncSetAttribute(tassemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }));
     tassemble_kernel<<<(unsigned)ceil_div(o, 32), 256, smem, s>>>(o, wp, G, ldg, Tm, ldt);
     count_launch();
     CT_CUDA(cudaGetLastError());

@@ -415,11 +415,8 @@ ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, 
                       int64_t rows_per, int *fallback, float *Tp, float *Vtp, int64_t ldt, cudaStream_t s) {
     auto fn = panel_gram_kernel<RPT>;
     const size_t dyn = sizeof(float) * GQ_LD * RPT * GQ_THREADS;
-    static bool attr = false;
-    if (!attr) {
-        CT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-        attr = true;
-    }
+    static PerContextOnce attr;  // the attribute belongs to each device's context
+    CT_CUDA(attr.run([&] { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn); }));
     int per_sm = 0;
     CT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GQ_THREADS, dyn));
     if (per_sm * num_sms() < G) {

@@ -62,6 +62,53 @@ ct_status gram(ct_factor f, int64_t j, int w, const void *Vt, void *G, cudaStrea
     return CT_OK;
 }
 
+// The top-block part of a narrow (w <= 32 columns) block reflector applied
+// to ncols columns, one warp per column, lane i holding row i:
+//   w  = W[:, c] + Vt^T C_top[:, c]     (W = Vb^T C_b from the rows below, or 0)
+//   w2 = op(T) w,   C_top[:, c] -= Vt w2,   W2[:, c] = w2
+// Vt (unit lower, explicit) and T (upper) are staged in shared memory; every
+// sum runs over r in ascending order.  Replaces three tiny GEMM launches per
+// panel update by one.
+template <typename T>
+__global__ void __launch_bounds__(256) top_block_kernel(int w, int64_t ncols, const T *Vt, const T *Tm,
+                                                        int64_t ldt, bool trans_t, const T *W, T *W2,
+                                                        int64_t ldw, T *C, int64_t ldc) {
+    __shared__ T sV[32][33], sT[32][33];
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int r = idx % 32, c = idx / 32;
+        const bool in = r < w && c < w;
+        sV[r][c] = in ? Vt[r + (int64_t)c * ldt] : T(0);
+        // sT[r][c] = op(T)(r, c)
+        sT[r][c] = in ? (trans_t ? Tm[c + (int64_t)r * ldt] : Tm[r + (int64_t)c * ldt]) : T(0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t col = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (col >= ncols) return;
+    const T cv = lane < w ? C[lane + col * ldc] : T(0);
+    T acc = lane < w ? W[lane + col * ldw] : T(0);
+    for (int r = 0; r < w; ++r) acc += sV[r][lane] * __shfl_sync(0xffffffffu, cv, r);  // (Vt^T C)_lane
+    T w2 = T(0);
+    for (int r = 0; r < w; ++r) w2 += sT[lane][r] * __shfl_sync(0xffffffffu, acc, r);   // (op(T) w)_lane
+    T upd = T(0);
+    for (int r = 0; r < w; ++r) upd += sV[lane][r] * __shfl_sync(0xffffffffu, w2, r);   // (Vt w2)_lane
+    if (lane < w) {
+        C[lane + col * ldc] = cv - upd;
+        W2[lane + col * ldw] = w2;
+    }
+}
+
+template <typename T>
+ct_status top_block(int w, int64_t ncols, const void *Vt, const void *Tm, int64_t ldt, bool trans_t,
+                    const void *W, void *W2, int64_t ldw, void *C, int64_t ldc, cudaStream_t s) {
+    const unsigned grid = (unsigned)ceil_div(ncols, 8);
+    top_block_kernel<T><<<grid, 256, 0, s>>>(w, ncols, (const T *)Vt, (const T *)Tm, ldt, trans_t,
+                                             (const T *)W, (T *)W2, ldw, (T *)C, ldc);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
 }  // namespace
 
 // C[j:M, 0:ncols] <- (I - V op(T) V^T) C, op(T) = T^T for Q^T, T for Q.
@@ -83,6 +130,25 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     const void *Vb = vb ? vb : at(f->VR, j + w, j, f->lda, es);
     const int64_t ldV = vb ? ldvb : f->lda;
     void *Cb = (char *)C + es * (size_t)w;
+    if (w <= 32) {
+        // narrow reflector (a panel's): the bulk products over the rows below
+        // on the engine, the w x w top-block work fused into one small kernel
+        if (kb > 0) {
+            GemmArgs g = mk(f, true, false, w, ncols, kb, 1.0, Vb, ldV, Cb, ldc, 0.0, W, NB);
+            g.kind = big;
+            CT_TRY(gemm(g, f->gemm_ws, s));
+        } else {
+            CT_TRY(fill_zero_2d(f->fp64, W, NB, w, ncols, s));
+        }
+        CT_TRY(f->fp64 ? top_block<double>(w, ncols, Vt, T, NB, qt, W, W2, NB, C, ldc, s)
+                       : top_block<float>(w, ncols, Vt, T, NB, qt, W, W2, NB, C, ldc, s));
+        if (kb > 0) {
+            GemmArgs g = mk(f, false, false, kb, ncols, w, -1.0, Vb, ldV, W2, NB, 1.0, Cb, ldc);
+            g.kind = big;
+            CT_TRY(gemm(g, f->gemm_ws, s));
+        }
+        return CT_OK;
+    }
     // W = V^T C
     CT_TRY(gemm(mk(f, true, false, w, ncols, w, 1.0, Vt, NB, C, ldc, 0.0, W, NB), f->gemm_ws, s));
     if (kb > 0) {
@@ -223,6 +289,7 @@ ct_status stage_v_block(ct_factor f, int64_t J, void *dst, int64_t *ldd, cudaStr
     const int64_t kb = f->row_end(j + w) - j - w;
     *ldd = round_up(std::max<int64_t>(kb, 1), 32);
     if (kb <= 0) return CT_OK;
+    ProfScope prof(PROF_H2D_V, s, 0.0, (double)es * kb * w);
     if (f->store) {  // disk tier: block J from the cache (read on demand if missing)
         DiskStore *d = f->store;
         int slot = -1;

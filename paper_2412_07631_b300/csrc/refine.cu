@@ -277,12 +277,15 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         if (have_dd) CT_CUDA(cudaMemcpyAsync(h_dd, dd, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CT_CUDA(cudaStreamSynchronize(st));
         double worst = 0.0;
+        bool bad_data = false;  // NaN/Inf in the residual or the iterate
         for (int32_t sl = 0; sl < k; ++sl) {
+            if (!std::isfinite(h_gg[sl]) || !std::isfinite(h_xx[sl]) || (have_dd && !std::isfinite(h_dd[sl])))
+                bad_data = true;
             const double xn = std::max(std::sqrt(h_xx[sl]), 1e-300);
             double v;
             if (use_cert) v = std::sqrt(h_gg[sl]) / (lam * xn);
-            else v = have_dd ? std::sqrt(h_dd[sl]) / xn : INFINITY;
-            if (!std::isfinite(v)) { worst = INFINITY; break; }
+            else v = have_dd ? std::sqrt(h_dd[sl]) / xn : INFINITY;  // no measure before a step
+            if (!std::isfinite(v)) { worst = INFINITY; continue; }
             worst = std::max(worst, v);
         }
         last = worst;
@@ -290,7 +293,8 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
             converged = true;
             break;
         }
-        if (outer >= max_outer) break;
+        // non-finite data cannot be refined away
+        if (outer >= max_outer || bad_data) break;
         ++outer;
         // inner CG from y = 0: s = R^-T g with the FP64 back-projection g = A~^T r
         to_f32_kernel<<<bn, 256, 0, st>>>((int64_t)nk, g, u);
@@ -436,6 +440,10 @@ ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t 
         count_launch();
         CT_TRY(measure(true));
         last = stop_value(true);
+        bool bad_data = false;  // NaN/Inf in the residual or the iterate: no step can fix it
+        for (int32_t s2 = 0; s2 < k; ++s2)
+            if (!std::isfinite(h_rr[s2]) || !std::isfinite(h_uu[s2])) bad_data = true;
+        if (bad_data) break;
         if (last <= tol) {
             if (!use_cert) { converged = true; break; }
             CT_TRY(normal(u, w));                              // verify on the true residual

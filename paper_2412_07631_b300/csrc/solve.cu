@@ -30,6 +30,7 @@ ct_status solve_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X,
     const int64_t M = f->M, m = f->m, n = f->n, ldbt = f->lda;
     CT_TRY(f->Bt.ensure(f->es() * (size_t)ldbt * k));
     void *Bt = f->Bt.ptr;
+    CT_TRY(scan_finite(io_kind(f), B, ldb, m, k, 40, s));  // NaN/Inf sinograms: CT_ERR_NONFINITE
     CT_TRY(copy_convert_2d(io_kind(f), B, ldb, fac_kind(f), Bt, ldbt, m, k, s));
     if (M > m) CT_TRY(fill_zero_2d(f->fp64, (char *)Bt + f->es() * m, ldbt, M - m, k, s));
     CT_TRY(run_graphed(f, f->g_direct, graph_key(f, k, Bt), s,
@@ -52,6 +53,7 @@ ct_status adjoint_refine_run(ct_factor f, const void *gX, int64_t ldgx, int32_t 
 
 ct_status adjoint_run(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB, int64_t ldgb,
                       const ct_opts *o, cudaStream_t s, ct_solve_info *info) {
+    CT_TRY(scan_finite(io_kind(f), gX, ldgx, f->n, k, 41, s));  // NaN/Inf gradients: CT_ERR_NONFINITE
     if (is_refine_prec(f->prec) && !(o && o->refine_max_iter < 0))
         return adjoint_refine_run(f, gX, ldgx, k, gB, ldgb, o, s, info);
     const int64_t M = f->M, m = f->m, n = f->n, ldbt = f->lda;

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "handles.cuh"
 #include "kernels.cuh"
+#include "simt_tile.cuh"
 
 namespace ctqr {
 
@@ -63,12 +64,11 @@ template <typename T, int BS>
 ct_status diag_solve(bool trans, int ni, const T *R, int64_t ldr, T *C, int64_t ldc, int64_t k,
                      cudaStream_t s) {
     const size_t smem = sizeof(T) * ((size_t)BS * BS + (size_t)BS * (KC + 1));
-    static bool attr = false;
-    if (!attr) {
-        CT_CUDA(cudaFuncSetAttribute(diag_solve_kernel<T, BS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static PerContextOnce attr;
+    CT_CUDA(attr.run([&] {
+        return cudaFuncSetAttribute(diag_solve_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    }));
     ProfScope prof(PROF_TRSM_DIAG, s, (double)ni * ni * k, sizeof(T) * ((double)ni * ni + 2.0 * ni * k));
     diag_solve_kernel<T, BS><<<(unsigned)ceil_div(k, KC), KC, smem, s>>>(trans, ni, R, ldr, C, ldc, k);
     count_launch();
@@ -115,12 +115,11 @@ __global__ void __launch_bounds__(TB) diag_inverse_kernel(int64_t n, const T *R,
 template <typename T, int TB>
 ct_status diag_inverse_launch(int64_t n, const T *R, int64_t ldr, T *Rinv, T *RinvT, cudaStream_t s) {
     const size_t smem = sizeof(T) * ((size_t)TB * TB + (size_t)TB * (TB + 1));
-    static bool attr = false;
-    if (!attr) {
-        CT_CUDA(cudaFuncSetAttribute(diag_inverse_kernel<T, TB>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static PerContextOnce attr;
+    CT_CUDA(attr.run([&] {
+        return cudaFuncSetAttribute(diag_inverse_kernel<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    }));
     diag_inverse_kernel<T, TB><<<(unsigned)ceil_div(n, TB), TB, smem, s>>>(n, R, ldr, Rinv, RinvT);
     count_launch();
     CT_CUDA(cudaGetLastError());
@@ -142,18 +141,51 @@ __global__ void scatter_diag_kernel(int64_t nblk, int TB, int SB, const T *Rinv,
     }
 }
 
+// One doubling level of the superblock inverses, for every superblock and
+// every pair of b x b diagonal blocks at once (blockIdx.z = superblock t x
+// pairs_per_sb + pair i).  The pair starting at local row p of superblock t
+// holds inv(A) and inv(C) on the diagonal of RinvB_t already; with the
+// coupling block R12 = R[p:p+b, p+b:p+b+bb] of R,
+//   stage 1:  Y = R12 inv(C)                        (b x bb, scratch of the pair)
+//   stage 2:  inv block (p, p+b) of RinvB_t = -inv(A) Y.
+// inv(C) and inv(A) are upper triangular, so the k range of a tile stops at
+// the tile's last column (stage 1) or starts at its first row (stage 2): the
+// terms left out are exact zeros.
+template <int STAGE>
+__global__ void __launch_bounds__(256) inv_double_kernel(int64_t n, int64_t SB, int64_t b,
+                                                         int64_t pairs_per_sb, const float *R,
+                                                         int64_t ldr, float *RinvB, float *Y) {
+    constexpr int BT = 128;
+    const int64_t z = blockIdx.z;
+    const int64_t t = z / pairs_per_sb, i = z - t * pairs_per_sb;
+    const int64_t s0 = t * SB, s1 = min(n, s0 + SB);
+    const int64_t pl = 2 * b * i, p = s0 + pl;
+    if (p + b >= s1) return;
+    const int64_t bb = min(b, s1 - p - b);
+    const int64_t m0 = (int64_t)blockIdx.x * BT, n0 = (int64_t)blockIdx.y * BT;
+    if (m0 >= b || n0 >= bb) return;
+    float *inv = RinvB + t * SB * SB;
+    float *Yz = Y + z * b * b;  // ld b
+    if (STAGE == 1)
+        simt_tile<float, BT, BT, 8, 8, 8>(false, false, b, bb, 0, min(bb, n0 + BT), 1.0f,
+                                           R + p + (p + b) * ldr, ldr, inv + (pl + b) + (pl + b) * SB, SB,
+                                           0.0f, Yz, b, m0, n0);
+    else
+        simt_tile<float, BT, BT, 8, 8, 8>(false, false, b, bb, m0, b, -1.0f, inv + pl + pl * SB, SB, Yz, b,
+                                           0.0f, inv + pl + (pl + b) * SB, SB, m0, n0);
+}
+
 }  // namespace
 
 // Tensor-core path: inverses of the SB x SB diagonal superblocks of R, by
 // doubling from the TB x TB inverses,
 //   inv([A B; 0 C]) = [inv(A), -inv(A) B inv(C); 0, inv(C)],
 // with the products on the FP32 CUDA cores (exact transposes of each other
-// are kept for R^-1 and R^-T, so the two applications stay adjoint).  The
-// superblocks are independent: their chains of small products run on
-// kInvStreams side streams (each with its own scratch), forked from and
-// joined back to the caller's stream.
+// are kept for R^-1 and R^-T, so the two applications stay adjoint).  Each
+// doubling level is two launches covering every superblock and every block
+// pair of that level (inv_double_kernel), so the grid fills the machine even
+// where one product is a single tile.
 static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
-    constexpr int kInvStreams = 8;
     const int TB = f->trsm_tb;
     const int64_t n = f->n;
     const int SB = (int)std::min<int64_t>(2048, round_up(n, TB));
@@ -166,60 +198,31 @@ static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
                                                               (float *)f->RinvB);
     count_launch();
     CT_CUDA(cudaGetLastError());
-    auto inv_at = [&](int64_t t, int64_t r, int64_t c) {
-        return (char *)f->RinvB + es * (t * blk + (size_t)r + (size_t)c * SB);
-    };
-    const int ns = (int)std::min<int64_t>(kInvStreams, nsb);
-    Scratch ws[kInvStreams], ys[kInvStreams];
-    cudaStream_t st[kInvStreams] = {};
-    cudaEvent_t ev[kInvStreams + 1] = {};
-    ct_status rc = CT_OK;
-    auto run = [&]() -> ct_status {
-        CT_CUDA(cudaEventCreateWithFlags(&ev[kInvStreams], cudaEventDisableTiming));
-        CT_CUDA(cudaEventRecord(ev[kInvStreams], s));
-        for (int i = 0; i < ns; ++i) {
-            CT_CUDA(cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking));
-            CT_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
-            CT_CUDA(cudaStreamWaitEvent(st[i], ev[kInvStreams], 0));
-            CT_TRY(ys[i].ensure(es * blk));
-        }
-        for (int64_t t = 0; t < nsb; ++t) {
-            const int i = (int)(t % ns);
-            void *Y = ys[i].ptr;
-            const int64_t s0 = t * SB, s1 = std::min<int64_t>(n, s0 + SB);
-            for (int64_t b = TB; b < SB; b *= 2) {
-                for (int64_t p = s0; p + b < s1; p += 2 * b) {
-                    const int64_t bb = std::min<int64_t>(b, s1 - p - b);
-                    // Y = R[p:p+b, p+b:p+b+bb] inv(C)
-                    GemmArgs g1{GEMM_F32, false, false, b, bb, bb, 1.0,
-                                (char *)f->Rm + es * (size_t)(p + (p + b) * f->ldr), f->ldr,
-                                inv_at(t, p + b - s0, p + b - s0), SB, 0.0, Y, SB};
-                    CT_TRY(gemm(g1, ws[i], st[i]));
-                    // inv block (p, p+b) = -inv(A) Y
-                    GemmArgs g2{GEMM_F32, false, false, b, bb, b, -1.0, inv_at(t, p - s0, p - s0), SB, Y, SB,
-                                0.0, inv_at(t, p - s0, p + b - s0), SB};
-                    CT_TRY(gemm(g2, ws[i], st[i]));
-                }
-            }
-            CT_TRY(transpose_any(0, (char *)f->RinvB + es * t * blk, SB, 0, (char *)f->RinvTB + es * t * blk,
-                                 SB, SB, SB, st[i]));
-        }
-        for (int i = 0; i < ns; ++i) {
-            CT_CUDA(cudaEventRecord(ev[i], st[i]));
-            CT_CUDA(cudaStreamWaitEvent(s, ev[i], 0));
-        }
-        return CT_OK;
-    };
-    rc = run();
-    // the side streams' work is complete before their scratch goes away
-    for (int i = 0; i < ns; ++i)
-        if (st[i]) cudaStreamSynchronize(st[i]);
-    for (int i = 0; i < ns; ++i) {
-        if (st[i]) cudaStreamDestroy(st[i]);
-        if (ev[i]) cudaEventDestroy(ev[i]);
+    // scratch Y: one b x b block per pair of a level (pairs of a superblock:
+    // ceil(SB / 2b), the last one possibly ragged or empty)
+    int64_t ymax = 1;
+    for (int64_t b = TB; b < SB; b *= 2) ymax = std::max(ymax, nsb * ceil_div(SB, 2 * b) * b * b);
+    Scratch ys;
+    CT_TRY(ys.ensure(sizeof(float) * (size_t)ymax));
+    for (int64_t b = TB; b < SB; b *= 2) {
+        const int64_t pairs = ceil_div(SB, 2 * b);
+        const int64_t tiles = ceil_div(b, 128);
+        dim3 grid((unsigned)tiles, (unsigned)tiles, (unsigned)(nsb * pairs));
+        const double fl = 2.0 * (double)nsb * pairs * b * b * b;  // both stages, triangular halves
+        ProfScope prof(PROF_SIMT_GEMM, s, fl, 4.0 * 4.0 * (double)nsb * pairs * b * b, b, b, b, nsb * pairs);
+        inv_double_kernel<1><<<grid, 256, 0, s>>>(n, SB, b, pairs, (const float *)f->Rm, f->ldr,
+                                                   (float *)f->RinvB, (float *)ys.ptr);
+        count_launch();
+        inv_double_kernel<2><<<grid, 256, 0, s>>>(n, SB, b, pairs, (const float *)f->Rm, f->ldr,
+                                                   (float *)f->RinvB, (float *)ys.ptr);
+        count_launch();
+        CT_CUDA(cudaGetLastError());
     }
-    if (ev[kInvStreams]) cudaEventDestroy(ev[kInvStreams]);
-    CT_TRY(rc);
+    for (int64_t t = 0; t < nsb; ++t)
+        CT_TRY(transpose_any(0, (char *)f->RinvB + es * t * blk, SB, 0, (char *)f->RinvTB + es * t * blk, SB,
+                             SB, SB, s));
+    // the scratch goes away with this call: its last readers must be done
+    CT_CUDA(cudaStreamSynchronize(s));
     f->trsm_sb = SB;
     return CT_OK;
 }

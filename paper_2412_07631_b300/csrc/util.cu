@@ -82,6 +82,22 @@ __global__ void fill_zero_kernel(T *dst, int64_t ld, int64_t rows, int64_t cols)
     dst[i + j * ld] = T(0);
 }
 
+// Raises DEV_NONFINITE (site `where`) if any element of the rows x cols
+// column-major block is NaN or Inf.  Grid-stride; one status write at most
+// per warp that meets one.
+template <typename T>
+__global__ void scan_finite_kernel(const T *A, int64_t ld, int64_t rows, int64_t cols, int where,
+                                   DevStatus *st) {
+    const int64_t total = rows * cols;
+    bool bad = false;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx % rows, j = idx / rows;
+        if (!isfinite(A[i + j * ld])) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(st, DEV_NONFINITE, where, 0);
+}
+
 template <typename T>
 __global__ void rdiag_minmax_kernel(const T *A, int64_t lda, int64_t n, double *out,
                                     DevStatus *st) {
@@ -289,6 +305,18 @@ ct_status fill_zero_2d(bool fp64, void *dst, int64_t ld, int64_t rows, int64_t c
     const unsigned b = (unsigned)ceil_div(total, 256);
     if (fp64) fill_zero_kernel<double><<<b, 256, 0, s>>>((double *)dst, ld, rows, cols);
     else fill_zero_kernel<float><<<b, 256, 0, s>>>((float *)dst, ld, rows, cols);
+    count_launch();
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status scan_finite(int kind, const void *A, int64_t ld, int64_t rows, int64_t cols, int where,
+                      cudaStream_t s) {
+    const int64_t total = rows * cols;
+    if (total == 0) return CT_OK;
+    const unsigned b = (unsigned)std::min<int64_t>(ceil_div(total, 256), 8 * (int64_t)num_sms());
+    if (kind == 1) scan_finite_kernel<double><<<b, 256, 0, s>>>((const double *)A, ld, rows, cols, where, device_status());
+    else scan_finite_kernel<float><<<b, 256, 0, s>>>((const float *)A, ld, rows, cols, where, device_status());
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;

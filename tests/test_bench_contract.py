@@ -135,3 +135,72 @@ def test_roofline_arithmetic():
     assert r["bound"] == "alu" and r["achieved"] == pytest.approx(50.0)
     assert r["peak"] == pytest.approx(148 * 128 * 2 * 2.032e9 / 1e12)
     assert bench.roofline_of(prof, "fp64", peaks, "measured")["peak"] == 1.25
+
+
+def test_roofline_uses_measured_tf32_peak():
+    peaks = {"bf16_tflops_sustained": 1357.3, "tf32_tflops_sustained": 740.0, "tf32_how": "test"}
+    prof = _prof(tc_gemm=(500.0, 2.0e14, 900))
+    r = bench.roofline_of(prof, "tf32", peaks, "measured")
+    assert r["peak"] == 740.0 and r["frac"] == pytest.approx(400.0 / 740.0)
+    assert "measured tf32" in r["peak_source"]
+
+
+def test_accuracy_figures_against_the_oracle(oracle_mod):
+    """The line's accuracy figures on a small case: the residual
+    ||A X - B||_F / ||B||_F equals the one formed with the oracle's dense A
+    (ray rows), and the per-slice SNR, RMSE and PSNR equal the oracle's
+    quality() (Sec. 3.1.3 equations) averaged over the slices."""
+    import numpy as np
+    from paper_2412_07631_b300 import synth
+    O = oracle_mod
+    g = O.Geometry(10, 16, 15, sqrt_lambda=0.05)
+    csr = O.siddon_csr(g)
+    Xt = synth.phantom_batch(10, 3, 8)
+    B = synth.poisson_sinogram(O.forward(csr, Xt), 10, 1e4, seed=5)
+    X, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    A = O.dense_system(g, csr)[: g.m]
+    want = np.linalg.norm(A @ X - B) / np.linalg.norm(B)
+    got = bench.residual_rel(O.forward(csr, X).T, B.T)
+    assert got == pytest.approx(want, rel=1e-12)
+    q = bench.quality_of(Xt, X)
+    per = [O.quality(Xt[:, s], X[:, s]) for s in range(3)]
+    assert q["snr_mean"] == pytest.approx(np.mean([p["snr"] for p in per]), rel=1e-12)
+    assert q["rmse_mean"] == pytest.approx(np.mean([p["rmse"] for p in per]), rel=1e-12)
+    assert q["psnr_mean"] == pytest.approx(np.mean([p["psnr"] for p in per]), rel=1e-12)
+    # consistent data: the residual of the exact least-squares image of
+    # noiseless sinograms is the lambda bias alone, far below the noisy one
+    P = O.forward(csr, Xt)
+    X0, _, _ = O.qr_solve(g, O.dense_system(g, csr), P)
+    assert bench.residual_rel(O.forward(csr, X0).T, P.T) < 0.1 * got
+
+
+def test_solve_roofline_arithmetic():
+    """floor = max(direct-solve flops / tensor peak, factor bytes / HBM
+    peak); frac = measured slices/s over k / floor."""
+    peaks = {"bf16_tflops_sustained": 1357.3, "tf32_tflops_sustained": 700.0, "hbm_gbs": 6500.0}
+    prof = _prof(tc_gemm=(300.0, 1.5e14, 100), spmm_fp64=(250.0, 3.0e11, 10))
+    ns, nv, nb, sl, k, _, _ = bench.WORKLOADS["c3"]
+    M, n, _, solve_fl = bench.flops_of(ns, nv, nb, sl, k)
+    r = bench.solve_roofline_of(prof, 900.0, k, M, n, solve_fl, "bf16", peaks)
+    floor = max(solve_fl / 700e12, M * n * 4 / 6500e9)
+    assert r["bound"] == "tensor" and r["floor_ms"] == pytest.approx(floor * 1e3)
+    assert r["frac"] == pytest.approx((k / 0.9) / (k / floor))
+    assert r["classes"]["tc_gemm"]["achieved_tflops"] == pytest.approx(500.0)
+    assert r["classes"]["spmm_fp64"]["frac"] == pytest.approx(1.2 / 1.25)
+    r = bench.solve_roofline_of(prof, 900.0, k, M, n, solve_fl, "fp64", peaks)
+    assert r["bound"] == "alu" and r["floor_ms"] == pytest.approx(solve_fl / 1.25e12 * 1e3)
+
+
+def test_host_link_arithmetic():
+    """Out-of-core copy evidence: GB/s per copy class, overlap = 1 - stall /
+    streaming time, link floor = bytes over the measured copy rates."""
+    prof = _prof(h2d_v=(400.0, 0.0, 20), h2d_cols=(100.0, 0.0, 2), d2h_cols=(120.0, 0.0, 2),
+                 copy_wait=(40.0, 0.0, 20))
+    prof["h2d_v"]["bytes"], prof["h2d_cols"]["bytes"], prof["d2h_cols"]["bytes"] = 20e9, 5e9, 5e9
+    link = {"h2d_gbs": 50.0, "d2h_gbs": 25.0}
+    r = bench.host_link_of(prof, 2000.0, link)
+    assert r["h2d_v"]["gbs"] == pytest.approx(50.0) and r["d2h_cols"]["gbs"] == pytest.approx(5e9 / 0.12 / 1e9)
+    assert r["overlap"] == pytest.approx(0.9)
+    assert r["link_floor_ms"] == pytest.approx((25e9 / 50e9 + 5e9 / 25e9) * 1e3)
+    assert r["link_floor_frac_of_qr"] == pytest.approx(700.0 / 2000.0)
+    assert bench.host_link_of(_prof(), 1.0, link) is None

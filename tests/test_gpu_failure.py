@@ -9,9 +9,14 @@
   16, R with exact zeros on its diagonal) is reported as CT_ERR_RANK by the
   |R_jj| >= n u max|R_jj| test, with the factor kept for inspection.
 * Refinement stopped short of its tolerance returns CT_ERR_NOCONV with the
-  best iterate written and its stopping measure reported; a sinogram with a
-  NaN gives an infinite stopping measure and CT_ERR_NOCONV instead of a
-  silently wrong image.  The same factor then solves normally."""
+  best iterate written and its stopping measure reported.  The same factor
+  then solves normally.
+* Non-finite data is reported, not turned into a silently wrong image: a NaN
+  written into A~ (through the system's device pointer) before the
+  factorisation gives CT_ERR_NONFINITE from ct_qr_factor, and a NaN in a
+  sinogram (or in the gradient fed to the adjoint) gives CT_ERR_NONFINITE
+  from the direct FP64/FP32 solves and from the refining ones.  The NaNs are
+  written from the host; nothing faults."""
 import time
 
 import numpy as np
@@ -91,14 +96,72 @@ def test_refinement_short_of_tolerance_reports_noconv(oracle_mod):
     with pytest.raises(ct.CTQRError) as ei:
         F.adjoint(gX, max_iter=1, tol=1e-300)
     assert ei.value.name == "CT_ERR_NOCONV"
-    # a NaN in one sinogram: the FP64 stopping measure is not finite
-    Bn = Bt.clone()
-    Bn[1, 5] = float("nan")
-    with pytest.raises(ct.CTQRError) as ei:
-        F.solve(Bn, max_iter=2, tol=1e-10)
-    assert ei.value.name == "CT_ERR_NOCONV"
-    F.solve(Bn, max_iter=2, tol=1e-10, allow_noconv=True)
-    assert F.last_info["stop_measure"] == float("inf")
     # the factor and the context are intact
     Xg = F.solve(Bt, max_iter=20, tol=1e-10).cpu().numpy().T
     assert rel_err_cols(Xg, Xo).max() <= 1e-6
+
+
+class _DeviceView:
+    """One element of device memory at a raw address, as a torch tensor (CUDA
+    array interface), so a test can write into library-owned storage."""
+
+    def __init__(self, ptr, typestr):
+        self.__cuda_array_interface__ = {"shape": (1,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3}
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("storage,precision", [("fp64", "fp64"), ("fp32", "fp32"), ("fp32", "tf32"),
+                                               ("fp32", "bf16")])
+def test_nonfinite_matrix_is_reported(storage, precision):
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    sysg = ct.System(ct.make_geometry(12, 20, 18, 0.05), storage)
+    es, ts = (8, "<f8") if storage == "fp64" else (4, "<f4")
+    ptr = ct.system_device_ptrs(sysg)["dense"] + es * (40 + 70 * sysg.lda)  # row 40 of column 70
+    torch.as_tensor(_DeviceView(ptr, ts), device="cuda").fill_(float("nan"))
+    torch.cuda.synchronize()
+    with pytest.raises(ct.CTQRError) as ei:
+        sysg.factor(precision)
+    assert ei.value.name == "CT_ERR_NONFINITE", str(ei.value)
+    sysg.free()
+    # the context is unaffected
+    sysg = ct.System(ct.make_geometry(12, 20, 18, 0.05), storage)
+    F = sysg.factor(precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    assert torch.isfinite(F.solve(torch.ones((1, sysg.m), dtype=dt, device="cuda"), max_iter=20,
+                                  tol=1e-10, allow_noconv=True)).all()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("storage,precision", [("fp64", "fp64"), ("fp32", "fp32"), ("fp32", "tf32")])
+def test_nonfinite_sinogram_or_gradient_is_reported(oracle_mod, storage, precision):
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    O = oracle_mod
+    g = O.Geometry(12, 20, 18, sqrt_lambda=0.05)
+    csr = O.siddon_csr(g)
+    B = synth.poisson_sinogram(O.forward(csr, synth.phantom_batch(12, 3, 6, 9)), 12, 1e4, seed=9)
+    Xo, _, _ = O.qr_solve(g, O.dense_system(g, csr), B)
+    sysg = ct.System(ct.make_geometry(12, 20, 18, 0.05), storage)
+    F = sysg.factor(precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(dt).cuda()
+    Bn = Bt.clone()
+    Bn[1, 5] = float("nan")
+    with pytest.raises(ct.CTQRError) as ei:
+        F.solve(Bn, max_iter=20, tol=1e-10)
+    assert ei.value.name == "CT_ERR_NONFINITE", str(ei.value)
+    Bn[1, 5] = float("inf")
+    with pytest.raises(ct.CTQRError) as ei:
+        F.solve(Bn, max_iter=20, tol=1e-10, allow_noconv=True)
+    assert ei.value.name == "CT_ERR_NONFINITE"
+    gX = torch.zeros((2, sysg.n), dtype=dt, device="cuda")
+    gX[0, 7] = float("nan")
+    with pytest.raises(ct.CTQRError) as ei:
+        F.adjoint(gX, max_iter=20, tol=1e-10)
+    assert ei.value.name == "CT_ERR_NONFINITE"
+    # the factor and the context are intact
+    tol = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 1e-6}[precision]
+    Xg = F.solve(Bt, max_iter=20, tol=1e-10).cpu().numpy().T
+    assert rel_err_cols(Xg, Xo).max() <= tol

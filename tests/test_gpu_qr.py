@@ -217,6 +217,28 @@ def test_factor_checkpoint_roundtrip(oracle_mod, tmp_path, precision):
     s3 = ct.System(ct.make_geometry(19, 31, 30, 0.05), storage)
     with pytest.raises(ct.CTQRError):
         ct.Factor.load(s3, path)
+    # tampered headers: block sizes the factorisation never makes are refused
+    # before any data is read; any other header change fails the checksum,
+    # which covers the header too
+    import struct
+    good = open(path, "rb").read()
+    for off, val, why in ((40, 0, "block sizes"), (48, 0, "block sizes"),
+                          (56, struct.unpack_from("<q", good, 56)[0] - 1, "block sizes"),
+                          (48, 33, "block sizes")):
+        raw = bytearray(good)
+        struct.pack_into("<q", raw, off, val)
+        open(path + ".hdr", "wb").write(bytes(raw))
+        with pytest.raises(ct.CTQRError) as e:
+            ct.Factor.load(s2, path + ".hdr")
+        assert e.value.status == 1 and why in str(e.value), (off, str(e.value))
+    import ctypes
+    rjj_min_at = 64 + ctypes.sizeof(ct.Geometry)  # magic .. nblocks, then the geometry
+    raw = bytearray(good)
+    struct.pack_into("<d", raw, rjj_min_at, 123.0)
+    open(path + ".hdr", "wb").write(bytes(raw))
+    with pytest.raises(ct.CTQRError) as e:
+        ct.Factor.load(s2, path + ".hdr")
+    assert e.value.status == 1
 
 
 @pytest.mark.gpu
@@ -299,7 +321,10 @@ def test_gram_panel_matches_column_panel(oracle_mod, precision, tol, ns, nv, nb,
     Rg, Rc = np.triu(VRg[:n]), np.triu(VRc[:n])
     sg = np.sign(np.diag(Rg)) * np.sign(np.diag(Rc))
     scale = np.abs(Rc).max()
-    assert np.abs(sg[:, None] * Rg - Rc).max() <= 2e-3 * scale
+    # a few roundings of the trailing updates' operand type: TF32 (2^-11) and
+    # FP32 panels within 2e-3 of the largest entry, BF16 (2^-8) within 8e-3
+    r_tol = 8e-3 if precision == "bf16" else 2e-3
+    assert np.abs(sg[:, None] * Rg - Rc).max() <= r_tol * scale
     assert not np.array_equal(VRg, VRc)  # a different kernel ran
 
 

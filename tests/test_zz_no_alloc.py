@@ -17,6 +17,9 @@ CASES = [  # kind, ta, tb, M, N, K: split-K partials in the array; K-major copie
     ("tf32", "T", "N", 64, 96, 40000),
     ("tf32", "N", "N", 300, 520, 1000),
     ("fp32", "T", "N", 48, 40, 30000),
+    # ct_gemm's plan splits K ten ways (40 MiB of partials): the depth is cut to
+    # what fits in the 16 MiB array
+    ("tf32", "T", "N", 1024, 1024, 16384),
 ]
 
 
@@ -67,6 +70,56 @@ def test_noalloc_gemm_matches_ct_gemm_twice_in_a_row():
             assert np.all(np.abs(got_ref - exact) <= tol)
             assert np.all(np.abs(got_new - exact) <= tol), (rep, kind, ta, tb)
             assert np.all(np.abs(got_new - got_ref) <= 2 * tol)
+
+
+@pytest.mark.gpu
+def test_noalloc_gemm_allocates_no_device_memory():
+    """Free device memory (cudaMemGetInfo) does not move across calls of the
+    allocation-free entry point.  Around the first call on the device it may
+    drop by the fixed array itself, which the driver places when it first
+    loads the array's module; nothing beyond that."""
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    L = ct.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(3)
+    ops = []
+    for kind, ta, tb, M, N, K in CASES:
+        A, B, C, lda, ldb, ldc, _, _ = _operands(rng, kind, ta, tb, M, N, K)
+        dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, C))
+        args = (ct.GEMM_KINDS[kind], ta.encode(), tb.encode(), M, N, K, 1.0,
+                ctypes.c_void_p(dA.data_ptr()), lda, ctypes.c_void_p(dB.data_ptr()), ldb, 0.5,
+                ctypes.c_void_p(dC.data_ptr()), ldc, stream)
+        ops.append((args, dA, dB, dC))
+        assert L.ct_gemm(*args) == 0  # loads every kernel the products use
+    torch.cuda.synchronize()
+
+    def free_bytes():
+        torch.cuda.synchronize()
+        return torch.cuda.mem_get_info()[0]
+
+    f0 = free_bytes()
+    assert L.ct_gemm_noalloc(*ops[0][0]) == 0, L.ct_last_error()
+    f1 = free_bytes()
+    assert 0 <= f0 - f1 <= (16 << 20) + (4 << 20), (f0, f1)
+    for _ in range(2):
+        for args, *_ in ops:
+            assert L.ct_gemm_noalloc(*args) == 0, L.ct_last_error()
+    assert free_bytes() == f1
+
+
+@pytest.mark.gpu
+def test_noalloc_refuses_bf16_and_split_kinds():
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    L = ct.lib()
+    d = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+    p = ctypes.c_void_p(d.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for kind in ("bf16", "tf32x3", "bf16x3"):
+        st = L.ct_gemm_noalloc(ct.GEMM_KINDS[kind], b"T", b"N", 64, 64, 64, 1.0, p, 64, p, 64, 0.0,
+                               p, 64, stream)
+        assert st == 1, kind
 
 
 @pytest.mark.gpu
