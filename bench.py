@@ -76,6 +76,26 @@ def oracle_geometry_of(O, name):
     return O.Geometry(ns, nv, nb, sqrt_lambda=sl)
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate (fallback only)
 
+# DRAM traffic of the BF16 SM-pair GEMM (gemm_pair_kernel<1>), one ncu launch
+# each (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) on the two
+# products of a 256^2 outer-block update at full size, beside the
+# algorithmic bytes of the same launch (BF16 operands once, FP32 C read and
+# written); profiles/gemm_pair_kernel_bf16_traffic_256x256.md.
+BF16_PAIR_TRAFFIC = {
+    "TN 2048x16384x131040": {"dram_bytes": 16870233856 + 131341824,
+                             "algorithmic_bytes": 2 * (2048 * 131040 + 131040 * 16384) + 2 * 4 * 2048 * 16384},
+    "NN 131040x32768x2048": {"dram_bytes": 36604698112 + 17159480320,
+                             "algorithmic_bytes": 2 * (131040 * 2048 + 2048 * 32768) + 2 * 4 * 131040 * 32768},
+}
+
+
+def traffic_ratio():
+    """DRAM bytes over algorithmic bytes of the captured BF16 update products
+    (one TN and one NN product per outer block, summed)."""
+    d = sum(v["dram_bytes"] for v in BF16_PAIR_TRAFFIC.values())
+    a = sum(v["algorithmic_bytes"] for v in BF16_PAIR_TRAFFIC.values())
+    return d / a
+
 
 def measure_tf32_peaks(torch, n=8192, seconds=4.0):
     """TF32 tensor-core peaks of this GPU, measured the way the BF16 peaks
@@ -247,6 +267,8 @@ def make_inputs(ct, torch, name, rank=0):
 
 
 NB_OUTER = 0  # 0: the library's default outer block width
+SOLVE_PLAN = (0, 0)  # (superblock rows, least split-K depth) of the solve; (0, 0): library defaults
+INNER_STOP = "precond"  # the refinement's inner stopping rule (Factor.inner_stop)
 OOC_BUDGET = 0  # > 0: out-of-core path with this device budget (bytes)
 DISK_PATH = ""  # out of core with A~ in this file (disk tier) instead of pinned host memory
 HOST_CACHE = 0  # pinned block cache of the disk tier (bytes)
@@ -279,6 +301,8 @@ def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, prof=None
     if prof is not None:
         prof["qr"] = ct.stats_read()
         ct.stats_reset(True)
+    F.solve_plan = SOLVE_PLAN
+    F.inner_stop = INNER_STOP
     if host:
         X = F.solve_host(B, out=out, max_iter=max_iter, tol=tol)
     else:
@@ -309,6 +333,8 @@ def run_step_kept(ct, torch, geom, precision, B, max_iter, tol):
     else:
         sysg = ct.System(geom, storage)
         F = sysg.factor(precision, nb_outer=NB_OUTER)
+    F.solve_plan = SOLVE_PLAN
+    F.inner_stop = INNER_STOP
     X = F.solve(B, max_iter=max_iter, tol=tol, allow_noconv=True)
     return X, sysg, F
 
@@ -441,6 +467,14 @@ def roofline_of(prof, precision, peaks, peak_src):
     if precision in ("bf16", "bf16x3"):
         r = roof("tc_gemm_bf16", "tensor", peaks["bf16_tflops_sustained"], f"{peak_src} bf16 sustained",
                  "tcgen05 GEMMs")
+        t = prof["tc_gemm_bf16"]
+        if precision == "bf16" and t["count"]:
+            ratio = traffic_ratio()
+            r["traffic"] = ratio * t["bytes"] / t["count"]
+            r["traffic_basis"] = {"per_launch_algorithmic_bytes": t["bytes"] / t["count"],
+                                  "dram_over_algorithmic": ratio, "captures": BF16_PAIR_TRAFFIC,
+                                  "how": "ncu DRAM bytes of the two full-size update products, scaled to the "
+                                         "class's mean algorithmic bytes per launch"}
         if prof["tc_gemm"]["count"]:
             r["tf32_class"] = roof("tc_gemm", "tensor", tf32_peak, tf32_src, "tcgen05 GEMMs")
         return r
@@ -670,6 +704,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cert", action="store_true")
+    ap.add_argument("--inner-stop", default="precond", choices=["precond", "normal"],
+                    help="inner stopping rule of the FP64 refinement (Factor.inner_stop)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="solve with the library's default plan instead of the one autotune.solve_plan "
+                         "measures on this workload before the warm-up (untimed)")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the profiled step, the TF32 peak measurement and the accuracy run "
                          "(for the long FP64 runs at 256^2)")
@@ -693,8 +732,9 @@ def main():
         return gemm_only(args)
     if args.diff:
         return diff_only(args)
-    global NB_OUTER, OOC_BUDGET, DISK_PATH, HOST_CACHE
+    global NB_OUTER, OOC_BUDGET, DISK_PATH, HOST_CACHE, SOLVE_PLAN, INNER_STOP
     NB_OUTER = args.nb_outer
+    INNER_STOP = args.inner_stop
     OOC_BUDGET = int(args.ooc_budget_gb * (1 << 30))
     HOST_CACHE = int(args.host_cache_gb * (1 << 30))
     if args.disk:
@@ -755,6 +795,19 @@ def main():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+
+    # ---- solve plan: autotune.solve_plan on this workload's factor and batch
+    #      (untimed; in-core tensor-core factors only) ----
+    tune = None
+    if not args.no_tune and OOC_BUDGET == 0 and args.precision not in ("fp32", "fp64"):
+        from paper_2412_07631_b300 import autotune
+        Xt_, sys_t, F_t = run_step_kept(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
+        del Xt_
+        SOLVE_PLAN = autotune.solve_plan(F_t, B, max_iter=args.max_iter, tol=args.tol, retune=True)
+        tune = dict(autotune.load_cache().get(
+            autotune._key(geom, args.precision, torch.cuda.get_device_name()) + f"|k{k}|solve", {}))
+        F_t.free()
+        sys_t.free()
 
     for _ in range(args.warmup):
         run_step(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
@@ -867,6 +920,7 @@ def main():
         _, cB = make_inputs(ct, torch, "c2")
         cmp = {"workload": workload_desc("c2")}
         mixed = args.precision if args.precision not in ("fp64", "fp32") else "tf32"
+        plan_c3, SOLVE_PLAN = SOLVE_PLAN, (0, 0)  # the tuned plan belongs to the 256^2 workload
         for prec in ("fp64", mixed):
             Bd = torch.from_numpy(cB).double().cuda()
             run_step(ct, torch, cg, prec, Bd, args.max_iter, args.tol) if prec == mixed else None
@@ -875,6 +929,7 @@ def main():
                          "slices_per_s": ck / (ph["solve"] * 1e-3),
                          "refine_iters": inf.get("iterations", 0),
                          "inner_iters": inf.get("inner_iterations", 0)}
+        SOLVE_PLAN = plan_c3
         # the FP64 path at this workload: its 128^2 QR rate over this
         # workload's QR flops, its 128^2 per-slice solve time scaled by the
         # per-slice flop ratio
@@ -923,7 +978,10 @@ def main():
                                                         else "pinned host memory")}
                                        if OOC_BUDGET else None),
                        "l2": "inputs larger than L2 (dense A~ of %.1f GB rebuilt every step)"
-                             % (M * n * 4 / 1e9)},
+                             % (M * n * 4 / 1e9),
+                       "solve_plan": {"solve_block": SOLVE_PLAN[0], "solve_split": SOLVE_PLAN[1],
+                                      "tuned": tune},
+                       "inner_stop": INNER_STOP},
             "qr_tflops": qr_fl / (qr_ms * 1e-3) / 1e12,
             "qr_tflops_dense_equivalent": flops_of(ns, nv, nb, sl, k, dense=True)[2] / (qr_ms * 1e-3) / 1e12,
             "slices_per_s": k / (solve_ms * 1e-3),

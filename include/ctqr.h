@@ -140,6 +140,12 @@ typedef struct {
     int32_t flags;           /* CT_OPT_* bits */
     int32_t stop_after;      /* disk-tier factorisation: return CT_ERR_INTERRUPTED after this
                                 many superpanels (0: run to the end); the file stays resumable */
+    int32_t solve_block;     /* solves with a tensor-core factor (TF32/BF16 and split kinds):
+                                rows of the triangular solve's diagonal superblocks, each applied
+                                as one GEMM with its stored inverse (0: 2048; otherwise 128 times
+                                a power of two, at most 16384).  A change rebuilds the inverses. */
+    int32_t solve_split;     /* solves: least depth of one split-K slice in the solve's GEMMs
+                                (0: 256; otherwise a multiple of 32, at least 32) */
 } ct_opts;
 
 /* ct_opts.flags: by default the repeated parts of a solve (the Q^T sweep plus
@@ -156,6 +162,12 @@ typedef struct {
  * a panel whose columns are nearly dependent in FP32; this bit always uses
  * the column-by-column sweep. */
 #define CT_OPT_COLUMN_PANEL 2
+/* ct_opts.flags for refining solves: the inner correction solve of each
+ * FP64 step stops on the normal-equation residual g - A~^T A~ d (tracked in
+ * FP32; reduced by 1e-4, or small enough that the next FP64 certificate is
+ * predicted to meet refine_tol, or no longer halving) instead of on the
+ * residual of the R~-preconditioned equations (reduced by 1e-4). */
+#define CT_OPT_INNER_STOP_NORMAL 4
 
 typedef struct {
     int32_t iterations;       /* refinement steps taken: FP64 residual + correction
@@ -445,15 +457,17 @@ CT_API ct_status ct_stats_reset(int32_t timing);
 
 /* Benchmark accounting; the paper has no counterpart.  Synchronises the
  * device, then returns the number of kernels launched since
- * the last reset and, per class (13 entries each; classes: 0 tensor-core GEMM
+ * the last reset and, per class (14 entries each; classes: 0 tensor-core GEMM
  * with TF32 operands, 1 CUDA-core GEMM, 2 panel, 3 triangular diagonal
- * blocks, 4 sparse FP64 products, 5 Siddon, 6 other, 7 sparse FP32 products,
- * 8 tensor-core GEMM with BF16 operands; out-of-core host traffic: 9 V blocks
- * streamed host to device, 10 superpanel columns host to device, 11 factored
- * columns device to host, 12 the compute stream's waits for a streamed V
- * block), the summed event time in ms, algorithmic flops, algorithmic bytes
- * (bytes copied for classes 9-11) and launch count (copies for 9-11, waits
- * for 12).  Any pointer may be NULL.  Errors: CT_ERR_CUDA (the synchronisation or an event query failed). */
+ * blocks, 4 sparse FP64 products, 5 Siddon, 6 other (split-K reductions),
+ * 7 sparse FP32 products, 8 tensor-core GEMM with BF16 operands; out-of-core
+ * host traffic: 9 V blocks streamed host to device, 10 superpanel columns
+ * host to device, 11 factored columns device to host, 12 the compute
+ * stream's waits for a streamed V block; 13 device-side operand
+ * conversions, transposes and layout copies), the summed event time in ms,
+ * algorithmic flops, algorithmic bytes (bytes copied for classes 9-11 and
+ * 13) and launch count (copies for 9-11, waits for 12).  Any pointer may
+ * be NULL.  Errors: CT_ERR_CUDA (the synchronisation or an event query failed). */
 CT_API ct_status ct_stats_read(int64_t *launches, double *ms, double *flops, double *bytes,
                                int64_t *count);
 

@@ -31,7 +31,8 @@ class Geometry(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("refine_max_iter", C.c_int32),
                 ("refine_tol", C.c_double), ("nb_outer", C.c_int32), ("nb_inner", C.c_int32),
-                ("flags", C.c_int32), ("stop_after", C.c_int32)]
+                ("flags", C.c_int32), ("stop_after", C.c_int32), ("solve_block", C.c_int32),
+                ("solve_split", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -310,9 +311,18 @@ class Factor:
         return torch.float32 if self.precision == "fp32" else torch.float64
 
     graphs = True  # capture repeated solve work in CUDA graphs (library default)
+    # solve plan (ct_opts.solve_block, ct_opts.solve_split): superblock rows of
+    # the triangular solve and least split-K depth of the solve's GEMMs (0, 0:
+    # library defaults); autotune.solve_plan measures the best for a geometry
+    solve_plan = (0, 0)
+    # inner stop of the refinement: "precond" (the R~-preconditioned residual)
+    # or "normal" (the normal-equation residual, CT_OPT_INNER_STOP_NORMAL)
+    inner_stop = "precond"
 
     def _opts(self, max_iter=0, tol=0.0):
-        return Opts(PRECISIONS[self.precision], max_iter, tol, 0, 0, 0 if self.graphs else 1)
+        sb, split = self.solve_plan
+        flags = (0 if self.graphs else 1) | (4 if self.inner_stop == "normal" else 0)
+        return Opts(PRECISIONS[self.precision], max_iter, tol, 0, 0, flags, 0, int(sb), int(split))
 
     def solve(self, B, out=None, max_iter: int = 0, tol: float = 0.0, stream=None,
               allow_noconv: bool = False):
@@ -432,7 +442,7 @@ class CTSolve:
 
 
 STAT_CLASSES = ["tc_gemm", "simt_gemm", "panel", "trsm_diag", "spmm_fp64", "siddon", "other",
-                "spmm_fp32", "tc_gemm_bf16", "h2d_v", "h2d_cols", "d2h_cols", "copy_wait"]
+                "spmm_fp32", "tc_gemm_bf16", "h2d_v", "h2d_cols", "d2h_cols", "copy_wait", "convert"]
 
 
 def selftest_wait_timeout(stream=None) -> str:

@@ -131,6 +131,9 @@ uint64_t graph_key(ct_factor f, int64_t k, const void *extra) {
     };
     mix((uint64_t)k);
     mix((uint64_t)(uintptr_t)extra);
+    mix((uint64_t)f->solve_sb_req);
+    mix((uint64_t)f->solve_chunk);
+    mix((uint64_t)(uintptr_t)f->RinvB);
     const Scratch *all[] = {&f->gemm_ws, &f->W, &f->W2, &f->G, &f->Bt, &f->trsm_ws,
                             &f->refine_ws, &f->misc, &f->misc2};
     for (const Scratch *sc : all) {
@@ -625,9 +628,45 @@ ct_status ct_factor_device_ptrs(ct_factor f, void **VR, int64_t *lda, void **tau
     return CT_OK;
 }
 
+}  // extern "C"
+
+// The solve plan of ct_opts (superblock rows of the triangular solve, least
+// split-K depth of the solve's GEMMs): validated and recorded in the factor;
+// a new superblock size drops the stored superblock inverses, which the next
+// triangular solve rebuilds.
+static ct_status apply_solve_plan(ct_factor f, const ct_opts *o) {
+    const int sb = o ? o->solve_block : 0;
+    const int chunk = o ? o->solve_split : 0;
+    if (sb != 0) {
+        const int q = sb / 128;
+        if (sb < 128 || sb > 16384 || sb % 128 != 0 || (q & (q - 1)) != 0) {
+            set_error("solve_block %d: 0, or 128 times a power of two up to 16384", sb);
+            return CT_ERR_ARG;
+        }
+    }
+    if (chunk != 0 && (chunk < 32 || chunk % 32 != 0)) {
+        set_error("solve_split %d: 0, or a multiple of 32", chunk);
+        return CT_ERR_ARG;
+    }
+    f->solve_chunk = chunk;
+    if (sb != f->solve_sb_req) {
+        if (f->RinvB) {  // cudaFree waits for the device, so no solve still reads them
+            CT_CUDA(cudaFree(f->RinvB));
+            CT_CUDA(cudaFree(f->RinvTB));
+            f->RinvB = f->RinvTB = nullptr;
+            f->trsm_sb = 0;
+        }
+        f->solve_sb_req = sb;
+    }
+    return CT_OK;
+}
+
+extern "C" {
+
 ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
                    const ct_opts *opts, void *stream, ct_solve_info *info) {
     if (!f || k < 0 || ldb < f->m || ldx < f->n) return CT_ERR_ARG;
+    CT_TRY(apply_solve_plan(f, opts));
     f->graphs_enabled = !(opts && (opts->flags & CT_OPT_NO_GRAPHS));
     if (k == 0) return CT_OK;
     if (!B || !X) return CT_ERR_ARG;
@@ -638,6 +677,7 @@ ct_status ct_solve(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, 
 ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X, int64_t ldx,
                         const ct_opts *opts, void *stream, ct_solve_info *info) {
     if (!f || k < 0 || ldb < f->m || ldx < f->n) return CT_ERR_ARG;
+    CT_TRY(apply_solve_plan(f, opts));
     if (k == 0) return CT_OK;
     if (!B || !X) return CT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -658,6 +698,7 @@ ct_status ct_solve_host(ct_factor f, const void *B, int64_t ldb, int32_t k, void
 ct_status ct_solve_adjoint(ct_factor f, const void *gX, int64_t ldgx, int32_t k, void *gB,
                            int64_t ldgb, const ct_opts *opts, void *stream, ct_solve_info *info) {
     if (!f || k < 0 || ldgx < f->n || ldgb < f->m) return CT_ERR_ARG;
+    CT_TRY(apply_solve_plan(f, opts));
     f->graphs_enabled = !(opts && (opts->flags & CT_OPT_NO_GRAPHS));
     if (k == 0) return CT_OK;
     if (!gX || !gB) return CT_ERR_ARG;

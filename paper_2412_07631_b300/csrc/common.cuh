@@ -234,7 +234,9 @@ enum ProfClass : int {
     // out-of-core host traffic (bytes = bytes copied): V blocks streamed to
     // the device, superpanel columns loaded, factored columns written back,
     // and the compute stream's stalls waiting for a streamed V block
-    PROF_H2D_V = 9, PROF_H2D_COLS = 10, PROF_D2H_COLS = 11, PROF_COPY_WAIT = 12, PROF_NCLASS = 13
+    PROF_H2D_V = 9, PROF_H2D_COLS = 10, PROF_D2H_COLS = 11, PROF_COPY_WAIT = 12,
+    // device-side operand conversions, transposes and layout copies
+    PROF_COPY = 13, PROF_NCLASS = 14
 };
 void count_launch(int n = 1);
 struct ProfScope {

@@ -72,6 +72,9 @@ ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void 
                         double beta, void *C, int64_t ldc, cudaStream_t s) {
     const int64_t total = M * N;
     if (total == 0) return CT_OK;
+    const double es = fp64 ? 8.0 : 4.0;
+    ProfScope prof(PROF_OTHER, s, (double)splits * total, es * (double)total * (splits + (beta != 0.0 ? 2 : 1)), M, N,
+                   splits, 0);
     const unsigned blocks = (unsigned)ceil_div(total, 256);
     if (fp64) {
         splitk_reduce_kernel<double><<<blocks, 256, 0, s>>>(M, N, splits, (const double *)P, alpha,
@@ -213,7 +216,7 @@ ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     const int64_t BN = tc ? 256 : (fp64 ? 64 : 128);
     const int64_t tiles = ceil_div(g.M, BM) * ceil_div(g.N, BN);
     int64_t splits, kchunk;
-    plan_splits(tiles, g.K, tc ? 256 : 128, tc ? 32 : 16, &splits, &kchunk);
+    plan_splits(tiles, g.K, g.min_chunk > 0 ? g.min_chunk : (tc ? 256 : 128), tc ? 32 : 16, &splits, &kchunk);
     const size_t esz = fp64 ? 8 : 4;
     const size_t pbytes = splits > 1 ? esz * (size_t)(g.M * g.N * splits) : 0;
     if (abytes + bbytes + pbytes > 0) CT_TRY(ws.ensure(abytes + bbytes + pbytes));

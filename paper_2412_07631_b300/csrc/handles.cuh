@@ -78,6 +78,11 @@ struct ct_factor_s {
     // (and their transposes), so each superblock is one GEMM
     void *RinvB = nullptr, *RinvTB = nullptr;
     int trsm_sb = 0;
+    // solve plan (ct_opts.solve_block / solve_split of the latest solve call):
+    // requested superblock rows (0: default) and least split-K depth of the
+    // solve's GEMMs (0: the engine's default)
+    int solve_sb_req = 0;
+    int64_t solve_chunk = 0;
     int64_t ldrt = 0;
     // captured graphs of the solve, and the stream they run on
     GraphSlot g_direct, g_iter;

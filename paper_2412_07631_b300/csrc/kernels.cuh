@@ -68,6 +68,7 @@ struct GemmArgs {
     double beta;
     void *C;
     int64_t ldc;
+    int64_t min_chunk = 0;  // least split-K depth (0: the engine's default)
 };
 // C = alpha op(A) op(B) + beta C (column-major).  Chooses split-K when the
 // output has too few tiles for the machine; partial sums go through `ws`

@@ -46,6 +46,7 @@ GemmArgs mk(ct_factor f, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
     g.beta = beta;
     g.C = C;
     g.ldc = ldc;
+    g.min_chunk = f->solve_chunk;  // 0 during the factorisation
     return g;
 }
 

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) inv_double_kernel(int64_t n, int64_t SB, 
 static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
     const int TB = f->trsm_tb;
     const int64_t n = f->n;
-    const int SB = (int)std::min<int64_t>(2048, round_up(n, TB));
+    const int SB = (int)std::min<int64_t>(f->solve_sb_req > 0 ? f->solve_sb_req : 2048, round_up(n, TB));
     const int64_t nsb = ceil_div(n, SB), nblk = ceil_div(n, TB);
     const size_t es = f->es(), blk = (size_t)SB * SB;
     CT_CUDA(cudaMalloc(&f->RinvB, es * nsb * blk));
@@ -230,7 +230,11 @@ static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
 // Inverse diagonal blocks of R (and, for the tensor-core path, R^T and the
 // superblock inverses), built once per factor on first use.
 ct_status trsm_prepare(ct_factor f, cudaStream_t s) {
-    if (f->Rinv) return CT_OK;
+    if (f->Rinv) {
+        // superblock inverses dropped by a change of the solve plan: rebuilt
+        if (tensor_kind(f->kind) && f->trsm_sb == 0) CT_TRY(build_superblock_inverses(f, s));
+        return CT_OK;
+    }
     const size_t es = f->es();
     const int TB = f->fp64 ? 64 : 128;
     const int64_t nbt = ceil_div(f->n, TB);
@@ -280,6 +284,7 @@ ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, 
         if (rows <= 0 || cols <= 0) return CT_OK;
         GemmArgs g{};
         g.kind = f->kind;
+        g.min_chunk = f->solve_chunk;
         g.alpha = -1.0;
         g.beta = 1.0;
         g.M = rows;
@@ -318,6 +323,7 @@ ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, 
                                       cudaMemcpyDeviceToDevice, s));
             GemmArgs d{};
             d.kind = f->kind;
+            d.min_chunk = f->solve_chunk;
             d.M = ns;
             d.N = k;
             d.K = ns;

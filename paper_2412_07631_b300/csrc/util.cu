@@ -221,9 +221,14 @@ ct_status split3_copy(const float *src, int64_t lds, bool src_kmajor, int dst_ki
     return CT_OK;
 }
 
+// Bytes of one element of a buffer kind: 0 float, 1 double, 2 bf16.
+static inline double kind_bytes(int kind) { return kind == 1 ? 8.0 : (kind == 2 ? 2.0 : 4.0); }
+
 ct_status transpose_any(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
                         int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
     if (rows == 0 || cols == 0) return CT_OK;
+    ProfScope prof(PROF_COPY, s, 0.0, (kind_bytes(src_kind) + kind_bytes(dst_kind)) * (double)rows * cols, rows,
+                   cols, src_kind, dst_kind);
     dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32)), block(32, 8);
     if (dst_kind == 2) {  // FP32 -> BF16
         if (src_kind != 0) return CT_ERR_ARG;
@@ -264,6 +269,8 @@ ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_ki
                           int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
     const int64_t total = rows * cols;
     if (total == 0) return CT_OK;
+    ProfScope prof(PROF_COPY, s, 0.0, (kind_bytes(src_kind) + kind_bytes(dst_kind)) * (double)total, rows, cols,
+                   src_kind, dst_kind);
     const unsigned b = (unsigned)ceil_div(total, 256);
     if (dst_kind == 2) {  // FP32 -> BF16
         if (src_kind != 0) return CT_ERR_ARG;

@@ -97,3 +97,23 @@ def test_binding_names_every_entry_point():
     assert not missing, missing
     assert ct.status_str(4) == "CT_ERR_RANK"
     assert isinstance(ct.last_error(), str)
+
+
+def _struct_fields(text, name):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    m = re.search(r"typedef struct \{([^{}]*)\} " + name + ";", text, re.S)
+    assert m, name
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    return [re.split(r"\s+", d.strip())[-1] for d in body.split(";") if d.strip()]
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes structures mirror the header's structs field by field (names,
+    order and sizes), so the library reads what the binding writes."""
+    import ctypes
+    import paper_2412_07631_b300 as ct
+    text = open(os.path.join(ROOT, "include", "ctqr.h")).read()
+    for cls, name in ((ct.Opts, "ct_opts"), (ct.SolveInfo, "ct_solve_info"), (ct.Geometry, "ct_geometry")):
+        assert [f for f, _ in cls._fields_] == _struct_fields(text, name), name
+    # the ABI sizes the library was built with (x86-64 System V alignment)
+    assert ctypes.sizeof(ct.Opts) == 40 and ctypes.sizeof(ct.Geometry) == 80

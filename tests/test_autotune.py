@@ -46,3 +46,39 @@ def test_autotune_real_run(tmp_path):
     assert nb in (64, 128)
     F = ct.System(g, "fp32").factor("tf32", nb_outer=nb)
     assert F.n == 32 * 32
+
+
+def test_solve_plan_picks_fastest_and_caches(tmp_path):
+    """The solve-plan tuner: the fastest (superblock rows, split depth) is
+    chosen, set on the factor and cached per geometry, precision and batch."""
+    from paper_2412_07631_b300 import autotune, make_geometry
+
+    class _B:
+        shape = (512, 100)
+
+    class _F:
+        precision = "bf16"
+        solve_plan = (0, 0)
+
+        class system:
+            geom = make_geometry(24, 40, 36, 0.05)
+
+    times = {(2048, 256): 9.0, (1024, 256): 9.5, (4096, 256): 8.0, (2048, 512): 8.5,
+             (2048, 1024): 8.9, (4096, 1024): 7.9}
+    calls = []
+
+    def timer(f, b, plan):
+        calls.append(tuple(plan))
+        return times[tuple(plan)]
+
+    path = str(tmp_path / "tune.json")
+    f = _F()
+    assert autotune.solve_plan(f, _B(), path=path, timer=timer) == (4096, 1024)
+    assert f.solve_plan == (4096, 1024) and sorted(calls) == sorted(times)
+    calls.clear()
+    g = _F()
+    assert autotune.solve_plan(g, _B(), path=path, timer=timer) == (4096, 1024) and calls == []
+    assert g.solve_plan == (4096, 1024)
+    class _B2:
+        shape = (64, 100)
+    assert autotune.solve_plan(_F(), _B2(), path=path, timer=lambda *a: 1.0) == (1024, 256)

@@ -204,3 +204,16 @@ def test_host_link_arithmetic():
     assert r["link_floor_ms"] == pytest.approx((25e9 / 50e9 + 5e9 / 25e9) * 1e3)
     assert r["link_floor_frac_of_qr"] == pytest.approx(700.0 / 2000.0)
     assert bench.host_link_of(_prof(), 1.0, link) is None
+
+
+def test_traffic_of_the_bf16_class():
+    """roofline.traffic = the captured DRAM/algorithmic ratio times the class's
+    mean algorithmic bytes per launch."""
+    peaks = {"bf16_tflops_sustained": 1401.4}
+    prof = _prof(tc_gemm_bf16=(800.0, 1.1e15, 4000))
+    prof["tc_gemm_bf16"]["bytes"] = 4000 * 2.0e9
+    r = bench.roofline_of(prof, "bf16", peaks, "measured")
+    ratio = bench.traffic_ratio()
+    assert 1.0 < ratio < 4.0
+    assert r["traffic"] == pytest.approx(ratio * 2.0e9)
+    assert bench.roofline_of(prof, "tf32", peaks, "measured")["traffic"] is None

@@ -48,3 +48,4 @@ def test_c2_against_lapack_oracle(c2_case, precision, tol):
     err = rel_err_cols(Xg, Xo)
     print(precision, "max rel err", err.max(), "info", F.last_info)
     assert err.max() <= tol
+
