@@ -268,7 +268,6 @@ def make_inputs(ct, torch, name, rank=0):
 
 NB_OUTER = 0  # 0: the library's default outer block width
 SOLVE_PLAN = (0, 0)  # (superblock rows, least split-K depth) of the solve; (0, 0): library defaults
-INNER_STOP = "precond"  # the refinement's inner stopping rule (Factor.inner_stop)
 OOC_BUDGET = 0  # > 0: out-of-core path with this device budget (bytes)
 DISK_PATH = ""  # out of core with A~ in this file (disk tier) instead of pinned host memory
 HOST_CACHE = 0  # pinned block cache of the disk tier (bytes)
@@ -302,7 +301,6 @@ def run_step(ct, torch, geom, precision, B, max_iter, tol, host=False, prof=None
         prof["qr"] = ct.stats_read()
         ct.stats_reset(True)
     F.solve_plan = SOLVE_PLAN
-    F.inner_stop = INNER_STOP
     if host:
         X = F.solve_host(B, out=out, max_iter=max_iter, tol=tol)
     else:
@@ -334,7 +332,6 @@ def run_step_kept(ct, torch, geom, precision, B, max_iter, tol):
         sysg = ct.System(geom, storage)
         F = sysg.factor(precision, nb_outer=NB_OUTER)
     F.solve_plan = SOLVE_PLAN
-    F.inner_stop = INNER_STOP
     X = F.solve(B, max_iter=max_iter, tol=tol, allow_noconv=True)
     return X, sysg, F
 
@@ -704,8 +701,6 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cert", action="store_true")
-    ap.add_argument("--inner-stop", default="precond", choices=["precond", "normal"],
-                    help="inner stopping rule of the FP64 refinement (Factor.inner_stop)")
     ap.add_argument("--no-tune", action="store_true",
                     help="solve with the library's default plan instead of the one autotune.solve_plan "
                          "measures on this workload before the warm-up (untimed)")
@@ -732,9 +727,8 @@ def main():
         return gemm_only(args)
     if args.diff:
         return diff_only(args)
-    global NB_OUTER, OOC_BUDGET, DISK_PATH, HOST_CACHE, SOLVE_PLAN, INNER_STOP
+    global NB_OUTER, OOC_BUDGET, DISK_PATH, HOST_CACHE, SOLVE_PLAN
     NB_OUTER = args.nb_outer
-    INNER_STOP = args.inner_stop
     OOC_BUDGET = int(args.ooc_budget_gb * (1 << 30))
     HOST_CACHE = int(args.host_cache_gb * (1 << 30))
     if args.disk:
@@ -980,8 +974,7 @@ def main():
                        "l2": "inputs larger than L2 (dense A~ of %.1f GB rebuilt every step)"
                              % (M * n * 4 / 1e9),
                        "solve_plan": {"solve_block": SOLVE_PLAN[0], "solve_split": SOLVE_PLAN[1],
-                                      "tuned": tune},
-                       "inner_stop": INNER_STOP},
+                                      "tuned": tune}},
             "qr_tflops": qr_fl / (qr_ms * 1e-3) / 1e12,
             "qr_tflops_dense_equivalent": flops_of(ns, nv, nb, sl, k, dense=True)[2] / (qr_ms * 1e-3) / 1e12,
             "slices_per_s": k / (solve_ms * 1e-3),

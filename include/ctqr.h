@@ -162,12 +162,6 @@ typedef struct {
  * a panel whose columns are nearly dependent in FP32; this bit always uses
  * the column-by-column sweep. */
 #define CT_OPT_COLUMN_PANEL 2
-/* ct_opts.flags for refining solves: the inner correction solve of each
- * FP64 step stops on the normal-equation residual g - A~^T A~ d (tracked in
- * FP32; reduced by 1e-4, or small enough that the next FP64 certificate is
- * predicted to meet refine_tol, or no longer halving) instead of on the
- * residual of the R~-preconditioned equations (reduced by 1e-4). */
-#define CT_OPT_INNER_STOP_NORMAL 4
 
 typedef struct {
     int32_t iterations;       /* refinement steps taken: FP64 residual + correction

@@ -315,14 +315,11 @@ class Factor:
     # the triangular solve and least split-K depth of the solve's GEMMs (0, 0:
     # library defaults); autotune.solve_plan measures the best for a geometry
     solve_plan = (0, 0)
-    # inner stop of the refinement: "precond" (the R~-preconditioned residual)
-    # or "normal" (the normal-equation residual, CT_OPT_INNER_STOP_NORMAL)
-    inner_stop = "precond"
 
     def _opts(self, max_iter=0, tol=0.0):
         sb, split = self.solve_plan
-        flags = (0 if self.graphs else 1) | (4 if self.inner_stop == "normal" else 0)
-        return Opts(PRECISIONS[self.precision], max_iter, tol, 0, 0, flags, 0, int(sb), int(split))
+        return Opts(PRECISIONS[self.precision], max_iter, tol, 0, 0, 0 if self.graphs else 1, 0,
+                    int(sb), int(split))
 
     def solve(self, B, out=None, max_iter: int = 0, tol: float = 0.0, stream=None,
               allow_noconv: bool = False):

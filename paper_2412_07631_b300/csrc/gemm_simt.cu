@@ -126,7 +126,8 @@ static ct_status gemm_copied(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
     const int64_t es = b16 ? 2 : 4;
     const int64_t Kc = split ? 3 * g.K : g.K;  // depth of the product of the copies
     const int64_t ldt = round_up(Kc, 64);
-    const size_t abytes = (size_t)round_up(es * ldt * g.M, 256);
+    const bool pre_a = g.kind == GEMM_BF16 && g.A16 != nullptr;  // A already converted by the caller
+    const size_t abytes = pre_a ? 0 : (size_t)round_up(es * ldt * g.M, 256);
     int64_t nslab = g.N;
     if ((size_t)(es * ldt) * (size_t)g.N > kChunkBytes)
         nslab = std::max<int64_t>(256, (int64_t)(kChunkBytes / (size_t)(es * ldt)) / 256 * 256);
@@ -141,9 +142,13 @@ static ct_status gemm_copied(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
     const size_t pbytes = std::max(splits > 1 ? 4 * (size_t)(g.M * nslab * splits) : (size_t)0,
                                    sp_last > 1 ? 4 * (size_t)(g.M * nlast * sp_last) : (size_t)0);
     CT_TRY(ws.ensure(abytes + bbytes + pbytes));
-    void *Ab = ws.ptr, *Bb = (char *)ws.ptr + abytes, *part = (char *)ws.ptr + abytes + bbytes;
+    void *Ab = pre_a ? const_cast<void *>(g.A16) : ws.ptr, *Bb = (char *)ws.ptr + abytes,
+         *part = (char *)ws.ptr + abytes + bbytes;
+    const int64_t lda_b = pre_a ? g.lda16 : ldt;
     const int split_kind = b16 ? 2 : 3;
-    if (split) CT_TRY(split3_copy((const float *)g.A, g.lda, g.ta, split_kind, false, Ab, ldt, g.K, g.M, s));
+    if (pre_a) {
+        // nothing to convert
+    } else if (split) CT_TRY(split3_copy((const float *)g.A, g.lda, g.ta, split_kind, false, Ab, ldt, g.K, g.M, s));
     else if (g.ta) CT_TRY(copy_convert_2d(0, g.A, g.lda, 2, Ab, ldt, g.K, g.M, s));
     else CT_TRY(transpose_any(0, g.A, g.lda, 2, Ab, ldt, g.M, g.K, s));
     for (int64_t n0 = 0; n0 < g.N; n0 += nslab) {
@@ -159,7 +164,7 @@ static ct_status gemm_copied(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
         b.ta = true;
         b.tb = false;
         b.A = Ab;
-        b.lda = ldt;
+        b.lda = lda_b;
         b.B = Bb;
         b.ldb = ldt;
         b.N = nn;

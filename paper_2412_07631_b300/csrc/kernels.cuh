@@ -69,6 +69,10 @@ struct GemmArgs {
     void *C;
     int64_t ldc;
     int64_t min_chunk = 0;  // least split-K depth (0: the engine's default)
+    // BF16 products only: op(A) already rounded to BF16 in the engine's
+    // K-major layout (element (k, m) at A16 + k + m * lda16), or NULL
+    const void *A16 = nullptr;
+    int64_t lda16 = 0;
 };
 // C = alpha op(A) op(B) + beta C (column-major).  Chooses split-K when the
 // output has too few tiles for the machine; partial sums go through `ws`
@@ -147,6 +151,11 @@ ct_status trsm_upper(GemmKind kind, bool trans, int64_t n, int64_t k, const void
 // BF16; 3: TF32 values stored as FP32.  dst: element (k', j) at dst[k' + j*ldt].
 ct_status split3_copy(const float *src, int64_t lds, bool src_kmajor, int dst_kind, bool second_operand,
                       void *dst, int64_t ldt, int64_t K, int64_t MN, cudaStream_t s);
+// FP32 rows x cols (column-major, ld lds) rounded to BF16 into colm (same
+// layout, ld ldc; skipped when NULL) and rowm (transposed: element (r, c) at
+// c + r * ldr) with one read of the source.
+ct_status convert_bf16_dual(const float *src, int64_t lds, int64_t rows, int64_t cols, void *colm, int64_t ldc,
+                            void *rowm, int64_t ldr, cudaStream_t s);
 ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,
                           int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s);
 // 0 = float, 1 = double for src/dst kinds above.

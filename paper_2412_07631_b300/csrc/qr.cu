@@ -131,12 +131,35 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     const void *Vb = vb ? vb : at(f->VR, j + w, j, f->lda, es);
     const int64_t ldV = vb ? ldvb : f->lda;
     void *Cb = (char *)C + es * (size_t)w;
+    // BF16 products.  W = V^T C of a panel's or mid block's reflector (w <=
+    // 256) is short and deep: it is bound by reading C, so it takes the FP32
+    // C directly on the TF32 path rather than paying a BF16 copy of C first.
+    // V below its top block is rounded to BF16 once, into each K-major
+    // layout a BF16 product reads (V^T C takes it as stored, C -= V W2
+    // transposed), instead of one conversion per product.
+    GemmKind tn_kind = big;
+    const void *v16c = nullptr, *v16r = nullptr;
+    int64_t ld16c = 0, ld16r = 0;
+    if (big == GEMM_BF16 && kb > 0) {
+        if (w <= 256) tn_kind = GEMM_TF32;
+        ld16c = round_up(kb, 64);
+        ld16r = round_up(w, 64);
+        const size_t cb = tn_kind == GEMM_BF16 ? (size_t)round_up(2 * ld16c * w, 256) : 0;
+        const size_t rb = (size_t)round_up(2 * ld16r * kb, 256);
+        CT_TRY(f->V16.ensure(cb + rb));
+        v16c = cb ? f->V16.ptr : nullptr;
+        v16r = (char *)f->V16.ptr + cb;
+        CT_TRY(convert_bf16_dual((const float *)Vb, ldV, kb, w, const_cast<void *>(v16c), ld16c,
+                                 const_cast<void *>(v16r), ld16r, s));
+    }
     if (w <= 32) {
         // narrow reflector (a panel's): the bulk products over the rows below
         // on the engine, the w x w top-block work fused into one small kernel
         if (kb > 0) {
             GemmArgs g = mk(f, true, false, w, ncols, kb, 1.0, Vb, ldV, Cb, ldc, 0.0, W, NB);
-            g.kind = big;
+            g.kind = tn_kind;
+            g.A16 = v16c;
+            g.lda16 = ld16c;
             CT_TRY(gemm(g, f->gemm_ws, s));
         } else {
             CT_TRY(fill_zero_2d(f->fp64, W, NB, w, ncols, s));
@@ -146,6 +169,8 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
         if (kb > 0) {
             GemmArgs g = mk(f, false, false, kb, ncols, w, -1.0, Vb, ldV, W2, NB, 1.0, Cb, ldc);
             g.kind = big;
+            g.A16 = v16r;
+            g.lda16 = ld16r;
             CT_TRY(gemm(g, f->gemm_ws, s));
         }
         return CT_OK;
@@ -154,7 +179,9 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     CT_TRY(gemm(mk(f, true, false, w, ncols, w, 1.0, Vt, NB, C, ldc, 0.0, W, NB), f->gemm_ws, s));
     if (kb > 0) {
         GemmArgs g = mk(f, true, false, w, ncols, kb, 1.0, Vb, ldV, Cb, ldc, 1.0, W, NB);
-        g.kind = big;
+        g.kind = tn_kind;
+        g.A16 = v16c;
+        g.lda16 = ld16c;
         CT_TRY(gemm(g, f->gemm_ws, s));
     }
     // W2 = op(T) W
@@ -164,6 +191,8 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     if (kb > 0) {
         GemmArgs g = mk(f, false, false, kb, ncols, w, -1.0, Vb, ldV, W2, NB, 1.0, Cb, ldc);
         g.kind = big;
+        g.A16 = v16r;
+        g.lda16 = ld16r;
         CT_TRY(gemm(g, f->gemm_ws, s));
     }
     return CT_OK;

@@ -43,7 +43,7 @@ namespace ctqr {
 namespace {
 
 constexpr int RB = 256;                // rows per reduction block
-constexpr double kInnerRed = 1e-4;     // inner CGLS: relative reduction of ||s|| (or of ||g_k||)
+constexpr double kInnerRed = 1e-4;     // inner CGLS: relative reduction of ||s||
 constexpr int kInnerMax = 40;          // inner CGLS: step limit per outer step
 
 // part[b*k + s] = sum over rows [b*RB, (b+1)*RB) of U[i,s]*V[i,s] (row-major,
@@ -199,7 +199,7 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
     const size_t nk = (size_t)n * k, Mk = (size_t)M * k;
     const size_t ldl = round_up(n, 32);
     const size_t bytes = sizeof(double) * (2 * Mk + 2 * nk + (size_t)nblk * k + 12 * (size_t)k) +
-                         sizeof(float) * (Mk + 6 * nk) + f->es() * ldl * k + 4096;
+                         sizeof(float) * (Mk + 5 * nk) + f->es() * ldl * k + 4096;
     CT_TRY(f->refine_ws.ensure(bytes));
     char *base = (char *)f->refine_ws.ptr;
     auto take = [&](size_t b) { char *p = base; base += round_up((int64_t)b, 256); return p; };
@@ -213,26 +213,23 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
     float *sv = (float *)take(sizeof(float) * nk);
     float *t = (float *)take(sizeof(float) * nk);
     float *u = (float *)take(sizeof(float) * nk);
-    float *gr = (float *)take(sizeof(float) * nk);  // g - A~^T A~ d, tracked in FP32
     double *part = (double *)take(sizeof(double) * nblk * k);
     double *vec = (double *)take(sizeof(double) * 12 * k);
     void *lp = take(f->es() * ldl * k);
     double *gamma = vec, *qq = vec + k, *alpha = vec + 2 * k, *beta = vec + 3 * k, *gnew = vec + 4 * k,
-           *gg = vec + 5 * k, *xx = vec + 6 * k, *dd = vec + 7 * k, *gk = vec + 8 * k;
-    const bool stop_on_g = o && (o->flags & CT_OPT_INNER_STOP_NORMAL);
+           *gg = vec + 5 * k, *xx = vec + 6 * k, *dd = vec + 7 * k;
     const unsigned bn = (unsigned)ceil_div((int64_t)nk, 256), bk = (unsigned)ceil_div(k, 128);
 
-    // per-slice scalars come back through pinned host memory: gg, xx, dd, gamma, gk
-    if (f->pinned_count < 5 * (size_t)k) {
+    // per-slice scalars come back through pinned host memory: gg, xx, dd, gamma
+    if (f->pinned_count < 4 * (size_t)k) {
         if (f->pinned) cudaFreeHost(f->pinned);
         f->pinned = nullptr;
         f->pinned_count = 0;
-        CT_CUDA(cudaMallocHost((void **)&f->pinned, sizeof(double) * 5 * (size_t)k));
-        f->pinned_count = 5 * (size_t)k;
+        CT_CUDA(cudaMallocHost((void **)&f->pinned, sizeof(double) * 4 * (size_t)k));
+        f->pinned_count = 4 * (size_t)k;
     }
-    double *h_gg = f->pinned, *h_xx = f->pinned + k, *h_dd = f->pinned + 2 * k, *h_gamma = f->pinned + 3 * k,
-           *h_gk = f->pinned + 4 * k;
-    std::vector<double> gamma0(k), gk0(k);
+    double *h_gg = f->pinned, *h_xx = f->pinned + k, *h_dd = f->pinned + 2 * k, *h_gamma = f->pinned + 3 * k;
+    std::vector<double> gamma0(k);
 
     // b~ (row-major, zero sqrt(lambda) rows), x0 (row-major)
     CT_CUDA(cudaMemsetAsync(btil, 0, sizeof(double) * Mk, st));
@@ -252,12 +249,6 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         axpy_cols<float><<<bn, 256, 0, s2>>>(n, k, alpha, 1.0, t, d);   // d += a t
         count_launch();
         CT_TRY(spmm_atr32(S, k, q, 0.0f, nullptr, 1.0f, u, s2));       // u = A~^T q
-        if (stop_on_g) {                                               // g_k -= a A~^T A~ t
-            axpy_cols<float><<<bn, 256, 0, s2>>>(n, k, alpha, -1.0, u, gr);
-            count_launch();
-            CT_TRY(launch_coldot<float>(n, k, gr, gr, part, gk, s2));
-            CT_CUDA(cudaMemcpyAsync(h_gk, gk, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
-        }
         CT_TRY(apply_rinv(f, true, 0, u, u, k, lp, s2));               // w = R^-T u
         axpy_cols<float><<<bn, 256, 0, s2>>>(n, k, alpha, -1.0, u, sv);  // s -= a w
         count_launch();
@@ -270,8 +261,7 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         CT_CUDA(cudaMemcpyAsync(h_gamma, gamma, sizeof(double) * k, cudaMemcpyDeviceToHost, s2));
         return CT_OK;
     };
-    const uint64_t key = graph_key(f, k, r) ^ ((uint64_t)M << 20) ^ 0x5152ull ^
-                         (stop_on_g ? 0x9e3779b97f4a7c15ull : 0ull);
+    const uint64_t key = graph_key(f, k, r) ^ ((uint64_t)M << 20) ^ 0x5152ull;
 
     int outer = 0, inner_total = 0;
     double last = INFINITY;
@@ -310,49 +300,24 @@ ct_status refine_run(ct_factor f, const void *B, int64_t ldb, int32_t k, void *X
         to_f32_kernel<<<bn, 256, 0, st>>>((int64_t)nk, g, u);
         count_launch();
         CT_CUDA(cudaGetLastError());
-        if (stop_on_g) {
-            CT_CUDA(cudaMemcpyAsync(gr, u, sizeof(float) * nk, cudaMemcpyDeviceToDevice, st));
-            CT_TRY(launch_coldot<float>(n, k, gr, gr, part, gk, st));
-            CT_CUDA(cudaMemcpyAsync(h_gk, gk, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        }
         CT_CUDA(cudaMemsetAsync(d, 0, sizeof(float) * nk, st));
         CT_TRY(apply_rinv(f, true, 0, u, sv, k, lp, st));       // s = R^-T g
         CT_CUDA(cudaMemcpyAsync(p, sv, sizeof(float) * nk, cudaMemcpyDeviceToDevice, st));
         CT_TRY(launch_coldot<float>(n, k, sv, sv, part, gamma, st));
         CT_CUDA(cudaMemcpyAsync(h_gamma, gamma, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CT_CUDA(cudaStreamSynchronize(st));
-        for (int32_t sl = 0; sl < k; ++sl) {
-            gamma0[sl] = h_gamma[sl];
-            gk0[sl] = h_gk[sl];
-        }
-        double best_g = INFINITY;
-        int best_at = 0;
+        for (int32_t sl = 0; sl < k; ++sl) gamma0[sl] = h_gamma[sl];
         for (int it = 0; it < kInnerMax; ++it) {
             CT_TRY(run_graphed(f, f->g_iter, key, st, inner_step));
             ++inner_total;
             CT_CUDA(cudaStreamSynchronize(st));
-            double red = 0.0, pred = 0.0;
+            double red = 0.0;
             for (int32_t sl = 0; sl < k; ++sl) {
-                double v;
-                if (stop_on_g) {
-                    // reduction of the normal-equation residual g_k = g - A~^T A~ d,
-                    // and the certificate it predicts for x + d
-                    v = gk0[sl] > 0.0 ? std::sqrt(h_gk[sl] / gk0[sl]) : 0.0;
-                    if (use_cert)
-                        pred = std::max(pred, std::sqrt(h_gk[sl]) / (lam * std::max(std::sqrt(h_xx[sl]), 1e-300)));
-                } else {
-                    v = gamma0[sl] > 0.0 ? std::sqrt(h_gamma[sl] / gamma0[sl]) : 0.0;
-                }
+                const double v = gamma0[sl] > 0.0 ? std::sqrt(h_gamma[sl] / gamma0[sl]) : 0.0;
                 if (!std::isfinite(v)) { red = INFINITY; break; }
                 red = std::max(red, v);
             }
             if (red <= kInnerRed) break;
-            if (stop_on_g) {
-                if (use_cert && pred <= 0.25 * tol) break;  // the next FP64 check should pass
-                // FP32 stagnation: no halving of the residual in 10 steps
-                if (red < 0.5 * best_g) { best_g = red; best_at = it; }
-                else if (it - best_at >= 10) break;
-            }
         }
         // x += d (FP64 accumulation); ||d|| for the unregularised stop
         add_f32_kernel<<<bn, 256, 0, st>>>((int64_t)nk, d, x);

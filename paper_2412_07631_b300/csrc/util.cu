@@ -26,6 +26,34 @@ __global__ void copy_convert_kernel(const S *src, int64_t lds, D *dst, int64_t l
     dst[i + j * ldd] = cvt<D>(src[i + j * lds]);
 }
 
+// FP32 -> BF16 (round to nearest even) in both layouts at once, from one read
+// of the source (rows x cols, column-major, ld lds): colm(r, c) at
+// r + c * ldc (the same layout) and rowm(r, c) at c + r * ldr (transposed).
+// 32 x 32 tiles, block (32, 8); the transposed writes go through shared
+// memory so both stores are contiguous along a warp.
+__global__ void to_bf16_dual_kernel(const float *src, int64_t lds, int64_t rows, int64_t cols,
+                                    __nv_bfloat16 *colm, int64_t ldc, __nv_bfloat16 *rowm, int64_t ldr) {
+    __shared__ float t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t r = r0 + tx, c = c0 + ty + 8 * q;
+        float v = 0.0f;
+        if (r < rows && c < cols) {
+            v = src[r + c * lds];
+            if (colm) colm[r + c * ldc] = __float2bfloat16_rn(v);
+        }
+        t[ty + 8 * q][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t r = r0 + ty + 8 * q, c = c0 + tx;
+        if (r < rows && c < cols) rowm[c + r * ldr] = __float2bfloat16_rn(t[tx][ty + 8 * q]);
+    }
+}
+
 // FP32 -> BF16 (round to nearest even), column by column: blockIdx.y strides
 // over columns, each thread converts 4 consecutive rows.
 __global__ void to_bf16_kernel(const float *src, int64_t lds, __nv_bfloat16 *dst, int64_t ldd,
@@ -263,6 +291,22 @@ ct_status transpose_any(int src_kind, const void *src, int64_t lds, int dst_kind
 ct_status transpose_d(const double *src, int64_t lds, double *dst, int64_t ldd, int64_t rows,
                       int64_t cols, cudaStream_t s) {
     return transpose_any(1, src, lds, 1, dst, ldd, rows, cols, s);
+}
+
+ct_status convert_bf16_dual(const float *src, int64_t lds, int64_t rows, int64_t cols, void *colm, int64_t ldc,
+                            void *rowm, int64_t ldr, cudaStream_t s) {
+    if (rows == 0 || cols == 0) return CT_OK;
+    ProfScope prof(PROF_COPY, s, 0.0, (colm ? 8.0 : 6.0) * (double)rows * cols, rows, cols, 0, colm ? 4 : 5);
+    for (int64_t c0 = 0; c0 < cols; c0 += 32 * 65535LL) {  // grid.y limit
+        const int64_t cc = std::min<int64_t>(cols - c0, 32 * 65535LL);
+        dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cc, 32)), block(32, 8);
+        to_bf16_dual_kernel<<<grid, block, 0, s>>>(src + c0 * lds, lds, rows, cc,
+                                                   colm ? (__nv_bfloat16 *)colm + c0 * ldc : nullptr, ldc,
+                                                   (__nv_bfloat16 *)rowm + c0, ldr);
+        count_launch();
+    }
+    CT_CUDA(cudaGetLastError());
+    return CT_OK;
 }
 
 ct_status copy_convert_2d(int src_kind, const void *src, int64_t lds, int dst_kind, void *dst,

@@ -49,29 +49,3 @@ def test_solve_plans_agree_and_certify(oracle_mod):
             F.solve(Bt, max_iter=-1)
         assert ei.value.name == "CT_ERR_ARG", bad
 
-
-@pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["tf32", "bf16"])
-def test_inner_stop_rules_certify(oracle_mod, precision):
-    """Both inner stopping rules of the FP64 refinement (the R~-preconditioned
-    residual, and the normal-equation residual with its predicted
-    certificate) end at a certified solution: the oracle's long-double bound
-    ||A~^T(b~ - A~x)|| / (lambda ||x||) <= 1e-6 on every slice, and the two
-    solutions agree to that bound."""
-    torch = need_cuda()
-    import paper_2412_07631_b300 as ct
-    O = oracle_mod
-    g = O.Geometry(48, 80, 70, sqrt_lambda=0.05)
-    csr = O.siddon_csr(g)
-    B = synth.poisson_sinogram(O.forward(csr, synth.phantom_batch(48, 12, 10)), 48, 5e3, seed=8)
-    sysg = ct.System(ct.make_geometry(48, 80, 70, 0.05), "fp32")
-    F = sysg.factor(precision)
-    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
-    out = {}
-    for rule in ("precond", "normal"):
-        F.inner_stop = rule
-        X = F.solve(Bt, max_iter=20, tol=1e-8).cpu().numpy().T
-        print(precision, rule, F.last_info)
-        assert O.certificate(g, csr, B, X).max() <= 1e-6
-        out[rule] = X
-    assert rel_err_cols(out["normal"], out["precond"]).max() <= 2e-6
