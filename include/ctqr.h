@@ -439,6 +439,23 @@ CT_API void ct_factor_free(ct_factor f);
  * Errors: CT_ERR_TIMEOUT (expected), CT_ERR_CUDA, CT_ERR_OOM. */
 CT_API ct_status ct_selftest_wait_timeout(void *stream);
 
+/* Sanitizer substitute (a debugging aid; the paper has no counterpart).
+ * enable != 0: every library scratch buffer allocated from now on (GEMM
+ * operand copies and split-K partials, workspaces of the factorisation and
+ * the solve) gets a 64 KiB guard band past its capacity, filled with the
+ * byte 0xA5; enable == 0: buffers allocated later get none.  Buffers that
+ * exist already keep their state.  Always returns CT_OK. */
+CT_API ct_status ct_debug_canaries(int32_t enable);
+
+/* Waits for the device, then reads the guard band of every live guarded
+ * scratch buffer: *checked = buffers read, *corrupted = buffers whose band
+ * no longer holds 0xA5 everywhere (a kernel wrote past the end of its
+ * scratch).  corrupt_first != 0 first overwrites one byte of the first
+ * band (inside that buffer's allocation) so that a test can see the check
+ * fire.  The paper has no counterpart.
+ * Errors: CT_ERR_ARG (NULL pointer), CT_ERR_CUDA. */
+CT_API ct_status ct_debug_check_canaries(int32_t corrupt_first, int64_t *checked, int64_t *corrupted);
+
 /* ---- Benchmark accounting (not part of the method) ---------------------- */
 
 /* Benchmark accounting; the paper has no counterpart.  Zero the launch

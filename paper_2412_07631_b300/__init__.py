@@ -59,7 +59,7 @@ SYMBOLS = ["ct_status_str", "ct_last_error", "ct_build_system", "ct_system_info"
            "ct_stats_read", "ct_stats_dump", "ct_gemm_noalloc", "ct_factor_save",
            "ct_factor_load", "ct_build_system_host", "ct_qr_factor_ooc", "ct_host_cache_release",
            "ct_build_system_disk", "ct_system_open_disk", "ct_disk_progress", "ct_disk_stats",
-           "ct_selftest_wait_timeout"]
+           "ct_selftest_wait_timeout", "ct_debug_canaries", "ct_debug_check_canaries"]
 
 
 def lib_path() -> str:
@@ -110,6 +110,8 @@ def lib():
     L.ct_disk_progress.argtypes = [vp, C.POINTER(I32), C.POINTER(I64)]
     L.ct_disk_stats.argtypes = [I32] + [C.POINTER(I64)] * 5 + [C.POINTER(C.c_double)] * 2
     L.ct_selftest_wait_timeout.argtypes = [vp]
+    L.ct_debug_canaries.argtypes = [I32]
+    L.ct_debug_check_canaries.argtypes = [I32, C.POINTER(I64), C.POINTER(I64)]
     for name in SYMBOLS:
         if name not in ("ct_status_str", "ct_last_error", "ct_system_free", "ct_factor_free"):
             getattr(L, name).restype = C.c_int
@@ -448,6 +450,21 @@ def selftest_wait_timeout(stream=None) -> str:
     "CT_ERR_TIMEOUT" once the bounded wait has given up (about 4 s)."""
     st = lib().ct_selftest_wait_timeout(_stream(stream))
     return lib().ct_status_str(st).decode()
+
+
+def debug_canaries(enable: bool = True):
+    """ct_debug_canaries: guard bands past the capacity of scratch buffers
+    allocated from now on (a sanitizer substitute)."""
+    _check(lib().ct_debug_canaries(1 if enable else 0))
+
+
+def debug_check_canaries(corrupt_first: bool = False) -> tuple[int, int]:
+    """ct_debug_check_canaries: (buffers checked, buffers whose guard band was
+    overwritten).  corrupt_first overwrites one guard byte first (a test of
+    the check itself)."""
+    checked, corrupted = C.c_int64(), C.c_int64()
+    _check(lib().ct_debug_check_canaries(1 if corrupt_first else 0, C.byref(checked), C.byref(corrupted)))
+    return checked.value, corrupted.value
 
 
 def disk_stats(reset: bool = False) -> dict:

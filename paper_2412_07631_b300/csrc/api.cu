@@ -173,26 +173,52 @@ ProfScope::~ProfScope() {
     cudaEventRecord(g_prof[slot].e1, s);
 }
 
+namespace {
+std::atomic<bool> g_canaries{false};
+std::mutex g_scratch_mu;
+std::vector<Scratch *> g_scratches;  // live buffers (registration order)
+}  // namespace
+
+Scratch::Scratch() {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    g_scratches.push_back(this);
+}
+
 ct_status Scratch::ensure(size_t need) {
     if (need <= bytes) return CT_OK;
     if (ptr) {
         cudaError_t e = cudaFree(ptr);
         ptr = nullptr;
         bytes = 0;
+        guarded = false;
         if (e != cudaSuccess) return cuda_status(e, "cudaFree", __FILE__, __LINE__);
     }
     size_t sz = (need + (2u << 20) - 1) & ~(size_t)((2u << 20) - 1);
-    cudaError_t e = cudaMalloc(&ptr, sz);
+    const bool guard = g_canaries.load();
+    cudaError_t e = cudaMalloc(&ptr, sz + (guard ? kGuardBytes : 0));
     if (e != cudaSuccess) {
         ptr = nullptr;
         return cuda_status(e, "cudaMalloc(scratch)", __FILE__, __LINE__);
     }
+    if (guard) {
+        e = cudaMemset((char *)ptr + sz, kGuardByte, kGuardBytes);
+        if (e != cudaSuccess) return cuda_status(e, "cudaMemset(guard)", __FILE__, __LINE__);
+    }
     bytes = sz;
+    guarded = guard;
     ++gen;
     return CT_OK;
 }
 
 Scratch::~Scratch() {
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        for (size_t i = 0; i < g_scratches.size(); ++i)
+            if (g_scratches[i] == this) {
+                g_scratches.erase(g_scratches.begin() + (long)i);
+                break;
+            }
+    }
     if (ptr) cudaFree(ptr);
 }
 
@@ -498,6 +524,37 @@ ct_status ct_factor_export(ct_factor f, void *VR, int64_t ldv, void *tau) {
 }
 
 ct_status ct_selftest_wait_timeout(void *stream) { return wait_selftest((cudaStream_t)stream); }
+
+ct_status ct_debug_canaries(int32_t enable) {
+    g_canaries.store(enable != 0);
+    return CT_OK;
+}
+
+ct_status ct_debug_check_canaries(int32_t corrupt_first, int64_t *checked, int64_t *corrupted) {
+    if (!checked || !corrupted) return CT_ERR_ARG;
+    *checked = 0;
+    *corrupted = 0;
+    CT_CUDA(cudaDeviceSynchronize());
+    std::vector<unsigned char> host(kGuardBytes);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    bool injected = false;
+    for (Scratch *sc : g_scratches) {
+        if (!sc->guarded || !sc->ptr) continue;
+        char *guard = (char *)sc->ptr + sc->bytes;
+        if (corrupt_first && !injected) {  // inside the allocation: the guard band itself
+            CT_CUDA(cudaMemset(guard, 0, 1));
+            injected = true;
+        }
+        CT_CUDA(cudaMemcpy(host.data(), guard, kGuardBytes, cudaMemcpyDeviceToHost));
+        ++*checked;
+        for (size_t i = 0; i < kGuardBytes; ++i)
+            if (host[i] != kGuardByte) {
+                ++*corrupted;
+                break;
+            }
+    }
+    return CT_OK;
+}
 
 ct_status ct_forward_project(ct_system sys, const double *X, int64_t ldx, int32_t k, double *P,
                              int64_t ldp, void *stream) {

@@ -249,12 +249,21 @@ struct ProfScope {
     ~ProfScope();
 };
 
-// Device scratch buffer owned by the library (grown on demand, never shrunk).
+// Device scratch buffer owned by the library (grown on demand, never
+// shrunk).  With guard bands on (ct_debug_canaries), a buffer allocated
+// gets kGuardBytes of the byte kGuardByte past its capacity; every live
+// buffer is registered so that ct_debug_check_canaries can verify them.
+constexpr size_t kGuardBytes = (size_t)64 << 10;
+constexpr unsigned char kGuardByte = 0xA5;
 struct Scratch {
     void *ptr = nullptr;
     size_t bytes = 0;
-    uint64_t gen = 0;  // bumped whenever the buffer moves (captured graphs key on it)
+    uint64_t gen = 0;      // bumped whenever the buffer moves (captured graphs key on it)
+    bool guarded = false;  // a guard band follows the capacity
     ct_status ensure(size_t need);
+    Scratch();
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
     ~Scratch();
 };
 

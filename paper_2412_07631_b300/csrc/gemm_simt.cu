@@ -33,8 +33,20 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const T *
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * N) return;
     int64_t i = idx % M, j = idx / M;
+    // the partials are summed in split order; loads are issued eight at a
+    // time so that deep splits are not a chain of dependent loads
+    const int64_t MN = M * N;
+    const T *p = P + idx;
     T acc = T(0);
-    for (int z = 0; z < splits; ++z) acc += P[(int64_t)z * M * N + idx];
+    int z = 0;
+    for (; z + 8 <= splits; z += 8) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = p[(int64_t)(z + u) * MN];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; z < splits; ++z) acc += p[(int64_t)z * MN];
     T *c = C + i + j * ldc;
     T v = alpha * acc;
     if (beta != T(0)) v += beta * *c;

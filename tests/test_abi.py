@@ -45,6 +45,8 @@ def test_bad_arguments_are_rejected_without_touching_the_device():
     assert L.ct_build_system(ctypes.byref(g), 0, None, ctypes.byref(h)) == 1
     assert L.ct_solve(None, None, 0, 1, None, 0, None, None, None) == 1
     assert L.ct_gemm(7, b"N", b"N", 1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1, None) == 1
+    assert L.ct_debug_check_canaries(0, None, None) == 1
+    assert L.ct_debug_canaries(0) == 0
 
 
 def test_disk_tier_refuses_bad_files_and_blocks_without_a_gpu(tmp_path):
