@@ -702,8 +702,9 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cert", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
-                    help="solve with the library's default plan instead of the one autotune.solve_plan "
-                         "measures on this workload before the warm-up (untimed)")
+                    help="use the library's default outer block width and solve plan instead of the ones "
+                         "autotune.outer_block and autotune.solve_plan measure on this workload before the "
+                         "warm-up (untimed)")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the profiled step, the TF32 peak measurement and the accuracy run "
                          "(for the long FP64 runs at 256^2)")
@@ -792,9 +793,13 @@ def main():
 
     # ---- solve plan: autotune.solve_plan on this workload's factor and batch
     #      (untimed; in-core tensor-core factors only) ----
-    tune = None
+    tune = tune_nb = None
     if not args.no_tune and OOC_BUDGET == 0 and args.precision not in ("fp32", "fp64"):
         from paper_2412_07631_b300 import autotune
+        if NB_OUTER == 0:  # the outer block width too, unless given
+            NB_OUTER = autotune.outer_block(geom, args.precision, candidates=(2048, 2560, 3072), retune=True)
+            tune_nb = dict(autotune.load_cache().get(
+                autotune._key(geom, args.precision, torch.cuda.get_device_name()), {}))
         Xt_, sys_t, F_t = run_step_kept(ct, torch, geom, args.precision, B, args.max_iter, args.tol)
         del Xt_
         SOLVE_PLAN = autotune.solve_plan(F_t, B, max_iter=args.max_iter, tol=args.tol, retune=True)
@@ -914,7 +919,9 @@ def main():
         _, cB = make_inputs(ct, torch, "c2")
         cmp = {"workload": workload_desc("c2")}
         mixed = args.precision if args.precision not in ("fp64", "fp32") else "tf32"
-        plan_c3, SOLVE_PLAN = SOLVE_PLAN, (0, 0)  # the tuned plan belongs to the 256^2 workload
+        # the tuned blocking belongs to the main workload
+        plan_c3, SOLVE_PLAN = SOLVE_PLAN, (0, 0)
+        nb_c3, NB_OUTER = NB_OUTER, args.nb_outer
         for prec in ("fp64", mixed):
             Bd = torch.from_numpy(cB).double().cuda()
             run_step(ct, torch, cg, prec, Bd, args.max_iter, args.tol) if prec == mixed else None
@@ -923,7 +930,7 @@ def main():
                          "slices_per_s": ck / (ph["solve"] * 1e-3),
                          "refine_iters": inf.get("iterations", 0),
                          "inner_iters": inf.get("inner_iterations", 0)}
-        SOLVE_PLAN = plan_c3
+        SOLVE_PLAN, NB_OUTER = plan_c3, nb_c3
         # the FP64 path at this workload: its 128^2 QR rate over this
         # workload's QR flops, its 128^2 per-slice solve time scaled by the
         # per-slice flop ratio
@@ -974,7 +981,8 @@ def main():
                        "l2": "inputs larger than L2 (dense A~ of %.1f GB rebuilt every step)"
                              % (M * n * 4 / 1e9),
                        "solve_plan": {"solve_block": SOLVE_PLAN[0], "solve_split": SOLVE_PLAN[1],
-                                      "tuned": tune}},
+                                      "tuned": tune},
+                       "nb_outer": {"value": NB_OUTER or "library default", "tuned": tune_nb}},
             "qr_tflops": qr_fl / (qr_ms * 1e-3) / 1e12,
             "qr_tflops_dense_equivalent": flops_of(ns, nv, nb, sl, k, dense=True)[2] / (qr_ms * 1e-3) / 1e12,
             "slices_per_s": k / (solve_ms * 1e-3),

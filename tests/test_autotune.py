@@ -82,3 +82,23 @@ def test_solve_plan_picks_fastest_and_caches(tmp_path):
     class _B2:
         shape = (64, 100)
     assert autotune.solve_plan(_F(), _B2(), path=path, timer=lambda *a: 1.0) == (1024, 256)
+
+
+@pytest.mark.gpu
+def test_solve_plan_real_run(tmp_path):
+    """The solve-plan tuner on the GPU: it times the candidates on the given
+    factor and batch, leaves the factor at the choice, and the factor then
+    solves with that plan."""
+    from gpu_util import need_cuda
+    torch = need_cuda()
+    import paper_2412_07631_b300 as ct
+    from paper_2412_07631_b300 import autotune
+    g = ct.make_geometry(40, 70, 58, 0.05)
+    sysg = ct.System(g, "fp32")
+    F = sysg.factor("bf16")
+    B = torch.ones((8, sysg.m), dtype=torch.float64, device="cuda")
+    plan = autotune.solve_plan(F, B, candidates=((512, 256), (1024, 64)), path=str(tmp_path / "t.json"),
+                               max_iter=10, tol=1e-8)
+    assert plan in ((512, 256), (1024, 64)) and F.solve_plan == plan
+    X = F.solve(B, max_iter=10, tol=1e-8)
+    assert torch.isfinite(X).all() and F.last_info["stop_measure"] <= 1e-8
