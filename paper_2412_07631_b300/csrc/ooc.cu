@@ -531,11 +531,28 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
     void *sp = nullptr, *stg[2] = {nullptr, nullptr};
     cudaStream_t cs = nullptr;
     Events ev;  // ready[0..1], free[0..1], host_ready
+    // Host tier: a superpanel's write-back (device to host) and the next
+    // superpanel's load (host to device) run in kPipe column chunks on two
+    // copy streams, each load chunk after the store of the same part of the
+    // device buffer, so the two directions of the link overlap.
+    constexpr int kPipe = 4;
+    const bool piped = d == nullptr;
+    cudaStream_t ss = nullptr, ls = nullptr;  // store stream, load stream
+    cudaEvent_t stored[kPipe] = {}, loaded = nullptr, computed = nullptr;
     auto fail = [&](ct_status st) {
         if (cs) {
             cudaStreamSynchronize(cs);
             cudaStreamDestroy(cs);
         }
+        for (cudaStream_t x : {ss, ls})
+            if (x) {
+                cudaStreamSynchronize(x);
+                cudaStreamDestroy(x);
+            }
+        for (cudaEvent_t x : stored)
+            if (x) cudaEventDestroy(x);
+        if (loaded) cudaEventDestroy(loaded);
+        if (computed) cudaEventDestroy(computed);
         cudaStreamSynchronize(s);
         cudaFree(sp);
         if (stg[1]) cudaFree(stg[1]);
@@ -567,6 +584,17 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail(CT_ERR_CUDA);
     for (auto &e : ev.e)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(CT_ERR_CUDA);
+    if (piped) {
+        if (cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&loaded, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&computed, cudaEventDisableTiming) != cudaSuccess)
+            return fail(CT_ERR_CUDA);
+        for (auto &e : stored)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(CT_ERR_CUDA);
+    }
+    const int64_t chunk = ceil_div(W, kPipe);  // columns per pipelined copy
+    int prev_chunks = 0;                       // store chunks of the previous superpanel in flight
     cudaEvent_t *ready = ev.e, *freed = ev.e + 2, host_ready = ev.e[4];
     // both staging buffers start free; no host block is pending
     for (int b = 0; b < 2; ++b)
@@ -595,7 +623,24 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
         const int64_t J0 = c0 / NB, J1 = ceil_div(c1, NB);
         const int64_t rows = f->row_end(c1);  // rows of these columns that can be nonzero
         // 1. the superpanel's columns
-        if ((st = load_cols(f, c0, c1, rows, sp, s)) != CT_OK) return fail(st);
+        if (piped) {
+            int q = 0;
+            for (int64_t a = c0; a < c1; a += chunk, ++q) {
+                const int64_t b = std::min(c1, a + chunk);
+                // the same part of the buffer held the previous superpanel's chunk q
+                if (q < prev_chunks && cudaStreamWaitEvent(ls, stored[q], 0) != cudaSuccess)
+                    return fail(CT_ERR_CUDA);
+                ProfScope prof(PROF_H2D_COLS, ls, 0.0, (double)es * rows * (b - a));
+                if (cudaMemcpy2DAsync((char *)sp + col_bytes * (size_t)(a - c0), col_bytes,
+                                      (char *)f->VR_host + col_bytes * (size_t)a, col_bytes, es * (size_t)rows,
+                                      b - a, cudaMemcpyHostToDevice, ls) != cudaSuccess)
+                    return fail(CT_ERR_CUDA);
+            }
+            if (cudaEventRecord(loaded, ls) != cudaSuccess || cudaStreamWaitEvent(s, loaded, 0) != cudaSuccess)
+                return fail(CT_ERR_CUDA);
+        } else if ((st = load_cols(f, c0, c1, rows, sp, s)) != CT_OK) {
+            return fail(st);
+        }
         // global column c of the superpanel sits at sp + (c - c0) columns
         f->VR = (char *)sp - col_bytes * (size_t)c0;
         // 2. the earlier outer blocks, V streamed through two staging buffers
@@ -646,9 +691,30 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
                 (st = d->set_progress(DISK_FACTORING, c0, c1, (int32_t)o.precision, nb, 0, 0)) != CT_OK)
                 return fail(st);
         }
-        if ((st = store_cols(f, c0, c1, rows, sp, s)) != CT_OK) return fail(st);
-        if (d && (st = write_block_records(f, J0, J1, s)) != CT_OK) return fail(st);
-        if (cudaEventRecord(host_ready, s) != cudaSuccess) return fail(CT_ERR_CUDA);
+        if (piped) {
+            // write-back on the store stream once this superpanel's work is done
+            if (cudaEventRecord(computed, s) != cudaSuccess || cudaStreamWaitEvent(ss, computed, 0) != cudaSuccess)
+                return fail(CT_ERR_CUDA);
+            int q = 0;
+            for (int64_t a = c0; a < c1; a += chunk, ++q) {
+                const int64_t b = std::min(c1, a + chunk);
+                {
+                    ProfScope prof(PROF_D2H_COLS, ss, 0.0, (double)es * rows * (b - a));
+                    if (cudaMemcpy2DAsync((char *)f->VR_host + col_bytes * (size_t)a, col_bytes,
+                                          (char *)sp + col_bytes * (size_t)(a - c0), col_bytes,
+                                          es * (size_t)rows, b - a, cudaMemcpyDeviceToHost, ss) != cudaSuccess)
+                        return fail(CT_ERR_CUDA);
+                }
+                if (cudaEventRecord(stored[q], ss) != cudaSuccess) return fail(CT_ERR_CUDA);
+            }
+            prev_chunks = q;
+            // the next superpanel streams these V blocks back from host memory
+            if (cudaEventRecord(host_ready, ss) != cudaSuccess) return fail(CT_ERR_CUDA);
+        } else {
+            if ((st = store_cols(f, c0, c1, rows, sp, s)) != CT_OK) return fail(st);
+            if (d && (st = write_block_records(f, J0, J1, s)) != CT_OK) return fail(st);
+            if (cudaEventRecord(host_ready, s) != cudaSuccess) return fail(CT_ERR_CUDA);
+        }
         if (d && o.stop_after > 0 && ++done_panels >= o.stop_after && c1 < f->n) {
             if ((st = d->flush()) != CT_OK ||
                 (st = d->set_progress(DISK_FACTORING, c1, c1, (int32_t)o.precision, nb, 0, 0)) != CT_OK)
@@ -658,10 +724,24 @@ extern "C" ct_status ct_qr_factor_ooc(ct_system sys, const ct_opts *opts, size_t
             return fail(CT_ERR_INTERRUPTED);
         }
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaStreamSynchronize(cs) != cudaSuccess)
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaStreamSynchronize(cs) != cudaSuccess ||
+        (ss && cudaStreamSynchronize(ss) != cudaSuccess) || (ls && cudaStreamSynchronize(ls) != cudaSuccess))
         return fail(CT_ERR_CUDA);
     cudaStreamDestroy(cs);
     cs = nullptr;
+    for (cudaStream_t *x : {&ss, &ls})
+        if (*x) {
+            cudaStreamDestroy(*x);
+            *x = nullptr;
+        }
+    for (auto &x : stored)
+        if (x) {
+            cudaEventDestroy(x);
+            x = nullptr;
+        }
+    if (loaded) cudaEventDestroy(loaded);
+    if (computed) cudaEventDestroy(computed);
+    loaded = computed = nullptr;
     cudaFree(sp);
     sp = nullptr;
     cudaFree(stg[1]);
