@@ -113,10 +113,11 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
                    Scratch &ws, cudaStream_t s, bool use_gram = true, void *Tp = nullptr,
                    void *Vtp = nullptr, int64_t ldt = 0, bool *made_t = nullptr);
 // panel_gram.cu: the Gram-based kernel; ws as sized by panel_gram_ws_bytes(G);
+// bar: 4 grid-meet counters the caller has zeroed on the stream;
 // *fallback is set to 1 if the panel was left for the column-by-column kernel.
 size_t panel_gram_ws_bytes(int G);
-ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
-                     int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
+ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar,
+                     int G, int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
                      cudaStream_t s);
 // One grid meet that cannot complete (failure-detection check): returns
 // CT_ERR_TIMEOUT once the bounded wait has given up.

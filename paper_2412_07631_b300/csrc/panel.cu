@@ -298,6 +298,9 @@ constexpr int RP_WARPS = RP_THREADS / 32;
 constexpr int RP_REC = 72;   // partial record: dots[32] | row[32] | ss  (floats, padded)
 constexpr int RP_TOT = 72;   // total record (64-bit words): dots[32] | row[32] | ss
 constexpr int RP_MAX_PER_WARP = 19;  // records per warp of the reducing CTA: G <= 152
+// leading bytes of the column-by-column kernel's workspace that must be zero
+// at launch: the totals [2][RP_TOT] words and the counters (256 bytes)
+constexpr size_t regs_zero_bytes() { return sizeof(uint64_t) * 2 * RP_TOT + 256; }
 
 __device__ __forceinline__ void st_word(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -611,13 +614,11 @@ ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float 
         set_error("panel: cooperative grid %d does not fit (%d per SM)", G, per_sm);
         return CT_ERR_CUDA;
     }
-    // workspace (regs_ws_bytes): totals [2][RP_TOT] words | counters [2] | records [2][G][RP_REC] floats
-    const size_t tot_bytes = sizeof(uint64_t) * 2 * RP_TOT;
-    const size_t cnt_bytes = 256;
+    // workspace (regs_ws_bytes): totals [2][RP_TOT] words | counters [2] | records [2][G][RP_REC]
+    // floats; the caller has zeroed the first regs_zero_bytes() on the stream
     uint64_t *tot = (uint64_t *)wsp;
-    unsigned *counter = (unsigned *)(wsp + tot_bytes);
-    float *rec = (float *)(wsp + tot_bytes + cnt_bytes);
-    CT_CUDA(cudaMemsetAsync(wsp, 0, tot_bytes + cnt_bytes, s));
+    unsigned *counter = (unsigned *)(wsp + regs_zero_bytes() - 256);
+    float *rec = (float *)(wsp + regs_zero_bytes());
     DevStatus *st = device_status();
     void *args[] = {&A,         &lda, &M,   &j0,   &tau,  &rec,  &tot,    &counter,
                     &st,        &rows_per, (void *)&only_if, &Tp, &Vtp, &ldt, &trec, &tcount};
@@ -706,7 +707,7 @@ ct_status panel_launch(T *A, int64_t lda, int64_t M, int64_t j0, int nb, T *tau,
 }  // namespace
 
 size_t regs_ws_bytes(int G) {
-    return sizeof(uint64_t) * 2 * RP_TOT + 256 + sizeof(float) * 2 * (size_t)G * RP_REC;
+    return regs_zero_bytes() + sizeof(float) * 2 * (size_t)G * RP_REC;
 }
 
 ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int nb, void *tau,
@@ -727,22 +728,24 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
         G = (int)ceil_div(rows, rows_per);
         const int64_t rpt = ceil_div(rows_per, RP_THREADS);
         if (rows >= 32 && rpt <= 4 && G <= RP_WARPS * RP_MAX_PER_WARP) {
-            // workspace: fallback flag + counter | column-by-column kernel | Gram kernel |
-            // partial Gram records of a fallback's T
+            // workspace: fallback flag, T counter, Gram grid-meet counters | column-by-column
+            // kernel | Gram kernel | partial Gram records of a fallback's T.  One memset
+            // zeroes every flag and counter of both kernels.
             const size_t rb = round_up((int64_t)regs_ws_bytes(G), 256);
             const size_t gb = round_up((int64_t)panel_gram_ws_bytes(G), 256);
             CT_TRY(ws.ensure(256 + rb + gb + sizeof(float) * 528 * (size_t)G));
             int *fallback = (int *)ws.ptr;
             unsigned *tcount = (unsigned *)((char *)ws.ptr + 64);
+            unsigned *gbar = (unsigned *)((char *)ws.ptr + 128);
             char *wr = (char *)ws.ptr + 256;
             float *trec = (float *)(wr + rb + gb);
             const int *only_if = nullptr;
             const bool want_t = use_gram && Tp != nullptr && Vtp != nullptr;
+            CT_CUDA(cudaMemsetAsync(ws.ptr, 0, 256 + regs_zero_bytes(), s));
             if (use_gram) {
-                CT_CUDA(cudaMemsetAsync(ws.ptr, 0, 256, s));
                 ProfScope prof(PROF_PANEL, s, 4.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32,
                                G, 10 + (int)rpt);
-                CT_TRY(panel_gram((float *)A, lda, M, j0, (float *)tau, wr + rb, G, rows_per, (int)rpt,
+                CT_TRY(panel_gram((float *)A, lda, M, j0, (float *)tau, wr + rb, gbar, G, rows_per, (int)rpt,
                                   fallback, want_t ? (float *)Tp : nullptr, (float *)Vtp, ldt, s));
                 only_if = fallback;
             }

@@ -34,6 +34,7 @@ constexpr int GQ_THREADS = 256;
 constexpr int GQ_WARPS = GQ_THREADS / 32;
 constexpr int GQ_TRI = 528;  // upper triangle of a 32 x 32 matrix
 constexpr int GQ_LD = 36;    // row stride of the shared copy of the rows (16-byte rows, 4-way stores)
+constexpr int GQ_MAX_GRID = 160;  // most CTAs of a launch (one per SM)
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -41,12 +42,17 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// (i, j), i <= j, of the column-packed upper triangle
+// (i, j), i <= j, of the column-packed upper triangle: j is the largest
+// integer with j (j + 1) / 2 <= e (the square root estimate, then one
+// integer correction either way)
 __device__ __forceinline__ void tri_ij(int e, int &i, int &j) {
-    j = 0;
-    while ((j + 1) * (j + 2) / 2 <= e) ++j;
+    j = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    if ((j + 1) * (j + 2) / 2 <= e) ++j;
+    if (j * (j + 1) / 2 > e) --j;
     i = e - j * (j + 1) / 2;
 }
+
+constexpr int GQ_PER = (GQ_TRI + GQ_THREADS - 1) / GQ_THREADS;  // entries of the triangle per thread
 
 // All CTAs meet (bounded wait).  Returns false on timeout or another CTA's
 // error; the caller then leaves.
@@ -88,7 +94,7 @@ __global__ void meet_timeout_kernel(unsigned *ctr, DevStatus *st) {
 
 struct GramShared {
     float g[32][33];             // Gram totals (symmetric), then scratch
-    float W[32][33];             // Q1 and its eliminations
+    float X[32][33];             // Q1 and its eliminations, then T (reconstruction)
     float Rm[3][32][33];         // R1, R2, U (the three right-hand triangles of the row solves)
     float rinv[3][32];
     float LR[32][33];            // first 32 rows of the result: V1 below the diagonal, D R on and above
@@ -139,60 +145,76 @@ __device__ bool gram_exchange(float *rows_sm, int64_t nloc, GramShared &s, float
     }
     __syncthreads();
     float *mine = rec + (size_t)blockIdx.x * GQ_TRI;
-    for (int e = threadIdx.x; e < GQ_TRI; e += GQ_THREADS) {
-        int i, j;
-        tri_ij(e, i, j);  // i <= j
-        const int ib = i / 4, jbb = j / 4;
-        // the block (ib, jbb) of the upper triangle, entry (i % 4, j % 4)
-        const int b = ib * 8 - ib * (ib - 1) / 2 + (jbb - ib);
-        const int q = (i % 4) * 4 + (j % 4);
-        float v = 0.0f;
 #pragma unroll
-        for (int g2 = 0; g2 < NGRP; ++g2) v += rows_sm[(g2 * NBLK + b) * 16 + q];
-        mine[e] = v;
+    for (int u = 0; u < GQ_PER; ++u) {
+        const int e = threadIdx.x + u * GQ_THREADS;
+        if (e < GQ_TRI) {
+            int i, j;
+            tri_ij(e, i, j);  // i <= j
+            const int ib = i / 4, jbb = j / 4;
+            // the block (ib, jbb) of the upper triangle, entry (i % 4, j % 4)
+            const int b = ib * 8 - ib * (ib - 1) / 2 + (jbb - ib);
+            const int q = (i % 4) * 4 + (j % 4);
+            float v = 0.0f;
+#pragma unroll
+            for (int g2 = 0; g2 < NGRP; ++g2) v += rows_sm[(g2 * NBLK + b) * 16 + q];
+            mine[e] = v;
+        }
     }
     if (!grid_meet(bar, G, st, site, &s.ok)) return false;
-    // CTA b sums entries [b*E, (b+1)*E) over all CTAs, warp by warp, lanes
-    // striding the records, in a fixed order
+    // CTA b sums entries [b*E, (b+1)*E) over all CTAs, warp by warp, lane l
+    // adding records l, l + 32, ... in that order (all loads issued first),
+    // then the lanes in a fixed tree
     const int E = (GQ_TRI + (int)G - 1) / (int)G;
     const int e0 = (int)blockIdx.x * E, e1 = min(GQ_TRI, e0 + E);
     for (int e = e0 + warp; e < e1; e += GQ_WARPS) {
+        constexpr int PERLANE = (GQ_MAX_GRID + 31) / 32;
+        float r[PERLANE];
+#pragma unroll
+        for (int u = 0; u < PERLANE; ++u) {
+            const unsigned b = lane + 32u * u;
+            r[u] = (b < G) ? __ldcg(rec + (size_t)b * GQ_TRI + e) : 0.0f;
+        }
         double v = 0.0;
-        for (unsigned b = lane; b < G; b += 32) v += (double)__ldcg(rec + (size_t)b * GQ_TRI + e);
+#pragma unroll
+        for (int u = 0; u < PERLANE; ++u)
+            if (lane + 32u * u < G) v += (double)r[u];
         v = warp_sum_d(v);
         if (lane == 0) tot[e] = v;
     }
     if (!grid_meet(bar + 1, G, st, site + 1, &s.ok)) return false;
-    for (int e = threadIdx.x; e < GQ_TRI; e += GQ_THREADS) {
-        int i, j;
-        tri_ij(e, i, j);
-        const float v = (float)__ldcg(tot + e);
-        s.g[i][j] = v;
-        s.g[j][i] = v;
+    float tv[GQ_PER];
+#pragma unroll
+    for (int u = 0; u < GQ_PER; ++u) {
+        const int e = threadIdx.x + u * GQ_THREADS;
+        tv[u] = (e < GQ_TRI) ? (float)__ldcg(tot + e) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < GQ_PER; ++u) {
+        const int e = threadIdx.x + u * GQ_THREADS;
+        if (e < GQ_TRI) {
+            int i, j;
+            tri_ij(e, i, j);
+            const float v = tv[u];
+            s.g[i][j] = v;
+            s.g[j][i] = v;
+        }
     }
     __syncthreads();
     return true;
 }
 
-// The small 32 x 32 steps (a few per panel) run on warp 0 with one row or
-// column per lane in registers: each of the 32 sequential steps is one
-// broadcast (shuffles) and 32 independent FMAs per lane, the pivot picked
-// from the registers by a 5-level select tree.  Reciprocal square roots and
-// reciprocals use the fast hardware approximations (a few ulp; the second
-// Cholesky pass and the FP64 refinement absorb such errors).
-
-// v[i] for a run-time i (select tree of depth 5).
-__device__ __forceinline__ float pick(const float (&v)[32], int i) {
-    float a16[16], a8[8], a4[4];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) a16[q] = (i & 16) ? v[q + 16] : v[q];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) a8[q] = (i & 8) ? a16[q + 8] : a16[q];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) a4[q] = (i & 4) ? a8[q + 4] : a8[q];
-    const float b0 = (i & 2) ? a4[2] : a4[0], b1 = (i & 2) ? a4[3] : a4[1];
-    return (i & 1) ? b1 : b0;
-}
+// The small 32 x 32 steps (a few per panel) run on warp 0, one row or
+// column per lane.  The dependent chains (the Cholesky steps, the triangular
+// solve for Q1, the sign-choosing LU and the solve for T) are unrolled: each
+// step reads its pivot from a register named at compile time and updates
+// only the trailing entries, one broadcast and one FMA each, which are the
+// FMAs of the full-width column sweep in the same order.  The loads and the
+// assembly of U and of the outputs go through 32 x 33 shared-memory copies
+// as short rolled loops (this code runs once per launch from a cold
+// instruction cache, where a short loop costs less than straight-line code).
+// Reciprocal square roots use the fast hardware approximation (a few ulp;
+// the second Cholesky pass and the FP64 refinement absorb such errors).
 
 // R <- chol(s.g) (upper, R^T R = G) into Rout, 1 / diag(R) into rinv, one
 // warp, lane c holding column c.  Returns false (same in every lane) if a
@@ -209,25 +231,22 @@ __device__ __noinline__ bool chol_warp(GramShared &s, float (*Rout)[33], float *
         if (near_identity) good = good && fabsf(g[r] - (r == lane ? 1.0f : 0.0f)) <= 0.25f;
     }
     const float d0 = s.g[lane][lane];
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < 32; ++i) {
-        const float gi = pick(g, i);
+        const float gi = g[i];
         const float gii = __shfl_sync(0xffffffffu, gi, i);
         const float dii = __shfl_sync(0xffffffffu, d0, i);
         const bool ok = gii > min_rel * dii;
         good = good && ok;
         const float ric = (lane >= i && ok) ? gi * rsqrtf(gii) : 0.0f;  // R_ic (R_ii for lane i)
-        Rout[i][lane] = ric;
-        // trailing update; rows k <= i of the column turn to scratch
+        Rout[i][lane] = ric;  // zero below the diagonal (lane < i)
+        // trailing update: rows k > i of the column (rows <= i are not read again)
 #pragma unroll
-        for (int k = 0; k < 32; ++k) g[k] = fmaf(-__shfl_sync(0xffffffffu, ric, k), ric, g[k]);
+        for (int k = i + 1; k < 32; ++k) g[k] = fmaf(-__shfl_sync(0xffffffffu, ric, k), ric, g[k]);
     }
     __syncwarp();
     const float rl = Rout[lane][lane];
     rinv[lane] = (rl > 0.0f) ? __frcp_rn(rl) : 1.0f;
-#pragma unroll
-    for (int r = 0; r < 32; ++r)
-        if (r > lane) Rout[r][lane] = 0.0f;
     __syncwarp();
     return __all_sync(0xffffffffu, good);
 }
@@ -238,46 +257,46 @@ __device__ __noinline__ bool chol_warp(GramShared &s, float (*Rout)[33], float *
 __device__ __noinline__ void reconstruct_warp(GramShared &s, const float *topbuf, float *tau, bool write_tau,
                                               float *Tp, float *Vtp, int64_t ldt) {
     const int lane = threadIdx.x % 32;
-    // Rz = R with its diagonal and lower part zero, into s.W (scratch here)
-#pragma unroll
-    for (int k = 0; k < 32; ++k) s.W[lane][k] = (k > lane) ? s.g[lane][k] : 0.0f;
+    float (*X)[33] = s.X;
     s.rw[lane] = __frcp_rn(s.g[lane][lane]);
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) X[r][lane] = __ldcg(topbuf + r * 32 + lane);  // A1, row by row
     __syncwarp();
-    // x <- A1 R^-1: step j fixes x_j = x[j] / R_jj and removes it from later columns
     float x[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) x[k] = __ldcg(topbuf + lane * 32 + k);
-#pragma unroll 1
-    for (int j = 0; j < 32; ++j) {
-        const float xj = pick(x, j) * s.rw[j];
+    for (int k = 0; k < 32; ++k) x[k] = X[lane][k];
+    // x <- A1 R^-1, forward over the columns: x_j = x_j / R_jj is removed
+    // from the later columns k > j (x_k -= x_j R_jk, j ascending)
 #pragma unroll
-        for (int k = 0; k < 32; ++k) x[k] = fmaf(-xj, s.W[j][k], x[k]);
+    for (int j = 0; j < 32; ++j) {
+        const float xj = x[j] * s.rw[j];
+#pragma unroll
+        for (int k = j + 1; k < 32; ++k) x[k] = fmaf(-xj, s.g[j][k], x[k]);
     }
 #pragma unroll
     for (int k = 0; k < 32; ++k) x[k] *= s.rw[k];
     // LU of I - Q1 D: step j picks d_j = -sign(w_jj), pivot 1 + |w_jj|,
     // multipliers l_rj = -d_j w_rj / (1 + |w_jj|) (rows below j), eliminates
-#pragma unroll 1
-    for (int j = 0; j < 32; ++j) {
-        float wj[32];
+    // them from the later columns k > j
 #pragma unroll
-        for (int k = 0; k < 32; ++k) wj[k] = __shfl_sync(0xffffffffu, x[k], j);
-        const float wjj = pick(wj, j);
+    for (int j = 0; j < 32; ++j) {
+        const float wjj = __shfl_sync(0xffffffffu, x[j], j);
         const float dj = (wjj >= 0.0f) ? -1.0f : 1.0f;
-        const float l = (lane > j) ? -dj * pick(x, j) * __frcp_rn(1.0f + fabsf(wjj)) : 0.0f;
+        const float l = (lane > j) ? -dj * x[j] * __frcp_rn(1.0f + fabsf(wjj)) : 0.0f;
         if (lane > j) s.LR[lane][j] = l;
         if (lane == j) s.dsign[j] = dj;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) x[k] = fmaf(-l, wj[k], x[k]);
+        for (int k = j + 1; k < 32; ++k) x[k] = fmaf(-l, __shfl_sync(0xffffffffu, x[k], j), x[k]);
     }
-    __syncwarp();
-    // lane r's row now holds w_rr and w_rk (k > r) as they stood at step r
-    float (*U)[33] = s.Rm[2];
-    const float xr = pick(x, lane);
-    const float ujj = 1.0f + fabsf(xr), dl = s.dsign[lane];
+    // row r now holds w_rr and w_rk (k > r) as they stood at step r
 #pragma unroll
+    for (int k = 0; k < 32; ++k) X[lane][k] = x[k];
+    __syncwarp();
+    float (*U)[33] = s.Rm[2];
+    const float ujj = 1.0f + fabsf(X[lane][lane]), dl = s.dsign[lane];
+#pragma unroll 4
     for (int k = 0; k < 32; ++k) {
-        U[lane][k] = (k > lane) ? -s.dsign[k] * x[k] : (k == lane ? ujj : 0.0f);
+        U[lane][k] = (k > lane) ? -s.dsign[k] * X[lane][k] : (k == lane ? ujj : 0.0f);
         if (k >= lane) s.LR[lane][k] = dl * s.g[lane][k];
     }
     s.rinv[2][lane] = __frcp_rn(ujj);
@@ -289,16 +308,18 @@ __device__ __noinline__ void reconstruct_warp(GramShared &s, const float *topbuf
         float t[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) t[k] = U[lane][k];
-#pragma unroll 1
-        for (int l = 0; l < 32; ++l) {
-            const float tl = pick(t, l);
 #pragma unroll
-            for (int k = 0; k < 32; ++k)
-                if (k > l) t[k] = fmaf(-tl, s.LR[k][l], t[k]);
+        for (int l = 0; l < 32; ++l) {
+#pragma unroll
+            for (int k = l + 1; k < 32; ++k) t[k] = fmaf(-t[l], s.LR[k][l], t[k]);
         }
 #pragma unroll
+        for (int k = 0; k < 32; ++k) X[lane][k] = t[k];
+        __syncwarp();
+        // column k of T and of the unit-lower top of V: lane = row
+#pragma unroll 4
         for (int k = 0; k < 32; ++k) {
-            Tp[lane + k * ldt] = (k >= lane) ? t[k] : 0.0f;
+            Tp[lane + k * ldt] = (k >= lane) ? X[lane][k] : 0.0f;
             Vtp[lane + k * ldt] = (k == lane) ? 1.0f : (k < lane ? s.LR[lane][k] : 0.0f);
         }
     }
@@ -411,24 +432,26 @@ __global__ void __launch_bounds__(GQ_THREADS, 1)
 }
 
 template <int RPT>
-ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
+ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar, int G,
                       int64_t rows_per, int *fallback, float *Tp, float *Vtp, int64_t ldt, cudaStream_t s) {
     auto fn = panel_gram_kernel<RPT>;
     const size_t dyn = sizeof(float) * GQ_LD * RPT * GQ_THREADS;
     static PerContextOnce attr;  // the attribute belongs to each device's context
     CT_CUDA(attr.run([&] { return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn); }));
+    if (G < 1 || G > GQ_MAX_GRID) {
+        set_error("gram panel: grid of %d CTAs outside 1..%d", G, GQ_MAX_GRID);
+        return CT_ERR_ARG;
+    }
     int per_sm = 0;
     CT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, GQ_THREADS, dyn));
     if (per_sm * num_sms() < G) {
         set_error("gram panel: cooperative grid %d does not fit (%d per SM)", G, per_sm);
         return CT_ERR_CUDA;
     }
-    // ws: barriers [4] + pad | totals [2][528] FP64 | top block [1024] | records [2][G][528]
-    unsigned *bar = (unsigned *)ws;
-    double *tot = (double *)((char *)ws + 256);
+    // ws: totals [2][528] FP64 | top block [1024] | records [2][G][528]
+    double *tot = (double *)ws;
     float *top = (float *)((char *)tot + sizeof(double) * 2 * GQ_TRI);
     float *rec = top + 1024;
-    CT_CUDA(cudaMemsetAsync(bar, 0, 256, s));
     DevStatus *st = device_status();
     void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &top, &bar, &fallback, &st, &rows_per, &Tp, &Vtp, &ldt};
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(GQ_THREADS), args, dyn, s));
@@ -455,17 +478,17 @@ ct_status wait_selftest(cudaStream_t s) {
 }
 
 size_t panel_gram_ws_bytes(int G) {
-    return 256 + sizeof(double) * 2 * GQ_TRI + sizeof(float) * (1024 + 2 * (size_t)G * GQ_TRI);
+    return sizeof(double) * 2 * GQ_TRI + sizeof(float) * (1024 + 2 * (size_t)G * GQ_TRI);
 }
 
-ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, int G,
-                     int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
+ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar,
+                     int G, int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
                      cudaStream_t s) {
     switch (rpt) {
-        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
-        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
-        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
-        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
         default: return CT_ERR_ARG;
     }
 }
