@@ -174,11 +174,14 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
 
 struct PairSched {
     int64_t mt, nt, tiles, work;
-    bool m_fast;
-    __device__ PairSched(int64_t M, int64_t N, int splits) {
+    bool m_fast, upper;
+    // upper: a square tile grid of which only the tiles on and above the
+    // diagonal are computed (a symmetric product whose lower part is unused)
+    __host__ __device__ PairSched(int64_t M, int64_t N, int splits, bool upper_only) {
         mt = (M + 2 * BMC - 1) / (2 * BMC);
         nt = (N + BN - 1) / BN;
-        tiles = mt * nt;
+        upper = upper_only && mt == nt;
+        tiles = upper ? mt * (mt + 1) / 2 : mt * nt;
         work = tiles * splits;
         m_fast = mt <= nt;
     }
@@ -189,7 +192,17 @@ struct PairSched {
     __device__ void decode(int64_t w, int64_t &mi, int64_t &ni, int64_t &z) const {
         constexpr int64_t kGroup = 8;
         z = w / tiles;
-        const int64_t t = w - z * tiles;
+        int64_t t = w - z * tiles;
+        if (upper) {  // row by row: tile row r holds nt - r tiles, from the diagonal on
+            int64_t r = 0;
+            while (t >= nt - r) {
+                t -= nt - r;
+                ++r;
+            }
+            mi = r;
+            ni = r + t;
+            return;
+        }
         const int64_t nf = m_fast ? mt : nt, ns = m_fast ? nt : mt;
         const int64_t g = t / (kGroup * nf), r = t - g * (kGroup * nf);
         const int64_t rows = min(kGroup, ns - g * kGroup);
@@ -203,7 +216,8 @@ template <int OP>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      int64_t M, int64_t N, int64_t K, int64_t kchunk, int splits, float alpha,
-                     float beta, float *C, int64_t ldc, int64_t split_stride, DevStatus *st) {
+                     float beta, float *C, int64_t ldc, int64_t split_stride, int upper_only,
+                     DevStatus *st) {
     constexpr int BK = Op2<OP>::BK;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
     const int64_t pair = blockIdx.x / 2, npairs = gridDim.x / 2;
-    const PairSched ts(M, N, splits);
+    const PairSched ts(M, N, splits, upper_only != 0);
 
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tmA);
@@ -455,8 +469,8 @@ ct_status launch_pair(const GemmArgs &g, int splits, int64_t kchunk, int64_t spl
     CUtensorMap ma, mb;
     CT_TRY(make_map2(&ma, OP == 1, g.A, g.K, g.M, g.lda, BK, BMC));
     CT_TRY(make_map2(&mb, OP == 1, g.B, g.K, g.N, g.ldb, BK, BNC));
-    const int64_t work = ceil_div(g.M, 2 * BMC) * ceil_div(g.N, BN) * splits;
-    const int64_t pairs = std::min<int64_t>(work, pairs_max);
+    const PairSched sched(g.M, g.N, splits, g.upper_only);
+    const int64_t pairs = std::min<int64_t>(sched.work, pairs_max);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -471,7 +485,7 @@ ct_status launch_pair(const GemmArgs &g, int splits, int64_t kchunk, int64_t spl
     cfg.numAttrs = 1;
     CT_CUDA(cudaLaunchKernelEx(&cfg, gemm_pair_kernel<OP>, ma, mb, g.M, g.N, g.K, kchunk, splits,
                                (float)g.alpha, (float)g.beta, (float *)g.C, g.ldc, split_stride,
-                               status));
+                               (int)g.upper_only, status));
     count_launch();
     return CT_OK;
 }

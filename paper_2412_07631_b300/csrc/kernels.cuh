@@ -73,6 +73,10 @@ struct GemmArgs {
     // K-major layout (element (k, m) at A16 + k + m * lda16), or NULL
     const void *A16 = nullptr;
     int64_t lda16 = 0;
+    // M == N and only C on and above the diagonal is wanted (a symmetric
+    // product): the paired kernel skips its 256 x 256 tiles strictly below
+    // the diagonal, whose part of C is then left undefined
+    bool upper_only = false;
 };
 // C = alpha op(A) op(B) + beta C (column-major).  Chooses split-K when the
 // output has too few tiles for the machine; partial sums go through `ws`

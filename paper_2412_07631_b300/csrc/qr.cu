@@ -51,14 +51,19 @@ GemmArgs mk(ct_factor f, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
 }
 
 // G (w x w, ld NB) = V^T V for the reflector block starting at column j.
+// G = V^T V of the block reflector at column j (w columns).  Its users (the
+// T recurrences and assemblies) read G on and above the diagonal only, so
+// the deep product below the top block may leave tiles strictly below the
+// diagonal undefined.
 ct_status gram(ct_factor f, int64_t j, int w, const void *Vt, void *G, cudaStream_t s) {
     const int64_t NB = f->NB;
     CT_TRY(gemm(mk(f, true, false, w, w, w, 1.0, Vt, NB, Vt, NB, 0.0, G, NB), f->gemm_ws, s));
     const int64_t kb = f->row_end(j + w) - j - w;
     if (kb > 0) {
         const void *Vb = at(f->VR, j + w, j, f->lda, f->es());
-        CT_TRY(gemm(mk(f, true, false, w, w, kb, 1.0, Vb, f->lda, Vb, f->lda, 1.0, G, NB),
-                    f->gemm_ws, s));
+        GemmArgs g = mk(f, true, false, w, w, kb, 1.0, Vb, f->lda, Vb, f->lda, 1.0, G, NB);
+        g.upper_only = true;
+        CT_TRY(gemm(g, f->gemm_ws, s));
     }
     return CT_OK;
 }
