@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -255,6 +256,22 @@ struct ProfScope {
 // buffer is registered so that ct_debug_check_canaries can verify them.
 constexpr size_t kGuardBytes = (size_t)64 << 10;
 constexpr unsigned char kGuardByte = 0xA5;
+// 32 FP32 values rounded to BF16 (nearest) and stored as four 16-byte
+// words at dst (16-byte aligned): one row of a row-major BF16 copy.
+__device__ __forceinline__ void store_bf16_row32(void *dst, const float (&x)[32]) {
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const __nv_bfloat162 p = __floats2bfloat162_rn(x[8 * q + 2 * h], x[8 * q + 2 * h + 1]);
+            w[h] = *reinterpret_cast<const uint32_t *>(&p);
+        }
+        d[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 struct Scratch {
     void *ptr = nullptr;
     size_t bytes = 0;

@@ -117,9 +117,12 @@ ct_status qr_factor_run(ct_factor f, cudaStream_t s);
 ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, cudaStream_t s);
 // C <- (I - V op(T) V^T) C for the block at column j (see qr.cu); vb/ldvb:
 // V below the top block from a staging buffer instead of VR (nullptr: VR).
+// v16r (BF16 updates of narrow blocks, w <= 32): the BF16 rounding of V below
+// its top block, row-major with ld round_up(w, 64), already made by the
+// panel kernel (nullptr: rounded here).
 ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void *T, bool qt, void *C,
                       int64_t ldc, int64_t ncols, cudaStream_t s, ctqr::GemmKind big, const void *vb,
-                      int64_t ldvb);
+                      int64_t ldvb, const void *v16r_made = nullptr);
 ct_status stage_v_block(ct_factor f, int64_t J, void *dst, int64_t *ldd, cudaStream_t s);
 // R X = C or R^T X = C in place for the factor's R (blocked, inverse diagonal blocks).
 ct_status trsm_factor(ct_factor f, bool trans, void *C, int64_t ldc, int64_t k, cudaStream_t s);

@@ -113,16 +113,21 @@ ct_status splitk_reduce(bool fp64, int64_t M, int64_t N, int splits, const void 
 // declined the panel, the column-by-column one (one exchange per column).
 // With Tp, Vtp (ld ldt) given, the Gram path (or its fallback) also writes
 // the panel's T_p and the unit-lower top of its V there and sets *made_t.
+// With V16 given, those kernels also store the BF16 rounding of V below its
+// top block (rows j0+32 .. M-1), row by row: element (r, k) at
+// V16[(r - j0 - 32) * ld16 + k] (16-byte aligned, ld16 a multiple of 8), and
+// set *made_v16.
 ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int nb, void *tau,
                    Scratch &ws, cudaStream_t s, bool use_gram = true, void *Tp = nullptr,
-                   void *Vtp = nullptr, int64_t ldt = 0, bool *made_t = nullptr);
+                   void *Vtp = nullptr, int64_t ldt = 0, bool *made_t = nullptr, void *V16 = nullptr,
+                   int64_t ld16 = 0, bool *made_v16 = nullptr);
 // panel_gram.cu: the Gram-based kernel; ws as sized by panel_gram_ws_bytes(G);
 // bar: 4 grid-meet counters the caller has zeroed on the stream;
 // *fallback is set to 1 if the panel was left for the column-by-column kernel.
 size_t panel_gram_ws_bytes(int G);
 ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar,
                      int G, int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
-                     cudaStream_t s);
+                     void *V16, int64_t ld16, cudaStream_t s);
 // One grid meet that cannot complete (failure-detection check): returns
 // CT_ERR_TIMEOUT once the bounded wait has given up.
 ct_status wait_selftest(cudaStream_t s);

@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
     panel_qr_regs_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec,
                          uint64_t *tot, unsigned *counter, DevStatus *st, int64_t rows_per,
                          const int *only_if, float *Tp, float *Vtp, int64_t ldt, float *trec,
-                         unsigned *tcount) {
+                         unsigned *tcount, uint8_t *V16, int64_t ld16) {
     // after the Gram-based kernel: run only if it declined this panel
     if (only_if != nullptr && *only_if == 0) return;
     __shared__ float red[RP_WARPS][32];
@@ -597,6 +597,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
         if (lr < nloc) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) A[(r0 + lr) + (j0 + k) * lda] = a[i][k];
+            const int64_t gr = r0 + lr;
+            if (V16 != nullptr && gr >= j0 + 32) store_bf16_row32(V16 + 2 * (size_t)((gr - j0 - 32) * ld16), a[i]);
         }
     }
     if (only_if != nullptr && Tp != nullptr) fallback_t(A, lda, j0, r0, nloc, tau, Tp, Vtp, ldt, trec, tcount);
@@ -605,7 +607,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
 template <int RPT>
 ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, char *wsp,
                             int G, int64_t rows_per, const int *only_if, float *Tp, float *Vtp, int64_t ldt,
-                            float *trec, unsigned *tcount, cudaStream_t s) {
+                            float *trec, unsigned *tcount, void *V16, int64_t ld16, cudaStream_t s) {
     const int64_t rows = M - j0;
     auto fn = panel_qr_regs_kernel<RPT>;
     int per_sm = 0;
@@ -620,8 +622,9 @@ ct_status panel_regs_launch(float *A, int64_t lda, int64_t M, int64_t j0, float 
     unsigned *counter = (unsigned *)(wsp + regs_zero_bytes() - 256);
     float *rec = (float *)(wsp + regs_zero_bytes());
     DevStatus *st = device_status();
+    uint8_t *v16 = (uint8_t *)V16;
     void *args[] = {&A,         &lda, &M,   &j0,   &tau,  &rec,  &tot,    &counter,
-                    &st,        &rows_per, (void *)&only_if, &Tp, &Vtp, &ldt, &trec, &tcount};
+                    &st,        &rows_per, (void *)&only_if, &Tp, &Vtp, &ldt, &trec, &tcount, &v16, &ld16};
     ProfScope prof(PROF_PANEL, s, 2.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32, G,
                    2 + RPT);
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(RP_THREADS), args, 0, s));
@@ -712,8 +715,10 @@ size_t regs_ws_bytes(int G) {
 
 ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int nb, void *tau,
                    Scratch &ws, cudaStream_t s, bool use_gram, void *Tp, void *Vtp, int64_t ldt,
-                   bool *made_t) {
+                   bool *made_t, void *V16, int64_t ld16, bool *made_v16) {
     if (made_t) *made_t = false;
+    if (made_v16) *made_v16 = false;
+    if (V16 != nullptr && (((uintptr_t)V16 & 15) || (ld16 & 7))) return CT_ERR_ARG;
     if (nb <= 0 || nb > 32 || M - j0 < 1) return CT_ERR_ARG;
     if (fp64) {
         if (nb <= 16) return panel_launch<double, 16>((double *)A, lda, M, j0, nb, (double *)tau, ws, s);
@@ -746,17 +751,18 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
                 ProfScope prof(PROF_PANEL, s, 4.0 * rows * 32 * 32, 2.0 * sizeof(float) * rows * 32, rows, 32,
                                G, 10 + (int)rpt);
                 CT_TRY(panel_gram((float *)A, lda, M, j0, (float *)tau, wr + rb, gbar, G, rows_per, (int)rpt,
-                                  fallback, want_t ? (float *)Tp : nullptr, (float *)Vtp, ldt, s));
+                                  fallback, want_t ? (float *)Tp : nullptr, (float *)Vtp, ldt, V16, ld16, s));
                 only_if = fallback;
             }
             float *tp = want_t ? (float *)Tp : nullptr;
             float *vp = want_t ? (float *)Vtp : nullptr;
             ct_status st;
-            if (rpt <= 1) st = panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
-            else if (rpt <= 2) st = panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
-            else if (rpt <= 3) st = panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
-            else st = panel_regs_launch<4>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, s);
+            if (rpt <= 1) st = panel_regs_launch<1>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, V16, ld16, s);
+            else if (rpt <= 2) st = panel_regs_launch<2>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, V16, ld16, s);
+            else if (rpt <= 3) st = panel_regs_launch<3>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, V16, ld16, s);
+            else st = panel_regs_launch<4>((float *)A, lda, M, j0, (float *)tau, wr, G, rows_per, only_if, tp, vp, ldt, trec, tcount, V16, ld16, s);
             if (st == CT_OK && made_t) *made_t = want_t;
+            if (st == CT_OK && made_v16) *made_v16 = V16 != nullptr;
             return st;
         }
     }

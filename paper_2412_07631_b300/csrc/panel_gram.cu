@@ -340,7 +340,7 @@ template <int RPT>
 __global__ void __launch_bounds__(GQ_THREADS, 1)
     panel_gram_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec, double *tot,
                       float *topbuf, unsigned *bar, int *fallback, DevStatus *st, int64_t rows_per,
-                      float *Tp, float *Vtp, int64_t ldt) {
+                      float *Tp, float *Vtp, int64_t ldt, uint8_t *V16, int64_t ld16) {
     __shared__ GramShared s;
     extern __shared__ float rows_sm[];  // [RPT * GQ_THREADS][GQ_LD], row-major
     const unsigned G = gridDim.x;
@@ -427,13 +427,15 @@ __global__ void __launch_bounds__(GQ_THREADS, 1)
         } else {
 #pragma unroll
             for (int k = 0; k < 32; ++k) A[gr + (j0 + k) * lda] = a[i][k];
+            if (V16 != nullptr) store_bf16_row32(V16 + 2 * (size_t)((gr - j0 - 32) * ld16), a[i]);
         }
     }
 }
 
 template <int RPT>
 ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar, int G,
-                      int64_t rows_per, int *fallback, float *Tp, float *Vtp, int64_t ldt, cudaStream_t s) {
+                      int64_t rows_per, int *fallback, float *Tp, float *Vtp, int64_t ldt, void *V16,
+                      int64_t ld16, cudaStream_t s) {
     auto fn = panel_gram_kernel<RPT>;
     const size_t dyn = sizeof(float) * GQ_LD * RPT * GQ_THREADS;
     static PerContextOnce attr;  // the attribute belongs to each device's context
@@ -453,7 +455,9 @@ ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, 
     float *top = (float *)((char *)tot + sizeof(double) * 2 * GQ_TRI);
     float *rec = top + 1024;
     DevStatus *st = device_status();
-    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &top, &bar, &fallback, &st, &rows_per, &Tp, &Vtp, &ldt};
+    uint8_t *v16 = (uint8_t *)V16;
+    void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &top, &bar, &fallback, &st, &rows_per, &Tp, &Vtp, &ldt,
+                    &v16, &ld16};
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(GQ_THREADS), args, dyn, s));
     count_launch();
     return CT_OK;
@@ -483,12 +487,12 @@ size_t panel_gram_ws_bytes(int G) {
 
 ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar,
                      int G, int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
-                     cudaStream_t s) {
+                     void *V16, int64_t ld16, cudaStream_t s) {
     switch (rpt) {
-        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
-        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
-        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
-        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, s);
+        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
+        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
+        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
+        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
         default: return CT_ERR_ARG;
     }
 }

@@ -125,7 +125,7 @@ ct_status top_block(int w, int64_t ncols, const void *Vt, const void *Tm, int64_
 // when given (a block streamed from host memory).
 ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void *T, bool qt,
                       void *C, int64_t ldc, int64_t ncols, cudaStream_t s, GemmKind big,
-                      const void *vb, int64_t ldvb) {
+                      const void *vb, int64_t ldvb, const void *v16r_made) {
     if (ncols <= 0) return CT_OK;
     const int64_t NB = f->NB;
     const size_t es = f->es();
@@ -145,7 +145,12 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     GemmKind tn_kind = big;
     const void *v16c = nullptr, *v16r = nullptr;
     int64_t ld16c = 0, ld16r = 0;
-    if (big == GEMM_BF16 && kb > 0) {
+    if (big == GEMM_BF16 && kb > 0 && w <= 32 && v16r_made != nullptr) {
+        // the panel kernel rounded V already (row-major, the layout C -= V W2 reads)
+        tn_kind = GEMM_TF32;
+        ld16r = round_up(w, 64);
+        v16r = v16r_made;
+    } else if (big == GEMM_BF16 && kb > 0) {
         if (w <= 256) tn_kind = GEMM_TF32;
         ld16c = round_up(kb, 64);
         ld16r = round_up(w, 64);
@@ -268,18 +273,26 @@ ct_status qr_factor_range(ct_factor f, int64_t J0, int64_t J1, int64_t col_end, 
                 // T_p of this panel goes straight into its diagonal block of T_J;
                 // the Gram panel kernels write it with the top of V
                 void *Tp = at(TJ, p - j, p - j, NB, es);
-                bool made = false;
+                bool made = false, made16 = false;
+                const int64_t ncols_in = q + wq - (p + wp);
+                // BF16 updates: the panel kernel also rounds V below its top
+                // block for the update of the rest of the mid block
+                void *v16 = nullptr;
+                const int64_t kbp = f->row_end(p + wp) - p - wp;
+                if (!f->fp64 && f->upd_kind == GEMM_BF16 && wp == 32 && ncols_in > 0 && kbp > 0) {
+                    CT_TRY(f->V16.ensure(2 * (size_t)round_up(wp, 64) * (size_t)kbp));
+                    v16 = f->V16.ptr;
+                }
                 CT_TRY(panel_qr(f->fp64, f->VR, lda, f->row_end(p + wp), p, wp, f->tau, f->panel_ws, s,
-                                f->gram_panel, Tp, Vtp, NB, &made));
+                                f->gram_panel, Tp, Vtp, NB, &made, v16, round_up(wp, 64), &made16));
                 if (!made) {
                     CT_TRY(extract_vtop(f->fp64, f->VR, lda, p, wp, Vtp, NB, s));
                     CT_TRY(gram(f, p, wp, Vtp, f->G.ptr, s));
                     CT_TRY(larft_from_gram(f->fp64, wp, f->G.ptr, NB, (char *)f->tau + es * p, Tp, NB, s));
                 }
-                const int64_t ncols_in = q + wq - (p + wp);
                 if (ncols_in > 0)
                     CT_TRY(apply_block(f, p, wp, Vtp, Tp, true, at(f->VR, p, p + wp, lda, es), lda,
-                                       ncols_in, s, f->upd_kind, nullptr, 0));
+                                       ncols_in, s, f->upd_kind, nullptr, 0, made16 ? v16 : nullptr));
             }
             const int64_t ncols_mid = j + w - (q + wq);
             if (wq < w && ncols_mid > 0) {
