@@ -518,7 +518,7 @@ CT_API ct_status ct_gemm(int32_t kind, char transa, char transb, int64_t M, int6
  * as the operands).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, and again after that
- * device's context has been re-created; make it before any stream capture.
+ * device's context has been re-created.
  * All calls share the array: calls that overlap on the GPU race.  A product
  * whose K-major operand copies would not fit in the array is refused with
  * CT_ERR_ARG (ct_last_error says how much it needs); the split-K depth of

@@ -18,8 +18,7 @@
 // code it is a host-side stand-in, not a device address), so the first call
 // on each device -- with that device current -- looks up the device addresses
 // with cudaGetSymbolAddress and keeps them for that device's context (a
-// context created anew, after cudaDeviceReset, is looked up again).  Make that
-// first call before any stream capture.
+// context created anew, after cudaDeviceReset, is looked up again).
 //
 // Accepted kinds: 0 (FP64), 1 (FP32) and 2 (TF32); the BF16 and split
 // products (kinds 3-5) need operand copies as large as the operands and are
