@@ -23,7 +23,9 @@
 // 128-byte stages) of its share of the work list.  Warp 0 issues TMA loads
 // into a 4-stage shared-memory ring; warp 1 allocates 512 TMEM columns (two
 // 128 x 256 FP32 accumulators) and one of its threads issues the MMAs (UMMA
-// M=128, N=256); warps 2-9 drain an accumulator with tcgen05.ld and write C
+// M=128, N=256, or N = the tile's columns inside C rounded up to 16 for a
+// narrow last tile, so a product of 32-224 columns, such as a panel's V^T C,
+// does not pay for 256); warps 2-9 drain an accumulator with tcgen05.ld and write C
 // while the MMAs of the next tile fill the other accumulator.  The tile order
 // puts the grid dimension with fewer tiles fastest, so CTAs resident at the
 // same time share the operand tile of the longer dimension through L2.
@@ -225,10 +227,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         constexpr uint32_t F = OpTraits<OP>::FMT;
-        const uint32_t idesc = (1u << 4)                       // D = F32
-                               | (F << 7) | (F << 10)          // A, B = TF32 or BF16, K-major
-                               | ((uint32_t)(BN >> 3) << 17)   // N
-                               | ((uint32_t)(BM >> 4) << 24);  // M
+        const uint32_t idesc0 = (1u << 4)                       // D = F32
+                                | (F << 7) | (F << 10)          // A, B = TF32 or BF16, K-major
+                                | ((uint32_t)(BM >> 4) << 24);  // M
         int64_t kt_glob = 0, local = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < ts.work && ok; w += gridDim.x, ++local) {
@@ -236,6 +237,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             ts.decode(w, mi, ni, z);
             const int64_t kb = z * kchunk, ke = min(K, kb + kchunk);
             const int nk = (int)((ke - kb + BK - 1) / BK);
+            // MMA width: the tile's columns inside C, rounded up to 16 (M = 128
+            // takes N = 16 .. 256 in steps of 16); B's rows beyond N are the
+            // copy engine's zero fill, and the epilogue stores no column >= N
+            const int64_t nvalid = min((int64_t)BN, N - ni * BN);
+            const uint32_t idesc = idesc0 | ((uint32_t)(((nvalid + 15) / 16 * 16) >> 3) << 17);
             const int b = (int)(local & 1);
             const uint32_t use = (uint32_t)(local >> 1);
             if (!mbar_wait(&acc_empty[b], (use & 1u) ^ 1u, st, 5)) break;
