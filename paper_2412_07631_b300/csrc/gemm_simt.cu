@@ -139,11 +139,12 @@ static ct_status gemm_copied(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
     const int64_t Kc = split ? 3 * g.K : g.K;  // depth of the product of the copies
     const int64_t ldt = round_up(Kc, 64);
     const bool pre_a = g.kind == GEMM_BF16 && g.A16 != nullptr;  // A already converted by the caller
+    const bool pre_b = g.kind == GEMM_BF16 && g.B16 != nullptr;  // B likewise: no copy, one slab
     const size_t abytes = pre_a ? 0 : (size_t)round_up(es * ldt * g.M, 256);
     int64_t nslab = g.N;
-    if ((size_t)(es * ldt) * (size_t)g.N > kChunkBytes)
+    if (!pre_b && (size_t)(es * ldt) * (size_t)g.N > kChunkBytes)
         nslab = std::max<int64_t>(256, (int64_t)(kChunkBytes / (size_t)(es * ldt)) / 256 * 256);
-    const size_t bbytes = (size_t)round_up(es * ldt * nslab, 256);
+    const size_t bbytes = pre_b ? 0 : (size_t)round_up(es * ldt * nslab, 256);
     const int64_t tiles = ceil_div(g.M, 128) * ceil_div(nslab, 256);
     int64_t splits, kchunk;
     plan_splits(tiles, Kc, 2048, 64, &splits, &kchunk);
@@ -167,7 +168,9 @@ static ct_status gemm_copied(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
         const int64_t nn = std::min(nslab, g.N - n0);
         const size_t fs = 4;  // FP32 operands and C
         const float *Bs = (const float *)((const char *)g.B + fs * (size_t)(g.tb ? n0 : n0 * g.ldb));
-        if (split) CT_TRY(split3_copy(Bs, g.ldb, !g.tb, split_kind, true, Bb, ldt, g.K, nn, s));
+        if (pre_b) {
+            // nothing to convert
+        } else if (split) CT_TRY(split3_copy(Bs, g.ldb, !g.tb, split_kind, true, Bb, ldt, g.K, nn, s));
         else if (!g.tb) CT_TRY(copy_convert_2d(0, Bs, g.ldb, 2, Bb, ldt, g.K, nn, s));
         else CT_TRY(transpose_any(0, Bs, g.ldb, 2, Bb, ldt, nn, g.K, s));
         GemmArgs b = g;
@@ -177,8 +180,8 @@ static ct_status gemm_copied(const GemmArgs &g, Scratch &ws, cudaStream_t s) {
         b.tb = false;
         b.A = Ab;
         b.lda = lda_b;
-        b.B = Bb;
-        b.ldb = ldt;
+        b.B = pre_b ? (const void *)((const char *)g.B16 + 2 * (size_t)(n0 * g.ldb16)) : (const void *)Bb;
+        b.ldb = pre_b ? g.ldb16 : ldt;
         b.N = nn;
         b.C = (char *)g.C + fs * (size_t)(n0 * g.ldc);
         int64_t sp = splits, kc = kchunk;
@@ -205,6 +208,7 @@ ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     if (g0.M < 0 || g0.N < 0 || g0.K < 0) return CT_ERR_ARG;
     if (g0.M == 0 || g0.N == 0) return CT_OK;
     const bool copied = g0.kind == GEMM_BF16 || g0.kind == GEMM_BF16X3 || g0.kind == GEMM_TF32X3;
+    if (g0.splits_out) *g0.splits_out = 0;
     if (copied && g0.K > 0) return gemm_copied(g0, ws, s);
     GemmArgs g = g0;
     const bool fp64 = g.kind == GEMM_F64;
@@ -261,6 +265,11 @@ ct_status gemm(const GemmArgs &g0, Scratch &ws, cudaStream_t s) {
     p.ldc = g.M;
     CT_TRY(tc ? gemm_tc_launch(p, (int)splits, kchunk, g.M * g.N, s)
               : gemm_simt_launch(p, (int)splits, kchunk, g.M * g.N, s));
+    if (g.partials_out != nullptr && g.splits_out != nullptr) {  // the caller reduces
+        *g.partials_out = part;
+        *g.splits_out = (int)splits;
+        return CT_OK;
+    }
     return splitk_reduce(fp64, g.M, g.N, (int)splits, part, g.alpha, g.beta, g.C, g.ldc, s);
 }
 

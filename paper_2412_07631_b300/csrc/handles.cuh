@@ -95,6 +95,7 @@ struct ct_factor_s {
     // work buffers
     ctqr::Scratch gemm_ws, W, W2, G, panel_ws, Bt, trsm_ws, refine_ws, host_pinned, misc, misc2;
     ctqr::Scratch V16;  // BF16 copies of a block reflector's V in both K-major layouts
+    ctqr::Scratch W2h;  // BF16 copy of a narrow reflector's W2 (K-major), from the top-block kernel
     size_t es() const { return fp64 ? 8 : 4; }
     // One past the last row the reflectors of columns [0, col_end) can touch.
     // Below the ray rows, A~ holds sqrt(lambda) I: row m+i is untouched until

@@ -77,6 +77,18 @@ struct GemmArgs {
     // product): the paired kernel skips its 256 x 256 tiles strictly below
     // the diagonal, whose part of C is then left undefined
     bool upper_only = false;
+    // BF16 products only: op(B) already rounded to BF16, K-major (element
+    // (k, n) at B16 + k + n * ldb16), or NULL
+    const void *B16 = nullptr;
+    int64_t ldb16 = 0;
+    // TF32 / FP32 / FP64 products: when the engine splits K, leave the
+    // partial products unreduced (*splits_out of them, each M x N with ld M,
+    // at *partials_out in the engine's scratch) instead of writing C; the
+    // caller sums them in split order, applies alpha and beta, and does so
+    // before the scratch is used again.
+    // *splits_out = 0 when C was written as usual.
+    void **partials_out = nullptr;
+    int *splits_out = nullptr;
 };
 // C = alpha op(A) op(B) + beta C (column-major).  Chooses split-K when the
 // output has too few tiles for the machine; partial sums go through `ws`

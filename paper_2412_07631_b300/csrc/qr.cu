@@ -50,7 +50,6 @@ GemmArgs mk(ct_factor f, bool ta, bool tb, int64_t M, int64_t N, int64_t K, doub
     return g;
 }
 
-// G (w x w, ld NB) = V^T V for the reflector block starting at column j.
 // G = V^T V of the block reflector at column j (w columns).  Its users (the
 // T recurrences and assemblies) read G on and above the diagonal only, so
 // the deep product below the top block may leave tiles strictly below the
@@ -74,11 +73,16 @@ ct_status gram(ct_factor f, int64_t j, int w, const void *Vt, void *G, cudaStrea
 //   w2 = op(T) w,   C_top[:, c] -= Vt w2,   W2[:, c] = w2
 // Vt (unit lower, explicit) and T (upper) are staged in shared memory; every
 // sum runs over r in ascending order.  Replaces three tiny GEMM launches per
-// panel update by one.
+// panel update by one.  With splits > 0, W is the sum of the engine's
+// unreduced split-K partials P (each w x ncols, ld w), added in split order
+// here instead of by a reduction launch; with W2b, the BF16 rounding of W2 is
+// stored as well (K-major for the BF16 product C -= V W2: element (k, c) at
+// W2b[k + c * ldb16]).
 template <typename T>
 __global__ void __launch_bounds__(256) top_block_kernel(int w, int64_t ncols, const T *Vt, const T *Tm,
                                                         int64_t ldt, bool trans_t, const T *W, T *W2,
-                                                        int64_t ldw, T *C, int64_t ldc) {
+                                                        int64_t ldw, T *C, int64_t ldc, const T *P, int splits,
+                                                        __nv_bfloat16 *W2b, int64_t ldb16) {
     __shared__ T sV[32][33], sT[32][33];
     for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
         const int r = idx % 32, c = idx / 32;
@@ -92,7 +96,16 @@ __global__ void __launch_bounds__(256) top_block_kernel(int w, int64_t ncols, co
     const int64_t col = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (col >= ncols) return;
     const T cv = lane < w ? C[lane + col * ldc] : T(0);
-    T acc = lane < w ? W[lane + col * ldw] : T(0);
+    T acc = T(0);
+    if (splits > 0) {
+        if (lane < w) {
+            const int64_t wn = (int64_t)w * ncols;
+            const T *p = P + lane + col * w;
+            for (int z = 0; z < splits; ++z) acc += p[(int64_t)z * wn];
+        }
+    } else if (lane < w) {
+        acc = W[lane + col * ldw];
+    }
     for (int r = 0; r < w; ++r) acc += sV[r][lane] * __shfl_sync(0xffffffffu, cv, r);  // (Vt^T C)_lane
     T w2 = T(0);
     for (int r = 0; r < w; ++r) w2 += sT[lane][r] * __shfl_sync(0xffffffffu, acc, r);   // (op(T) w)_lane
@@ -101,15 +114,18 @@ __global__ void __launch_bounds__(256) top_block_kernel(int w, int64_t ncols, co
     if (lane < w) {
         C[lane + col * ldc] = cv - upd;
         W2[lane + col * ldw] = w2;
+        if (W2b != nullptr) W2b[lane + col * ldb16] = __float2bfloat16_rn((float)w2);
     }
 }
 
 template <typename T>
 ct_status top_block(int w, int64_t ncols, const void *Vt, const void *Tm, int64_t ldt, bool trans_t,
-                    const void *W, void *W2, int64_t ldw, void *C, int64_t ldc, cudaStream_t s) {
+                    const void *W, void *W2, int64_t ldw, void *C, int64_t ldc, cudaStream_t s,
+                    const void *P = nullptr, int splits = 0, void *W2b = nullptr, int64_t ldb16 = 0) {
     const unsigned grid = (unsigned)ceil_div(ncols, 8);
     top_block_kernel<T><<<grid, 256, 0, s>>>(w, ncols, (const T *)Vt, (const T *)Tm, ldt, trans_t,
-                                             (const T *)W, (T *)W2, ldw, (T *)C, ldc);
+                                             (const T *)W, (T *)W2, ldw, (T *)C, ldc, (const T *)P, splits,
+                                             (__nv_bfloat16 *)W2b, ldb16);
     count_launch();
     CT_CUDA(cudaGetLastError());
     return CT_OK;
@@ -165,22 +181,40 @@ ct_status apply_block(ct_factor f, int64_t j, int w, const void *Vt, const void 
     if (w <= 32) {
         // narrow reflector (a panel's): the bulk products over the rows below
         // on the engine, the w x w top-block work fused into one small kernel
+        // W = V_b^T C_b: a split-K product leaves its partials to the
+        // top-block kernel, which adds them in split order
+        void *P = nullptr;
+        int splits = 0;
         if (kb > 0) {
             GemmArgs g = mk(f, true, false, w, ncols, kb, 1.0, Vb, ldV, Cb, ldc, 0.0, W, NB);
             g.kind = tn_kind;
             g.A16 = v16c;
             g.lda16 = ld16c;
+            g.partials_out = &P;
+            g.splits_out = &splits;
             CT_TRY(gemm(g, f->gemm_ws, s));
         } else {
             CT_TRY(fill_zero_2d(f->fp64, W, NB, w, ncols, s));
         }
-        CT_TRY(f->fp64 ? top_block<double>(w, ncols, Vt, T, NB, qt, W, W2, NB, C, ldc, s)
-                       : top_block<float>(w, ncols, Vt, T, NB, qt, W, W2, NB, C, ldc, s));
+        // BF16 product below: the top-block kernel also rounds W2 for it
+        void *w2b = nullptr;
+        const int64_t ldw2b = round_up(w, 64);
+        if (kb > 0 && big == GEMM_BF16) {
+            CT_TRY(f->W2h.ensure(2 * (size_t)ldw2b * ncols));
+            w2b = f->W2h.ptr;
+        }
+        CT_TRY(f->fp64 ? top_block<double>(w, ncols, Vt, T, NB, qt, W, W2, NB, C, ldc, s, P, splits)
+                       : top_block<float>(w, ncols, Vt, T, NB, qt, W, W2, NB, C, ldc, s, P, splits, w2b,
+                                          ldw2b));
         if (kb > 0) {
             GemmArgs g = mk(f, false, false, kb, ncols, w, -1.0, Vb, ldV, W2, NB, 1.0, Cb, ldc);
             g.kind = big;
             g.A16 = v16r;
             g.lda16 = ld16r;
+            if (w2b != nullptr) {
+                g.B16 = w2b;
+                g.ldb16 = ldw2b;
+            }
             CT_TRY(gemm(g, f->gemm_ws, s));
         }
         return CT_OK;
