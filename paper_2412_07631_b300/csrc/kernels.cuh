@@ -135,13 +135,11 @@ ct_status panel_qr(bool fp64, void *A, int64_t lda, int64_t M, int64_t j0, int n
                    int64_t ld16 = 0, bool *made_v16 = nullptr);
 // panel_gram.cu: the Gram-based kernel; ws as sized by panel_gram_ws_bytes(G);
 // bar: 4 grid-meet counters the caller has zeroed on the stream;
-// *fallback is set to 1 if the Gram route declined the panel.
+// *fallback is set to 1 if the panel was left for the column-by-column kernel.
 size_t panel_gram_ws_bytes(int G);
-// If it declines the panel, the column-by-column sweep runs in the same launch
-// (workspace regs_ws, zeroed as for its own kernel; trec and tcount for T).
 ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar,
                      int G, int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
-                     void *V16, int64_t ld16, void *regs_ws, float *trec, unsigned *tcount, cudaStream_t s);
+                     void *V16, int64_t ld16, cudaStream_t s);
 // One grid meet that cannot complete (failure-detection check): returns
 // CT_ERR_TIMEOUT once the bounded wait has given up.
 ct_status wait_selftest(cudaStream_t s);

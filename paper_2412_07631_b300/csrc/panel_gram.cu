@@ -26,7 +26,6 @@
 // the fallback flag; the column-by-column kernel then factors it.
 #include "common.cuh"
 #include "kernels.cuh"
-#include "panel_regs.cuh"
 
 namespace ctqr {
 namespace {
@@ -341,8 +340,7 @@ template <int RPT>
 __global__ void __launch_bounds__(GQ_THREADS, 1)
     panel_gram_kernel(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, float *rec, double *tot,
                       float *topbuf, unsigned *bar, int *fallback, DevStatus *st, int64_t rows_per,
-                      float *Tp, float *Vtp, int64_t ldt, uint8_t *V16, int64_t ld16, float *rrec,
-                      uint64_t *rtot, unsigned *rcounter, float *trec, unsigned *tcount) {
+                      float *Tp, float *Vtp, int64_t ldt, uint8_t *V16, int64_t ld16) {
     __shared__ GramShared s;
     extern __shared__ float rows_sm[];  // [RPT * GQ_THREADS][GQ_LD], row-major
     const unsigned G = gridDim.x;
@@ -385,10 +383,8 @@ __global__ void __launch_bounds__(GQ_THREADS, 1)
                 if (threadIdx.x == 0) s.bad = good ? 0 : 1;
             }
             __syncthreads();
-            if (s.bad) {  // the same decision in every CTA: the grid sweeps the panel column by column
+            if (s.bad) {
                 if (blockIdx.x == 0 && threadIdx.x == 0) *fallback = 1;
-                panel_regs_body<RPT>(A, lda, M, j0, tau, rrec, rtot, rcounter, st, rows_per, Tp, Vtp, ldt, trec,
-                                     tcount, V16, ld16);
                 return;
             }
         } else {
@@ -439,7 +435,7 @@ __global__ void __launch_bounds__(GQ_THREADS, 1)
 template <int RPT>
 ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar, int G,
                       int64_t rows_per, int *fallback, float *Tp, float *Vtp, int64_t ldt, void *V16,
-                      int64_t ld16, void *regs_ws, float *trec, unsigned *tcount, cudaStream_t s) {
+                      int64_t ld16, cudaStream_t s) {
     auto fn = panel_gram_kernel<RPT>;
     const size_t dyn = sizeof(float) * GQ_LD * RPT * GQ_THREADS;
     static PerContextOnce attr;  // the attribute belongs to each device's context
@@ -460,12 +456,8 @@ ct_status gram_launch(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, 
     float *rec = top + 1024;
     DevStatus *st = device_status();
     uint8_t *v16 = (uint8_t *)V16;
-    // the column sweep's workspace (layout of its own kernel's)
-    uint64_t *rtot = (uint64_t *)regs_ws;
-    unsigned *rcounter = (unsigned *)((char *)regs_ws + regs_zero_bytes() - 256);
-    float *rrec = (float *)((char *)regs_ws + regs_zero_bytes());
     void *args[] = {&A, &lda, &M, &j0, &tau, &rec, &tot, &top, &bar, &fallback, &st, &rows_per, &Tp, &Vtp, &ldt,
-                    &v16, &ld16, &rrec, &rtot, &rcounter, &trec, &tcount};
+                    &v16, &ld16};
     CT_CUDA(cudaLaunchCooperativeKernel((const void *)fn, dim3(G), dim3(GQ_THREADS), args, dyn, s));
     count_launch();
     return CT_OK;
@@ -495,12 +487,12 @@ size_t panel_gram_ws_bytes(int G) {
 
 ct_status panel_gram(float *A, int64_t lda, int64_t M, int64_t j0, float *tau, void *ws, unsigned *bar,
                      int G, int64_t rows_per, int rpt, int *fallback, float *Tp, float *Vtp, int64_t ldt,
-                     void *V16, int64_t ld16, void *regs_ws, float *trec, unsigned *tcount, cudaStream_t s) {
+                     void *V16, int64_t ld16, cudaStream_t s) {
     switch (rpt) {
-        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, regs_ws, trec, tcount, s);
-        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, regs_ws, trec, tcount, s);
-        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, regs_ws, trec, tcount, s);
-        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, regs_ws, trec, tcount, s);
+        case 1: return gram_launch<1>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
+        case 2: return gram_launch<2>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
+        case 3: return gram_launch<3>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
+        case 4: return gram_launch<4>(A, lda, M, j0, tau, ws, bar, G, rows_per, fallback, Tp, Vtp, ldt, V16, ld16, s);
         default: return CT_ERR_ARG;
     }
 }
