@@ -98,10 +98,18 @@ __global__ void __launch_bounds__(256) top_block_kernel(int w, int64_t ncols, co
     const T cv = lane < w ? C[lane + col * ldc] : T(0);
     T acc = T(0);
     if (splits > 0) {
-        if (lane < w) {
+        if (lane < w) {  // in split order, the loads eight at a time
             const int64_t wn = (int64_t)w * ncols;
             const T *p = P + lane + col * w;
-            for (int z = 0; z < splits; ++z) acc += p[(int64_t)z * wn];
+            int z = 0;
+            for (; z + 8 <= splits; z += 8) {
+                T v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = p[(int64_t)(z + u) * wn];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += v[u];
+            }
+            for (; z < splits; ++z) acc += p[(int64_t)z * wn];
         }
     } else if (lane < w) {
         acc = W[lane + col * ldw];
