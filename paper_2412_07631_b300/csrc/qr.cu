@@ -264,7 +264,10 @@ static ct_status assemble_t(ct_factor f, int64_t wblk, const void *G, void *T, v
                             int64_t step) {
     const size_t es = f->es();
     const int64_t NB = f->NB;
-    const GemmKind small_kind = f->fp64 ? GEMM_F64 : GEMM_F32;
+    // The refining precisions assemble T from split-TF32 products on the
+    // tensor cores (TF32x3: near FP32, three passes); FP32 and FP64 factors
+    // keep their own arithmetic.
+    const GemmKind small_kind = f->fp64 ? GEMM_F64 : (is_refine_prec(f->prec) ? GEMM_TF32X3 : GEMM_F32);
     for (int64_t o = step; o < wblk; o += step) {
         const int64_t wp = std::min<int64_t>(step, wblk - o);
         if (!f->fp64 && wp <= 32 && (size_t)o * 33 * sizeof(float) <= 200 * 1024) {
