@@ -179,12 +179,16 @@ __global__ void __launch_bounds__(256) inv_double_kernel(int64_t n, int64_t SB, 
 
 // Tensor-core path: inverses of the SB x SB diagonal superblocks of R, by
 // doubling from the TB x TB inverses,
-//   inv([A B; 0 C]) = [inv(A), -inv(A) B inv(C); 0, inv(C)],
-// with the products on the FP32 CUDA cores (exact transposes of each other
-// are kept for R^-1 and R^-T, so the two applications stay adjoint).  Each
-// doubling level is two launches covering every superblock and every block
-// pair of that level (inv_double_kernel), so the grid fills the machine even
-// where one product is a single tile.
+//   inv([A B; 0 C]) = [inv(A), -inv(A) B inv(C); 0, inv(C)]
+// (exact transposes of each other are kept for R^-1 and R^-T, so the two
+// applications stay adjoint).  The narrow levels (blocks below kInvTensorB)
+// run on the FP32 CUDA cores, two launches per level covering every
+// superblock and every block pair of it (inv_double_kernel), so the grid
+// fills the machine where one product is a single tile; the wide levels,
+// which hold most of the flops, run on the tensor-core GEMM engine in split
+// TF32 (TF32x3), two products per block pair.
+constexpr int64_t kInvTensorB = 512;
+
 static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
     const int TB = f->trsm_tb;
     const int64_t n = f->n;
@@ -201,11 +205,34 @@ static ct_status build_superblock_inverses(ct_factor f, cudaStream_t s) {
     // scratch Y: one b x b block per pair of a level (pairs of a superblock:
     // ceil(SB / 2b), the last one possibly ragged or empty)
     int64_t ymax = 1;
-    for (int64_t b = TB; b < SB; b *= 2) ymax = std::max(ymax, nsb * ceil_div(SB, 2 * b) * b * b);
+    for (int64_t b = TB; b < SB; b *= 2)
+        ymax = std::max(ymax, b >= kInvTensorB ? b * b : nsb * ceil_div(SB, 2 * b) * b * b);
     Scratch ys;
     CT_TRY(ys.ensure(sizeof(float) * (size_t)ymax));
     for (int64_t b = TB; b < SB; b *= 2) {
         const int64_t pairs = ceil_div(SB, 2 * b);
+        if (b >= kInvTensorB) {
+            // the wide levels (most of the flops) as two products per pair on
+            // the tensor-core engine, split TF32 (TF32x3: near-FP32 accuracy);
+            // the zero halves of the triangular factors are multiplied too
+            for (int64_t t = 0; t < nsb; ++t) {
+                const int64_t s0 = t * SB, len = std::min<int64_t>(n - s0, SB);
+                char *inv = (char *)f->RinvB + es * t * blk;
+                for (int64_t i = 0; i < pairs; ++i) {
+                    const int64_t pl = 2 * b * i;
+                    if (pl + b >= len) continue;
+                    const int64_t bb = std::min<int64_t>(b, len - pl - b);
+                    GemmArgs g1{GEMM_TF32X3, false, false, b, bb, bb, 1.0,
+                                (const char *)f->Rm + es * ((s0 + pl) + (s0 + pl + b) * f->ldr), f->ldr,
+                                inv + es * ((pl + b) + (pl + b) * SB), SB, 0.0, ys.ptr, b};
+                    CT_TRY(gemm(g1, f->trsm_ws, s));
+                    GemmArgs g2{GEMM_TF32X3, false, false, b, bb, b, -1.0, inv + es * (pl + pl * SB), SB, ys.ptr, b,
+                                0.0, inv + es * (pl + (pl + b) * SB), SB};
+                    CT_TRY(gemm(g2, f->trsm_ws, s));
+                }
+            }
+            continue;
+        }
         const int64_t tiles = ceil_div(b, 128);
         dim3 grid((unsigned)tiles, (unsigned)tiles, (unsigned)(nsb * pairs));
         const double fl = 2.0 * (double)nsb * pairs * b * b * b;  // both stages, triangular halves
