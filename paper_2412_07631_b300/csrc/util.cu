@@ -54,6 +54,44 @@ __global__ void to_bf16_dual_kernel(const float *src, int64_t lds, int64_t rows,
     }
 }
 
+// The same conversion over 64 x 64 tiles: each thread reads 16 values and
+// writes the transposed copy as pairs (4-byte stores, 128 bytes per warp).
+// Needs rowm 4-byte aligned and ldr even.
+__global__ void __launch_bounds__(256) to_bf16_dual64_kernel(const float *src, int64_t lds, int64_t rows,
+                                                             int64_t cols, __nv_bfloat16 *colm, int64_t ldc,
+                                                             __nv_bfloat16 *rowm, int64_t ldr) {
+    __shared__ __align__(16) float t[64][66];  // t[row][col] of the tile
+    const int64_t r0 = (int64_t)blockIdx.x * 64, c0 = (int64_t)blockIdx.y * 64;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int lr = tx + 32 * h, lc = ty + 8 * q;
+            const int64_t r = r0 + lr, c = c0 + lc;
+            float v = 0.0f;
+            if (r < rows && c < cols) {
+                v = src[r + c * lds];
+                if (colm) colm[r + c * ldc] = __float2bfloat16_rn(v);
+            }
+            t[lr][lc] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int lr = ty + 8 * q, lc = 2 * tx;
+        const int64_t r = r0 + lr, c = c0 + lc;
+        if (r < rows && c < cols) {
+            const float2 p = *reinterpret_cast<const float2 *>(&t[lr][lc]);
+            if (c + 1 < cols)
+                *reinterpret_cast<__nv_bfloat162 *>(rowm + c + r * ldr) = __floats2bfloat162_rn(p.x, p.y);
+            else
+                rowm[c + r * ldr] = __float2bfloat16_rn(p.x);
+        }
+    }
+}
+
 // FP32 -> BF16 (round to nearest even), column by column: blockIdx.y strides
 // over columns, each thread converts 4 consecutive rows.
 __global__ void to_bf16_kernel(const float *src, int64_t lds, __nv_bfloat16 *dst, int64_t ldd,
@@ -297,12 +335,18 @@ ct_status convert_bf16_dual(const float *src, int64_t lds, int64_t rows, int64_t
                             void *rowm, int64_t ldr, cudaStream_t s) {
     if (rows == 0 || cols == 0) return CT_OK;
     ProfScope prof(PROF_COPY, s, 0.0, (colm ? 8.0 : 6.0) * (double)rows * cols, rows, cols, 0, colm ? 4 : 5);
-    for (int64_t c0 = 0; c0 < cols; c0 += 32 * 65535LL) {  // grid.y limit
-        const int64_t cc = std::min<int64_t>(cols - c0, 32 * 65535LL);
-        dim3 grid((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cc, 32)), block(32, 8);
-        to_bf16_dual_kernel<<<grid, block, 0, s>>>(src + c0 * lds, lds, rows, cc,
-                                                   colm ? (__nv_bfloat16 *)colm + c0 * ldc : nullptr, ldc,
-                                                   (__nv_bfloat16 *)rowm + c0, ldr);
+    const bool wide = (ldr & 1) == 0 && ((uintptr_t)rowm & 3) == 0;  // pairs of the transposed copy
+    const int64_t tile = wide ? 64 : 32;
+    for (int64_t c0 = 0; c0 < cols; c0 += tile * 65535LL) {  // grid.y limit
+        const int64_t cc = std::min<int64_t>(cols - c0, tile * 65535LL);
+        dim3 grid((unsigned)ceil_div(rows, tile), (unsigned)ceil_div(cc, tile)), block(32, 8);
+        __nv_bfloat16 *cm = colm ? (__nv_bfloat16 *)colm + c0 * ldc : nullptr;
+        if (wide)
+            to_bf16_dual64_kernel<<<grid, block, 0, s>>>(src + c0 * lds, lds, rows, cc, cm, ldc,
+                                                         (__nv_bfloat16 *)rowm + c0, ldr);
+        else
+            to_bf16_dual_kernel<<<grid, block, 0, s>>>(src + c0 * lds, lds, rows, cc, cm, ldc,
+                                                       (__nv_bfloat16 *)rowm + c0, ldr);
         count_launch();
     }
     CT_CUDA(cudaGetLastError());
